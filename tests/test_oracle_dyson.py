@@ -1,0 +1,137 @@
+"""Pins for the dielectric adjoint E and the GMRES solvers (eqs.
+dyson_discretised, op_discretised; Algorithm 1; Lemmas
+inexact_residual_norm, gmres_y_k_bound; Theorem inexact_gmres_dyson).  CPU only."""
+import numpy as np
+import pytest
+
+from oracle import gmres, groundstate, response
+from workloads import make_system, perturbation
+
+
+@pytest.fixture(scope="module")
+def ins():
+    s = make_system("tiny_insulator")
+    return s, groundstate.solve(s)
+
+
+@pytest.fixture(scope="module")
+def metal():
+    s = make_system("tiny_metal")
+    return s, groundstate.solve(s)
+
+
+def test_rescaling_is_an_identity(ins):
+    """eq. op_discretised: v - ||Kv|| chi0(Kv/||Kv||) = v - chi0 K v (linearity)."""
+    s, gs = ins
+    v = np.random.default_rng(0).normal(size=s.dims)
+    np.testing.assert_allclose(response.dielectric(gs, v),
+                               v - response.chi0(gs, response.apply_K(v, gs)), atol=1e-13)
+
+
+def test_adjoint_is_the_dielectric_operator(ins):
+    """E = 1 - chi0 K has transpose 1 - K chi0 (chi0 and K symmetric, Sec. 2.2)."""
+    s, gs = ins
+    rng = np.random.default_rng(1)
+    u, v = rng.normal(size=s.dims), rng.normal(size=s.dims)
+    lhs = (u * response.dielectric(gs, v)).sum()
+    rhs = ((u - response.apply_K(response.chi0(gs, u), gs)) * v).sum()
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("which", ["ins", "metal"])
+def test_gmres_matches_dense_solve(which, ins, metal):
+    s, gs = ins if which == "ins" else metal
+    E = response.dense_operator(lambda v: response.dielectric(gs, v), s.dims)
+    b = response.chi0(gs, perturbation(s))
+    b /= np.linalg.norm(b)
+    x_dense = np.linalg.solve(E, b.ravel()).reshape(s.dims)
+    x, hist = gmres.gmres(lambda v: response.dielectric(gs, v), b, tol=1e-13, m=20)
+    np.testing.assert_allclose(x, x_dense, atol=1e-11)
+    assert np.linalg.norm(b - response.dielectric(gs, x)) < 1e-12
+
+
+@pytest.fixture(scope="module")
+def rhs(ins):
+    s, gs = ins
+    b = response.chi0(gs, perturbation(s))
+    return b / np.linalg.norm(b)
+
+
+def _true_residual(gs, b, x):
+    return float(np.linalg.norm(b - response.dielectric(gs, x)))
+
+
+def test_guaranteed_strategy_reaches_tau(ins, rhs):
+    """Theorem inexact_gmres_dyson: with tau^CG <= C_{i,n} s/(3m) tau/||r~_{i-1}||
+    (exact prefactor, gaps kept) the true residual is <= tau."""
+    s, gs = ins
+    for tau in (1e-6, 1e-9):
+        res = gmres.inexact_gmres(gs, rhs, tau, 10, "grt_exact")
+        assert res.converged
+        assert _true_residual(gs, rhs, res.x) <= tau
+
+
+def test_residual_lemmas_hold(ins, rhs):
+    """Lemma inexact_residual_norm and Lemma gmres_y_k_bound on the last cycle,
+    with a deliberately loose static strategy so that the errors matter."""
+    s, gs = ins
+    for strategy in ("D10", "agr", "bal"):
+        res = gmres.inexact_gmres(gs, rhs, 1e-8, 8, strategy, track_errors=True)
+        y, H, r = res.cycle_y, res.cycle_H, res.cycle_res
+        true = _true_residual(gs, rhs, res.x)
+        bound = res.cycle_err0 + r[-1] + sum(e * abs(yi) for e, yi in zip(res.cycle_errs, y))
+        assert true <= bound * (1 + 1e-8) + 1e-15
+        sigma = np.linalg.svd(H, compute_uv=False)[-1]
+        for i in range(len(y)):
+            assert abs(y[i]) <= r[i] / sigma * (1 + 1e-10)
+
+
+def test_adaptive_tolerances_grow_as_gmres_converges(ins, rhs):
+    """tau^CG_i ~ 1/||r~_{i-1}|| (Remark rmk:superlinear_convergence): the CG
+    tolerance rises and the inner work per step falls."""
+    s, gs = ins
+    kxc = response.exchange_kernel(gs.rho)
+    tols = [gmres.cg_tolerances(gs, "bal", 1e-9, i, 10, 1.0, r, 1.0, 1.0)[0]
+            for i, r in [(1, 1.0), (2, 1e-3), (3, 1e-6)]]
+    assert tols[0] < tols[1] < tols[2]
+    res = gmres.inexact_gmres(gs, rhs, 1e-9, 20, "bal")
+    assert res.converged
+    assert _true_residual(gs, rhs, res.x) < 1e-8
+    del kxc
+
+
+def test_bal_prefactor_formula(ins, metal):
+    """Table strategies: bal = sqrt|Omega|/sqrt(Nocc) * sqrt|Omega| / (2 f_n sqrt(Ng Nocc));
+    k-form (Table strategies_k with Nocc_k N_mp -> Nocc): |Omega|/(2 f w_k Nocc sqrt(Ng))."""
+    s, gs = ins
+    nocc = gs.kblocks[0].nocc
+    pf = gmres.prefactors(gs, "bal", 1.0)
+    ref = np.sqrt(gs.volume) / np.sqrt(nocc) * np.sqrt(gs.volume) / (
+        2 * 2.0 * np.sqrt(gs.n_grid * nocc))
+    np.testing.assert_allclose(pf, ref, rtol=1e-14)
+    s, gs = metal
+    pf = gmres.prefactors(gs, "bal", 1.0)
+    ntot = sum(kb.nocc for kb in gs.kblocks)
+    i = 0
+    for kb in gs.kblocks:
+        for n in range(kb.nocc):
+            assert abs(pf[i] - gs.volume / (2 * kb.f[n] * kb.weight * ntot * np.sqrt(gs.n_grid))) \
+                <= 1e-12 * pf[i]
+            i += 1
+
+
+def test_cg_stays_in_range_of_Q(ins):
+    """Remark rmk:sternheimer_solution: CG iterates lie in range(Q); >= 1 iteration."""
+    s, gs = ins
+    kb = gs.kblocks[0]
+    Phi = kb.vecs[:, :kb.nocc]
+    rng = np.random.default_rng(3)
+    b = rng.normal(size=len(kb.eps)) + 1j * rng.normal(size=len(kb.eps))
+    b -= Phi @ (Phi.conj().T @ b)
+    x, it, rn = gmres.sternheimer_cg(kb.H, kb.eps[0], Phi, b, 1e-12, kb.kinetic, 1.0)
+    assert np.abs(Phi.conj().T @ x).max() < 1e-12
+    A = kb.H - kb.eps[0] * np.eye(len(kb.eps))
+    Q = np.eye(len(kb.eps)) - Phi @ Phi.conj().T
+    assert np.linalg.norm(b - Q @ A @ Q @ x) < 1e-11
+    _, it1, _ = gmres.sternheimer_cg(kb.H, kb.eps[0], Phi, b, 1e3, kb.kinetic, 1.0)
+    assert it1 == 1

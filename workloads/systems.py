@@ -1,0 +1,189 @@
+"""Seeded synthetic systems shaped like the paper's workloads.
+
+The paper's experiments (Sec. 4: an aluminium supercell, a Heusler alloy and
+silicon, all with GTH pseudopotentials and PBE) cannot be reproduced without
+DFTK and its pseudopotential files.  These systems stand in for them: a
+local external potential made of attractive Gaussian pseudo-atoms,
+``V(r) = -D * sum_a sum_R exp(-|r - R_a - R|^2 / (2 sigma^2))``, sampled on
+the real-space grid X of Sec. 2.3.1, a Gamma-centred Monkhorst-Pack k-grid
+(Sec. 4.1.1) and a Gaussian-bump perturbation dV0.
+
+Conventions (shared with the C ABI, see include/ikr.h):
+  * ``lattice`` is 3x3 with the cell vectors a_1, a_2, a_3 as COLUMNS (bohr).
+  * Real-space arrays have shape (N1, N2, N3) in C order; point (i1,i2,i3) is
+    r = i1/N1 a_1 + i2/N2 a_2 + i3/N3 a_3.
+  * k-points are fractional coordinates in the reciprocal basis b_1, b_2, b_3.
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class System:
+    name: str
+    lattice: np.ndarray          # (3,3) columns are cell vectors [bohr]
+    dims: tuple                  # FFT grid (N1, N2, N3)
+    Ecut: float                  # kinetic-energy cut-off [Ha]
+    kpoints: np.ndarray          # (Nk, 3) fractional reciprocal coordinates
+    kweights: np.ndarray         # (Nk,) weights summing to 1
+    V: np.ndarray                # (N1,N2,N3) external potential on the grid [Ha]
+    n_electrons: int             # total electron count N
+    temperature: float           # smearing T [Ha]; 0 => insulator, f = 2 for N/2 bands
+    nbands: int                  # eigenpairs requested per k-point
+    positions: np.ndarray        # (Natom, 3) Cartesian atom positions [bohr]
+    depth: float
+    width: float
+    seed: int
+
+    @property
+    def volume(self) -> float:
+        return float(abs(np.linalg.det(self.lattice)))
+
+    @property
+    def n_grid(self) -> int:
+        return int(np.prod(self.dims))
+
+
+def monkhorst_pack(grid):
+    """Gamma-centred, unshifted MP grid k = sum_i (j_i / l_i) b_i with equal
+    weights 1/(l1 l2 l3) (Sec. 4.1.1; no symmetry reduction), folded to
+    fractional coordinates in [-1/2, 1/2)."""
+    ks = []
+    for j in itertools.product(*[range(l) for l in grid]):
+        k = np.array([jj / l for jj, l in zip(j, grid)], dtype=np.float64)
+        k = k - np.floor(k + 0.5)
+        ks.append(k)
+    ks = np.array(ks)
+    w = np.full(len(ks), 1.0 / len(ks))
+    return ks, w
+
+
+def _grid_points(lattice, dims):
+    fr = [np.arange(n) / n for n in dims]
+    f1, f2, f3 = np.meshgrid(*fr, indexing="ij")
+    frac = np.stack([f1, f2, f3], axis=-1)          # (N1,N2,N3,3)
+    return frac @ lattice.T                          # Cartesian
+
+
+def gaussian_sum_on_grid(lattice, dims, centers, amplitude, width):
+    """sum_c sum_R amplitude * exp(-|r - c - R|^2 / (2 width^2)) on the grid,
+    with enough periodic images R for the tail to fall below 1e-16."""
+    r = _grid_points(lattice, dims)
+    out = np.zeros(dims, dtype=np.float64)
+    reach = 9.0 * width
+    nimg = [int(math.ceil(reach / np.linalg.norm(lattice[:, i]))) + 1 for i in range(3)]
+    for c in np.atleast_2d(centers):
+        for n in itertools.product(*[range(-m, m + 1) for m in nimg]):
+            shift = lattice @ np.array(n, dtype=np.float64)
+            d = r - (c + shift)
+            d2 = np.einsum("...i,...i->...", d, d)
+            out += amplitude * np.exp(-d2 / (2.0 * width * width))
+    return out
+
+
+def _random_positions(rng, lattice, natoms, min_sep):
+    pos = []
+    inv = np.linalg.inv(lattice)
+    while len(pos) < natoms:
+        p = lattice @ rng.random(3)
+        ok = True
+        for q in pos:
+            d = inv @ (p - q)
+            d -= np.round(d)
+            if np.linalg.norm(lattice @ d) < min_sep:
+                ok = False
+                break
+        if ok:
+            pos.append(p)
+    return np.array(pos)
+
+
+def make_system(name: str) -> System:
+    """Build one of the named synthetic systems (see CONFIGS / TEST_SYSTEMS)."""
+    spec = dict(_SPECS[name])
+    seed = spec["seed"]
+    rng = np.random.default_rng(seed)
+    lattice = np.diag(spec["cell"]).astype(np.float64)
+    if spec["layout"] == "random":
+        positions = _random_positions(rng, lattice, spec["natoms"], spec["min_sep"])
+    elif spec["layout"] == "diamond":
+        a = spec["cell"][0]
+        fcc = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]])
+        basis = np.concatenate([fcc, fcc + 0.25]) * a
+        positions = basis + rng.normal(0.0, spec["jitter"], size=basis.shape)
+    elif spec["layout"] == "slab":
+        Lx, Ly, _ = spec["cell"]
+        pts = []
+        for z in spec["layers"]:
+            for i, j in itertools.product(range(2), range(2)):
+                pts.append([(i + 0.25) * Lx / 2, (j + 0.25) * Ly / 2, z])
+        positions = np.array(pts) + rng.normal(0.0, spec["jitter"], size=(len(pts), 3))
+    elif spec["layout"] == "cubic_lattice":
+        n = spec["per_side"]
+        a = spec["cell"][0] / n
+        pts = [[(i + .5) * a, (j + .5) * a, (k + .5) * a]
+               for i, j, k in itertools.product(range(n), repeat=3)]
+        positions = np.array(pts) + rng.normal(0.0, spec["jitter"], size=(n ** 3, 3))
+    else:
+        raise ValueError(spec["layout"])
+    dims = tuple(spec["dims"])
+    V = gaussian_sum_on_grid(lattice, dims, positions, -spec["depth"], spec["width"])
+    kpts, kw = monkhorst_pack(spec.get("kgrid", (1, 1, 1)))
+    return System(name=name, lattice=lattice, dims=dims, Ecut=float(spec["Ecut"]),
+                  kpoints=kpts, kweights=kw, V=V, n_electrons=int(spec["n_electrons"]),
+                  temperature=float(spec.get("T", 0.0)), nbands=int(spec["nbands"]),
+                  positions=positions, depth=float(spec["depth"]),
+                  width=float(spec["width"]), seed=seed)
+
+
+def perturbation(system: System, kind: str = "bump", seed: int = 0,
+                 amplitude: float = 0.1, width: float = 1.0) -> np.ndarray:
+    """A seeded local perturbation dV0 on the grid: a periodic Gaussian bump of
+    the given amplitude [Ha] and width [bohr] at a random centre."""
+    rng = np.random.default_rng(10_000 + seed)
+    if kind != "bump":
+        raise ValueError(kind)
+    c = system.lattice @ rng.random(3)
+    return gaussian_sum_on_grid(system.lattice, system.dims, c[None, :], amplitude, width)
+
+
+# name -> recipe.  "cfg*" follow the five workload descriptions; "tiny*" are
+# the small cases the oracle solves densely in seconds.
+_SPECS = {
+    # Plain Gamma-point insulator: L=10, Ecut=10, 2 Gaussians (3 Ha, 1 bohr), 4 bands.
+    "cfg1": dict(seed=1, cell=(10.0, 10.0, 10.0), dims=(32, 32, 32), Ecut=10.0,
+                 layout="random", natoms=2, min_sep=3.0, depth=3.0, width=1.0,
+                 n_electrons=8, nbands=6),
+    # Diamond-like cell: a=10.26, 8 Gaussians (4 Ha, 0.8 bohr), 2x2x2 k, 32 electrons.
+    # With these wells band 16 sits inside a near-degenerate group (gap ~2e-4 Ha),
+    # so the system is treated as a metal with Fermi-Dirac smearing T = 0.01 Ha.
+    "cfg2": dict(seed=2, cell=(10.26, 10.26, 10.26), dims=(48, 48, 48), Ecut=15.0,
+                 layout="diamond", jitter=0.02, depth=4.0, width=0.8,
+                 n_electrons=32, nbands=36, T=0.01, kgrid=(2, 2, 2)),
+    # Metallic slab: 10x10x60, 12 Gaussians in 3 layers, 4x4x1 k, 40 bands, FD T=0.01.
+    "cfg3": dict(seed=3, cell=(10.0, 10.0, 60.0), dims=(40, 40, 216), Ecut=20.0,
+                 layout="slab", layers=(25.0, 30.0, 35.0), jitter=0.02, depth=3.0,
+                 width=1.0, n_electrons=48, nbands=40, T=0.01, kgrid=(4, 4, 1)),
+    # Large Gamma-point cell: 20.5 bohr, 64 Gaussians, 128 bands, 96^3 grid.
+    "cfg4": dict(seed=4, cell=(20.5, 20.5, 20.5), dims=(96, 96, 96), Ecut=20.0,
+                 layout="cubic_lattice", per_side=4, jitter=0.05, depth=3.0,
+                 width=1.0, n_electrons=256, nbands=130),
+    # Tiny cases for dense checks.
+    "tiny_insulator": dict(seed=11, cell=(6.0, 6.0, 6.0), dims=(12, 12, 12), Ecut=3.0,
+                           layout="random", natoms=2, min_sep=2.5, depth=3.0, width=1.0,
+                           n_electrons=4, nbands=4),
+    "tiny_ortho_k": dict(seed=12, cell=(5.0, 6.0, 7.0), dims=(10, 12, 14), Ecut=3.0,
+                         layout="random", natoms=2, min_sep=2.5, depth=3.0, width=1.0,
+                         n_electrons=4, nbands=4, kgrid=(2, 1, 1)),
+    "tiny_metal": dict(seed=13, cell=(6.0, 6.0, 6.0), dims=(12, 12, 12), Ecut=3.0,
+                       layout="random", natoms=2, min_sep=2.5, depth=2.0, width=1.0,
+                       n_electrons=6, nbands=24, T=0.05, kgrid=(2, 1, 1)),
+}
+
+CONFIGS = ("cfg1", "cfg2", "cfg3", "cfg4")
+TEST_SYSTEMS = ("tiny_insulator", "tiny_ortho_k", "tiny_metal")
