@@ -1,0 +1,192 @@
+// Mixed-precision Sternheimer solves: FP32 CG (FP32 FFTs, potential products,
+// projections and vector updates) inside an FP64 defect-correction loop.
+//
+// The paper's tolerances are absolute FP64 numbers; an FP32 CG can only reduce
+// its residual to about 1e-6 of its right-hand side.  Each refinement pass
+// therefore solves A d = r in FP32 to max(tol_s, kRel ||r_s||), adds d to the
+// FP64 iterate and, only for systems whose tolerance lies below what FP32 alone
+// reaches, recomputes r = b - A x with an FP64 Hamiltonian application.
+#include <algorithm>
+#include <cmath>
+
+#include "solver.hpp"
+
+namespace ikr {
+
+namespace {
+
+constexpr double kRel = 2e-5;     // relative residual an FP32 CG solve is asked for
+constexpr double kTrust = 1e-3;   // tol >= kTrust ||b||: the FP32 recursive residual is trusted
+constexpr int kMaxRefine = 8;
+
+// partial sums of |v|^2 per system (chunks of 256)
+__global__ void k_sys_norm2(const double2* __restrict__ v, int ld, const int* __restrict__ sys_k,
+                            const int* __restrict__ nb_k, const int* __restrict__ active,
+                            double* __restrict__ part, int nparts) {
+  __shared__ double sh[32];
+  const int s = blockIdx.y;
+  if (active && !active[s]) return;
+  const int nb = nb_k[sys_k[s]];
+  const int g = blockIdx.x * 256 + threadIdx.x;
+  double a = 0.0;
+  if (g < nb) {
+    const double2 x = v[(size_t)s * ld + g];
+    a = x.x * x.x + x.y * x.y;
+  }
+  a = block_sum(a, sh);
+  if (threadIdx.x == 0) part[(size_t)s * nparts + blockIdx.x] = a;
+}
+
+// X64 += D32 (per active system); optionally zero D32 afterwards.
+__global__ void k_add_f32(double2* __restrict__ X, const float2* __restrict__ D, int ld,
+                          const int* __restrict__ sys_k, const int* __restrict__ nb_k,
+                          const int* __restrict__ active) {
+  const int s = blockIdx.y;
+  if (active && !active[s]) return;
+  const int nb = nb_k[sys_k[s]];
+  const int g = blockIdx.x * 256 + threadIdx.x;
+  if (g >= nb) return;
+  const size_t o = (size_t)s * ld + g;
+  const float2 d = D[o];
+  double2 x = X[o];
+  x.x += d.x;
+  x.y += d.y;
+  X[o] = x;
+}
+
+// R = B - W for active systems; R32 = (float) R
+__global__ void k_residual(const double2* __restrict__ B, const double2* __restrict__ W, int ld,
+                           const int* __restrict__ sys_k, const int* __restrict__ nb_k,
+                           const int* __restrict__ active, double2* __restrict__ R,
+                           float2* __restrict__ R32) {
+  const int s = blockIdx.y;
+  if (active && !active[s]) return;
+  const int nb = nb_k[sys_k[s]];
+  const int g = blockIdx.x * 256 + threadIdx.x;
+  if (g >= nb) return;
+  const size_t o = (size_t)s * ld + g;
+  const double2 b = B[o], w = W[o];
+  const double2 r = make_double2(b.x - w.x, b.y - w.y);
+  R[o] = r;
+  R32[o] = make_float2((float)r.x, (float)r.y);
+}
+
+}  // namespace
+
+CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv, const std::vector<double>& shift,
+                    const std::vector<double>& kappa, const std::vector<double>& tol, int maxit) {
+  const int n = L.n;
+  CgStats out;
+  out.fp32 = true;
+  out.iters.assign(n, 0);
+  out.status.assign(n, 1);
+  out.res.assign(n, 0.0);
+  if (n == 0) return out;
+  ensure_workspace(c, n);
+  ensure_pinned(c, n);
+  Workspace& w = c->ws;
+  w.rn.reserve(n);
+  const int ld = c->ld;
+  const cudaStream_t strm = c->stream;
+  const dim3 egrid((ld + 255) / 256, n);
+  const int nparts = (ld + 255) / 256;
+  IKR_CUDA(cudaMemsetAsync(Xv, 0, sizeof(double2) * n * ld, strm));
+  to_fp32(c, Bv, (size_t)n * ld, w.B32.p);
+  auto sys_norms = [&](const double2* v, const int* act, const int* hmask, std::vector<double>& dst) {
+    {
+      ProfScope ps(c, kKidCgVec, 1);
+      k_sys_norm2<<<egrid, 256, 0, strm>>>(v, ld, L.d_k.p, c->d_nb.p, act, w.dpart.p, nparts);
+      IKR_CUDA(cudaGetLastError());
+    }
+    sys_reduce(c, w.dpart.p, nparts, n, act, w.rn.p);
+    IKR_CUDA(cudaMemcpyAsync(c->h_pinned_d, w.rn.p, sizeof(double) * n, cudaMemcpyDeviceToHost, strm));
+    IKR_CUDA(cudaStreamSynchronize(strm));
+    for (int s = 0; s < n; ++s)
+      if (!hmask || hmask[s]) dst[s] = std::sqrt(std::max(0.0, c->h_pinned_d[s]));
+  };
+  std::vector<double> bnorm(n, 0.0), rnorm(n, 0.0);
+  sys_norms(Bv, nullptr, nullptr, bnorm);
+  rnorm = bnorm;
+  std::vector<int> accepted(n, 0), need(n, 0), check(n, 0);
+  for (int pass = 0; pass < kMaxRefine; ++pass) {
+    int nneed = 0;
+    std::vector<double> t32(n, 1e300);
+    for (int s = 0; s < n; ++s) {
+      need[s] = !accepted[s];
+      if (need[s]) {
+        ++nneed;
+        t32[s] = std::max(tol[s], kRel * rnorm[s]);
+      }
+    }
+    if (nneed == 0) break;
+    // FP32 CG on the current residual (systems already accepted run one
+    // iteration and their update is discarded by the mask below)
+    CgStats st = cg_solve<float>(c, L, w.B32.p, w.X32.p, shift, kappa, t32, maxit);
+    for (int s = 0; s < n; ++s) {
+      if (!need[s]) continue;
+      out.iters[s] += st.iters[s];
+      out.n_ham += st.iters[s];
+      if (st.status[s] == 2) out.status[s] = 2;
+    }
+    IKR_CUDA(cudaMemcpyAsync(w.active.p, need.data(), sizeof(int) * n, cudaMemcpyHostToDevice, strm));
+    {
+      ProfScope ps(c, kKidCgVec, 1);
+      k_add_f32<<<egrid, 256, 0, strm>>>(Xv, w.X32.p, ld, L.d_k.p, c->d_nb.p, w.active.p);
+      IKR_CUDA(cudaGetLastError());
+    }
+    // A system whose tolerance is loose against its right-hand side is
+    // accepted on the FP32 recursive residual; the others are checked in FP64.
+    bool any = false;
+    for (int s = 0; s < n; ++s) {
+      check[s] = 0;
+      if (!need[s]) continue;
+      if (st.status[s] == 2) {
+        accepted[s] = 1;
+        continue;
+      }
+      if (tol[s] >= kTrust * bnorm[s] && st.status[s] == 1) {
+        accepted[s] = 1;
+        rnorm[s] = st.res[s];
+      } else {
+        check[s] = 1;
+        any = true;
+      }
+    }
+    if (!any) break;
+    // FP64 residual r = b - Q (H - eps) Q x
+    IKR_CUDA(cudaMemcpyAsync(w.active.p, check.data(), sizeof(int) * n, cudaMemcpyHostToDevice, strm));
+    const int* act = w.active.p;
+    double2* coef = reinterpret_cast<double2*>(w.coef.p);
+    proj_coef<double>(c, L, Xv, ld, act, coef);
+    proj_apply<double>(c, L, coef, Xv, 1.0, -1.0, Xv, ld, nullptr, nullptr, act);
+    IKR_CUDA(cudaMemcpyAsync(w.val.p, shift.data(), sizeof(double) * n, cudaMemcpyHostToDevice, strm));
+    launch_z_inverse<double>(c, L, Xv, ld, act, w.b1.p);
+    launch_plane<double>(c, L, w.b1.p, c->d_Vt.p, nullptr, act, w.b4.p);
+    launch_z_forward<double>(c, L, w.b4.p, w.W.p, ld, Xv, w.val.p, true, act);
+    proj_coef<double>(c, L, w.W.p, ld, act, coef);
+    proj_apply<double>(c, L, coef, w.W.p, 1.0, -1.0, w.W.p, ld, nullptr, nullptr, act);
+    {
+      ProfScope ps(c, kKidCgVec, 1);
+      k_residual<<<egrid, 256, 0, strm>>>(Bv, w.W.p, ld, L.d_k.p, c->d_nb.p, act, w.R.p, w.B32.p);
+      IKR_CUDA(cudaGetLastError());
+    }
+    for (int s = 0; s < n; ++s)
+      if (check[s]) {
+        out.n_ham += 1;
+        out.n_ham_fp64 += 1;
+      }
+    sys_norms(w.R.p, act, check.data(), rnorm);
+    for (int s = 0; s < n; ++s)
+      if (check[s] && rnorm[s] <= tol[s]) accepted[s] = 1;
+  }
+  for (int s = 0; s < n; ++s) {
+    out.res[s] = rnorm[s];
+    out.max_iters = std::max(out.max_iters, out.iters[s]);
+    if (!accepted[s] && out.status[s] == 1) out.status[s] = 3;
+    if (out.status[s] == 3) out.noconv++;
+    if (out.status[s] == 2) out.numeric++;
+  }
+  return out;
+}
+
+}  // namespace ikr

@@ -1,0 +1,69 @@
+// Declarations of the kernel wrappers in fft.cu and ops.cu.
+#pragma once
+
+#include "context.hpp"
+
+namespace ikr {
+
+template <typename T> struct CgVecs {
+  C_t<T>* X;
+  C_t<T>* R;
+  C_t<T>* P;
+  C_t<T>* Z;
+  C_t<T>* W;
+  const C_t<T>* B;
+};
+
+// fft.cu
+template <typename R>
+void launch_z_inverse(ikr_ctx* c, const SysList& L, const C_t<R>* sphere, int ld, const int* active,
+                      C_t<R>* b1);
+template <typename R>
+void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, const double* pot_scale,
+                  const int* active, C_t<R>* b4);
+template <typename R>
+void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* out, int ld,
+                      const C_t<R>* psi, const double* shift, bool kinetic, const int* active);
+template <typename R>
+void launch_density(ikr_ctx* c, int nsys, const C_t<R>* b1phi, const C_t<R>* b1d,
+                    const double* coef_a, const double* coef_b, double* out, double scale);
+template <typename R>
+void to_plane_layout(ikr_ctx* c, const double* in, R* out, double scale, const double* dscale);
+void full_fft(ikr_ctx* c, double2* data, bool inverse);
+
+template <typename R> const R* kin_all_ptr(ikr_ctx* c);
+template <> inline const double* kin_all_ptr<double>(ikr_ctx* c) { return c->d_kin_all.p; }
+template <> inline const float* kin_all_ptr<float>(ikr_ctx* c) { return c->d_kin_all32.p; }
+
+// ops.cu
+int proj_chunks(ikr_ctx* c);
+int cg_chunks(ikr_ctx* c);
+template <typename R>
+void proj_coef(ikr_ctx* c, const SysList& L, const C_t<R>* Y, int ldy, const int* active, double2* coef);
+template <typename R>
+void proj_apply(ikr_ctx* c, const SysList& L, const double2* coef, const C_t<R>* in, R alpha, R beta,
+                C_t<R>* out, int ldy, const C_t<R>* dv, double* dpart, const int* active);
+void sys_reduce(ikr_ctx* c, const double* part, int nparts, int nsys, const int* active, double* out);
+template <typename R>
+void cg_xr(ikr_ctx* c, const SysList& L, int mode, CgVecs<R>& v, const double* sys, const int* active,
+           double* dpart);
+template <typename R>
+void cg_p(ikr_ctx* c, const SysList& L, int mode, CgVecs<R>& v, const double* sys, const int* active);
+void cg_scalars(ikr_ctx* c, int stage, double* sys, const double* val, int nsys, int maxit, int* active);
+void count_active(ikr_ctx* c, const int* active, int n, int* dout);
+void chi0_sys(ikr_ctx* c, const SysList& L, const double2* M, double* deps, double2* coefP);
+void occupation_response(ikr_ctx* c, const double* deps, double* coef_a, double* coef_b, double* deF);
+void apply_K(ikr_ctx* c, const double* v, double* Kv, double* d_norm);
+void apply_kerker(ikr_ctx* c, const double* v, double* Tv, double alpha);
+void norm2(ikr_ctx* c, const double* x, double* d_out3);
+void axpy(ikr_ctx* c, const double* x, const double* y, double sa, const double* da, double* out);
+void scale_by(ikr_ctx* c, const double* w, const double* dinv, double* out);
+void multidot(ikr_ctx* c, const double* V, int nv, const double* w, double* h, int accumulate);
+void sub_combination(ikr_ctx* c, const double* V, int nv, const double* h, double* w);
+void add_combination(ikr_ctx* c, const double* V, int nv, const double* y, const double* x0, double* x);
+void exchange_kernel(ikr_ctx* c);
+void grid_max(ikr_ctx* c, const double* v, size_t n, double* dout);
+void to_fp32(ikr_ctx* c, const double2* in, size_t n, float2* out);
+void to_fp64(ikr_ctx* c, const float2* in, size_t n, double2* out);
+
+}  // namespace ikr

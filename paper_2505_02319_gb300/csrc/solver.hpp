@@ -1,0 +1,53 @@
+// Internal interfaces of the solver layer (solver.cu, mixed.cu).
+#pragma once
+
+#include <functional>
+#include <vector>
+
+#include "ops.hpp"
+
+namespace ikr {
+
+struct CgStats {
+  std::vector<int> iters, status;   // status: 1 converged, 2 numeric, 3 iteration cap
+  std::vector<double> res;          // final recursive residual norms
+  long long n_ham = 0, n_ham_fp64 = 0;
+  int max_iters = 0, noconv = 0, numeric = 0;
+  bool fp32 = false;
+};
+
+struct RunStats {
+  long long n_ham = 0, n_ham_fp64 = 0;
+  int e_applies = 0, e_applies_fp32 = 0;
+  int cg_max_iters = 0, cg_noconv = 0, cg_numeric = 0;
+  double kv_norm = 0.0, sigma = 0.0;
+  void add(const CgStats& s) {
+    n_ham += s.n_ham;
+    n_ham_fp64 += s.fp32 ? s.n_ham_fp64 : s.n_ham;
+    cg_max_iters = std::max(cg_max_iters, s.max_iters);
+    cg_noconv += s.noconv;
+    cg_numeric += s.numeric;
+    if (s.fp32) e_applies_fp32++;
+  }
+};
+
+using TolFn = std::function<std::vector<double>(double)>;
+
+void ensure_workspace(ikr_ctx* c, int n);
+void ensure_pinned(ikr_ctx* c, int n);
+template <typename R>
+void hamiltonian(ikr_ctx* c, int k, const C_t<R>* psi, C_t<R>* hpsi, int ld, int nvec);
+template <typename R>
+CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, const std::vector<double>& shift,
+                 const std::vector<double>& kappa, const std::vector<double>& tol, int maxit);
+CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv, const std::vector<double>& shift,
+                    const std::vector<double>& kappa, const std::vector<double>& tol, int maxit);
+void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::vector<double>& tol,
+               int maxit, int precision, double* drho, RunStats& rs);
+void dielectric_core(ikr_ctx* c, const double* v, double* Ev, const TolFn& tol_fn, int maxit, int precision,
+                     RunStats& rs);
+std::vector<double> strategy_tolerances(ikr_ctx* c, const ikr_solve_opts& o, int i, double s, double rprev,
+                                        double kv_norm, double b_norm);
+void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o, ikr_report* rep);
+
+}  // namespace ikr

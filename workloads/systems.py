@@ -177,7 +177,7 @@ _SPECS = {
     "tiny_insulator": dict(seed=11, cell=(6.0, 6.0, 6.0), dims=(12, 12, 12), Ecut=3.0,
                            layout="random", natoms=2, min_sep=2.5, depth=3.0, width=1.0,
                            n_electrons=4, nbands=4),
-    "tiny_ortho_k": dict(seed=12, cell=(5.0, 6.0, 7.0), dims=(10, 12, 14), Ecut=3.0,
+    "tiny_ortho_k": dict(seed=12, cell=(5.0, 6.0, 7.0), dims=(10, 12, 16), Ecut=3.0,
                          layout="random", natoms=2, min_sep=2.5, depth=3.0, width=1.0,
                          n_electrons=4, nbands=4, kgrid=(2, 1, 1)),
     "tiny_metal": dict(seed=13, cell=(6.0, 6.0, 6.0), dims=(12, 12, 12), Ecut=3.0,
