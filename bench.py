@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Time-to-solve of the Dyson equation E drho = b to tau = 1e-8 on one GB300.
+
+Workload (the configuration the headline metric is quoted on): the
+diamond-like cell, a = 10.26 bohr, 8 Gaussian pseudo-atoms (4 Ha, 0.8 bohr,
+seeded 0.02 bohr displacements), Ecut = 15 Ha, 2x2x2 Monkhorst-Pack k-points,
+48^3 grid, 32 electrons with Fermi-Dirac smearing T = 0.01 Ha (251 Sternheimer
+systems per E application), perturbation a 0.1 Ha Gaussian bump,
+b = chi0 dV0 / ||chi0 dV0||.  One step = one call of ikr_solve_response
+(Algorithm 1, m = 20, bal tolerances) with the mixed-precision path; the FP64
+path is timed beside it.  All inputs are seeded and synthetic.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solve εδρ=b to 1e-8 (mixed vs FP64, 1 GB300); H-apply HBM GB/s"
+WORKLOAD = "cfg2"
+WORKLOAD_DESC = ("diamond-like cell a=10.26 bohr, 8 Gaussian pseudo-atoms, Ecut=15 Ha, 2x2x2 k, 48^3 grid, "
+                 "FD T=0.01 Ha (251 Sternheimer systems), GMRES m=20 bal tau=1e-8")
+TAU = 1e-8
+M = 20
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ clocks --
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ algorithmic work --
+def plane_pass_work(ctx_geom, fp_bytes):
+    """Algorithmic bytes and flops of one (system, z-plane-pass) unit of the
+    plane kernel: the 2D transforms of the pruned plane, see the design doc."""
+    import math
+    Nx, Ny, Nz, nc, nxa = ctx_geom
+    c = 2 * fp_bytes                               # complex element size
+    # bytes: read the z-transformed columns, write the result, read the potential plane
+    byts = 2.0 * Nz * nc * c + Nz * Ny * Nx * fp_bytes
+    fl = lambda n: 5.0 * n * math.log2(n)          # flops of one length-n complex FFT
+    flops = Nz * (2 * nxa * fl(Ny) + 2 * Ny * fl(Nx) + 2.0 * Ny * Nx)
+    return byts, flops
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path)), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------------- ours --
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local_rank)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2505_02319_gb300 import groundstate, ikr
+    from workloads import make_system, perturbation
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    s = make_system(WORKLOAD)
+    t0 = time.time()
+    ctx = groundstate.context_for(s)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    info = ctx.groundstate_info(ctx.nbands, s.n_grid)
+    nsys = int(info["nocc"].sum())
+    dV = torch.tensor(perturbation(s).ravel(), device="cuda")
+    b, _ = ctx.apply_chi0(dV, tol=np.full(nsys, 1e-12))
+    b = (b / torch.linalg.norm(b)).contiguous()
+    opts = ikr.default_opts(tau=TAU, m=M, strategy="bal", precision=ikr.MIXED)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def solve(o):
+        return ctx.solve_response(b, opts=o)
+
+    for _ in range(max(args.warmup, 3)):
+        x, rep = solve(opts)
+    # full per-class event profile of one solve (kernel time shares)
+    ctx.profile_start(timed=ikr.Context.KERNEL_CLASSES)
+    solve(opts)
+    shares = ctx.profile_read()
+    dominant = max(shares, key=lambda k: shares[k]["ms"])
+    # timed steps: the dominant class is timed live with CUDA events on the stream
+    clocks = Clocks(local_rank)
+    times = []
+    ctx.profile_start(timed=(dominant,))
+    clocks.start()
+    for _ in range(args.steps):
+        flush.fill_(1.0)                                  # L2 flush between timed steps
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, rep = solve(opts)
+        e1.record(stream)
+        barrier()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    launches = sum(v["launches"] for v in prof.values())
+    t_local = sum(times)
+    t_tensor = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
+    t_max = float(t_tensor.item())
+    rep = rep[0]
+    # FP64 path, same problem
+    fp64 = None
+    if not args.no_fp64:
+        o64 = ikr.default_opts(tau=TAU, m=M, strategy="bal", precision=ikr.FP64)
+        flush.fill_(1.0)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x64, rep64 = solve(o64)
+        e1.record(stream)
+        barrier()
+        fp64 = dict(time_s=e0.elapsed_time(e1) / 1e3, n_ham=rep64[0]["n_ham"], outer_iters=rep64[0]["outer_iters"])
+    # true residuals ||b - E x|| with tight FP64 E applications (not timed)
+    Ex, _ = ctx.apply_dielectric(x, tol=np.full(nsys, 1e-12))
+    true_res = float(torch.linalg.norm(b - Ex))
+    if fp64 is not None:
+        Ex64, _ = ctx.apply_dielectric(x64, tol=np.full(nsys, 1e-12))
+        fp64["true_residual"] = float(torch.linalg.norm(b - Ex64))
+        fp64["rel_diff_vs_mixed"] = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+    # end to end through the public API with host buffers
+    b_host = b.cpu().pin_memory()
+    x_host = torch.empty_like(b_host).pin_memory()
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bd = b_host.to("cuda", non_blocking=True)
+        xd, _ = ctx.solve_response(bd, opts=opts)
+        x_host.copy_(xd, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        e2e_times.append(e0.elapsed_time(e1) / 1e3)
+    # roofline of the dominant kernel class
+    g = ctx.fft_geometry()
+    geom = (s.dims[0], s.dims[1], s.dims[2], g["ncols"], g["nxa"])
+    peaks, src = measured_peaks()
+    d = prof[dominant]
+    avg_ms = d["ms"] / max(d["timed_calls"], 1)
+    roof = roofline(dominant, d, avg_ms, geom, rep, peaks, src, ctx)
+    value = t_max / args.steps
+    out = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * value, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + ": " + WORKLOAD_DESC, "precision": "mixed (FP32 CG, FP64 elsewhere)",
+                   "tau": TAU, "m": M, "strategy": "bal", "systems_per_E": nsys,
+                   "l2": "flushed (512 MiB write) between timed steps", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "clocks": clk,
+        "e2e": {"value": statistics.median(e2e_times), "unit": "s", "h2d_bytes_per_step": b_host.numel() * 8,
+                "d2h_bytes_per_step": x_host.numel() * 8},
+        "gpu_launches": int(launches / max(args.steps, 1)),
+        "roofline": roof,
+        "solve": {"outer_iters": rep["outer_iters"], "restarts": rep["restarts"], "e_applies": rep["e_applies"],
+                  "n_ham": rep["n_ham"], "n_ham_fp64": rep["n_ham_fp64"], "est_residual": rep["est_residual"],
+                  "true_residual": true_res, "step_times_s": times},
+        "fp64": fp64,
+        "speedup_vs_fp64": (fp64["time_s"] / value) if fp64 else None,
+        "kernel_ms_one_solve": {k: round(v["ms"], 3) for k, v in shares.items()},
+        "setup_s": setup_s,
+    }
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline(s, rep["e_applies"])
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def roofline(name, d, avg_ms, geom, rep, peaks, src, ctx):
+    """Achieved = algorithmic work per launch / average launch duration."""
+    units = d.get("units", 0)
+    calls = max(d["timed_calls"], 1)
+    if name == "plane" and units:
+        # mixed path: FP32 and FP64 plane launches; account each unit at its precision
+        u32, u64 = d.get("units_fp32", units), d.get("units_fp64", 0)
+        b32, f32 = plane_pass_work(geom, 4)
+        b64, f64 = plane_pass_work(geom, 8)
+        flops = (u32 * f32 + u64 * f64) / calls
+        byts = (u32 * b32 + u64 * b64) / calls
+        tfl = flops / (avg_ms * 1e-3) / 1e12
+        # FP32 peak derived from unit counts and clocks: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": tfl, "peak": peak, "unit": "TFLOP/s",
+                "frac": tfl / peak, "traffic": None, "peak_source": "derived (FP32 lanes x clock)",
+                "hbm_gbs": byts / (avg_ms * 1e-3) / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
+                "hbm_frac": byts / (avg_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                "algorithmic_bytes_per_launch": byts, "algorithmic_flops_per_launch": flops,
+                "avg_launch_ms": avg_ms, "units_per_launch": units / calls}
+    return {"kernel": name, "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": None, "traffic": None, "avg_launch_ms": avg_ms}
+
+
+# ------------------------------------------------------------ CPU baseline --
+def cpu_baseline(system, e_applies):
+    """The oracle, as it stands, on a bounded sample of the workload: its exact
+    chi0 (pseudo-inverse Sternheimer solutions from dense diagonalisation) for
+    the first k-point, scaled to a full E application (x number of k-points,
+    plus one K^Hxc application) and to a solve (x the E applications the GPU
+    solve used).  Dense diagonalisation (setup) is not timed."""
+    import numpy as np
+    from oracle import groundstate as ogs, response as oresp
+    from workloads import perturbation
+    cores = len(os.sched_getaffinity(0))
+    k0 = system.kpoints[:1]
+    sub = type(system)(**{**system.__dict__, "kpoints": k0, "kweights": np.ones(1)})
+    gs = ogs.solve(sub)
+    dV = perturbation(system)
+    t0 = time.time()
+    oresp.chi0(gs, dV)
+    t_k = time.time() - t0
+    t0 = time.time()
+    oresp.apply_K(dV, gs)
+    t_K = time.time() - t0
+    t_E = len(system.kpoints) * t_k + t_K
+    return {"value": t_E * e_applies, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle chi0 of k-point 1 of {len(system.kpoints)} ({t_k:.2f} s) + one K apply "
+                      f"({t_K:.3f} s), scaled x{len(system.kpoints)} k-points and x{e_applies} E applications "
+                      f"of one solve"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from workloads import make_system
+    s = make_system(WORKLOAD)
+    e_applies = 20   # E applications of one solve at tau = 1e-8 (GPU solve: 19 + restart residual)
+    vals = []
+    cb = None
+    for _ in range(max(args.steps, 1)):
+        cb = cpu_baseline(s, e_applies)
+        vals.append(cb["value"])
+    v = statistics.median(vals)
+    cb["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD + ": " + WORKLOAD_DESC, "parallelism": "CPU oracle"},
+           "cpu_baseline": cb, "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus and "RANK" in os.environ else 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

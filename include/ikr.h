@@ -230,9 +230,14 @@ typedef struct {
   long long launches;          /* kernel launches since ikr_profile_start */
   long long timed_calls;       /* wrapper calls bracketed by events */
   double ms;                   /* summed event time of those calls */
+  long long units_fp32;        /* systems processed by FP32 launches of the class */
+  long long units_fp64;        /* systems processed by FP64 launches of the class */
 } ikr_kernel_stat;
 ikr_status ikr_profile_start(ikr_ctx* ctx, unsigned mask);
 int ikr_profile_read(ikr_ctx* ctx, ikr_kernel_stat* out, int cap);
+/* The pruned transform geometry (host output, 5 ints): N1, N2, N3, the number
+ * of sphere columns (j1, j2) transformed along z, and of active x positions. */
+ikr_status ikr_fft_geometry(const ikr_ctx* ctx, int* out);
 
 /* Frees the context and all device memory it owns.  NULL is allowed. */
 void ikr_destroy(ikr_ctx* ctx);

@@ -310,6 +310,8 @@ ikr_status ikr_profile_start(ikr_ctx* c, unsigned mask) {
   if (!c) return IKR_ERR_ARG;
   for (int i = 0; i < kNumKid; ++i) {
     c->prof.launches[i] = 0;
+    c->prof.units32[i] = 0;
+    c->prof.units64[i] = 0;
     c->prof.used[i] = 0;
   }
   c->prof.mask = mask;
@@ -333,8 +335,20 @@ int ikr_profile_read(ikr_ctx* c, ikr_kernel_stat* out, int cap) {
     }
     out[i].timed_calls = (long long)pairs;
     out[i].ms = ms;
+    out[i].units_fp32 = c->prof.units32[i];
+    out[i].units_fp64 = c->prof.units64[i];
   }
   return (int)kNumKid;
+}
+
+ikr_status ikr_fft_geometry(const ikr_ctx* c, int* out) {
+  if (!c || !out) return IKR_ERR_ARG;
+  out[0] = c->N[0];
+  out[1] = c->N[1];
+  out[2] = c->N[2];
+  out[3] = c->nc;
+  out[4] = c->nxa;
+  return IKR_OK;
 }
 
 }  // extern "C"

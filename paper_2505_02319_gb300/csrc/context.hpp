@@ -135,6 +135,8 @@ enum KernelClass {
 struct Profiler {
   unsigned mask = 0;                    // bit i: time class i with CUDA events
   long long launches[kNumKid] = {};
+  long long units32[kNumKid] = {};      // work units (systems) launched in FP32
+  long long units64[kNumKid] = {};      // ... and in FP64
   std::vector<cudaEvent_t> ev[kNumKid];
   size_t used[kNumKid] = {};
 };
@@ -191,6 +193,7 @@ struct ikr_ctx {
   double* h_pinned_d = nullptr;
   size_t pinned_bytes = 0;
   ikr::Profiler prof;
+  int active_hint = 0;          // systems active in the next masked launch (for accounting)
   ~ikr_ctx() {
     if (h_pinned) cudaFreeHost(h_pinned);
     for (auto& v : prof.ev)
@@ -208,8 +211,10 @@ struct ProfScope {
   ikr_ctx* c;
   int id;
   bool timed;
-  ProfScope(ikr_ctx* c_, int id_, int nlaunch) : c(c_), id(id_) {
+  ProfScope(ikr_ctx* c_, int id_, int nlaunch, long long units = 0, int fp_bytes = 8) : c(c_), id(id_) {
     c->prof.launches[id] += nlaunch;
+    if (fp_bytes == 4) c->prof.units32[id] += units;
+    else c->prof.units64[id] += units;
     timed = (c->prof.mask >> id) & 1u;
     if (timed) record();
   }

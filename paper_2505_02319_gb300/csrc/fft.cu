@@ -352,7 +352,7 @@ template <typename R>
 void launch_z_inverse(ikr_ctx* c, const SysList& L, const C_t<R>* sphere, int ld, const int* active,
                       C_t<R>* b1) {
   if (L.n == 0) return;
-  ProfScope ps(c, kKidZInv, 1);
+  ProfScope ps(c, kKidZInv, 1, active ? c->active_hint : L.n, (int)sizeof(R));
   const int Nz = c->N[2];
   const int LZ = lines_per_cta(Nz);
   const size_t smem = sizeof(C_t<R>) * (Nz + 2 * LZ * (Nz + 1));
@@ -367,7 +367,7 @@ template <typename R>
 void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, const double* pot_scale,
                   const int* active, C_t<R>* b4) {
   if (L.n == 0) return;
-  ProfScope ps(c, kKidPlane, 1);
+  ProfScope ps(c, kKidPlane, 1, active ? c->active_hint : L.n, (int)sizeof(R));
   const int Nx = c->N[0], Ny = c->N[1], Nz = c->N[2];
   const size_t smem = sizeof(C_t<R>) * (Nx + Ny + 2 * (size_t)Ny * (Nx + 1)) + sizeof(int) * c->nxa;
   set_smem(k_plane<R>, smem);
@@ -382,7 +382,7 @@ template <typename R>
 void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* out, int ld,
                       const C_t<R>* psi, const double* shift, bool kinetic, const int* active) {
   if (L.n == 0) return;
-  ProfScope ps(c, kKidZFwd, 1);
+  ProfScope ps(c, kKidZFwd, 1, active ? c->active_hint : L.n, (int)sizeof(R));
   const int Nz = c->N[2];
   const int LZ = lines_per_cta(Nz);
   const size_t smem = sizeof(C_t<R>) * (Nz + 2 * LZ * (Nz + 1));
@@ -407,7 +407,7 @@ void launch_density(ikr_ctx* c, int nsys, const C_t<R>* b1phi, const C_t<R>* b1d
   const int Nx = c->N[0], Ny = c->N[1], Nz = c->N[2];
   IKR_REQUIRE(Nx * Ny <= kDensThreads * kDensMaxPerThread, IKR_ERR_ARG,
               "grid plane too large for the density kernel");
-  ProfScope ps(c, kKidDensity, 2);
+  ProfScope ps(c, kKidDensity, 2, nsys, (int)sizeof(R));
   const int G = density_groups(c, nsys);
   c->ws.dens_part.reserve((size_t)G * c->Ng);
   const size_t np = (size_t)Ny * (Nx + 1);

@@ -153,6 +153,8 @@ CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv
       }
     }
     if (!any) break;
+    c->active_hint = 0;
+    for (int s = 0; s < n; ++s) c->active_hint += check[s];
     // FP64 residual r = b - Q (H - eps) Q x
     IKR_CUDA(cudaMemcpyAsync(w.active.p, check.data(), sizeof(int) * n, cudaMemcpyHostToDevice, strm));
     const int* act = w.active.p;

@@ -140,6 +140,7 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
   sys_reduce(c, w.dpart.p, pch, n, act, w.val.p);
   cg_scalars(c, 0, sys, w.val.p, n, maxit, act);
   cg_p<R>(c, L, 0, v, sys, act);
+  c->active_hint = n;
   for (int it = 1; it <= maxit; ++it) {
     // W = Q (H - eps) P
     launch_z_inverse<R>(c, L, v.P, c->ld, act, Bufs<R>::b1(c));
@@ -163,6 +164,7 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
     count_active(c, act, n, dcount);
     IKR_CUDA(cudaMemcpyAsync(c->h_pinned, dcount, sizeof(int), cudaMemcpyDeviceToHost, strm));
     IKR_CUDA(cudaStreamSynchronize(strm));
+    c->active_hint = c->h_pinned[0];
     if (c->h_pinned[0] == 0) break;
   }
   IKR_CUDA(cudaMemcpyAsync(hs.data(), sys, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, strm));

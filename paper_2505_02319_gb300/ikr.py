@@ -66,7 +66,7 @@ class SolveOpts(ct.Structure):
 
 class KernelStat(ct.Structure):
     _fields_ = [("name", ct.c_char_p), ("launches", ct.c_longlong), ("timed_calls", ct.c_longlong),
-                ("ms", ct.c_double)]
+                ("ms", ct.c_double), ("units_fp32", ct.c_longlong), ("units_fp64", ct.c_longlong)]
 
 
 def _load():
@@ -94,6 +94,7 @@ def _load():
         "ikr_version": (ct.c_char_p, []),
         "ikr_profile_start": (I, [P, ct.c_uint]),
         "ikr_profile_read": (I, [P, ct.POINTER(KernelStat), I]),
+        "ikr_fft_geometry": (I, [P, ct.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -212,7 +213,14 @@ class Context:
         arr = (KernelStat * 16)()
         n = _LIB.ikr_profile_read(self._h, arr, 16)
         return {arr[i].name.decode(): dict(launches=arr[i].launches, timed_calls=arr[i].timed_calls,
-                                           ms=arr[i].ms) for i in range(n)}
+                                           ms=arr[i].ms, units_fp32=arr[i].units_fp32,
+                                           units_fp64=arr[i].units_fp64,
+                                           units=arr[i].units_fp32 + arr[i].units_fp64) for i in range(n)}
+
+    def fft_geometry(self):
+        g = (ct.c_int * 5)()
+        self._check(_LIB.ikr_fft_geometry(self._h, g))
+        return dict(dims=(g[0], g[1], g[2]), ncols=g[3], nxa=g[4])
 
     # -- queries -------------------------------------------------------------
     @property
