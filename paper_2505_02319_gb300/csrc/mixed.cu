@@ -16,7 +16,7 @@ namespace ikr {
 namespace {
 
 constexpr double kRel = 2e-5;     // relative residual an FP32 CG solve is asked for
-constexpr double kTrust = 1e-3;   // tol >= kTrust ||b||: the FP32 recursive residual is trusted
+constexpr double kTrust = 1e-2;   // tol >= kTrust ||b||: the FP32 recursive residual is trusted
 constexpr int kMaxRefine = 8;
 
 // partial sums of |v|^2 per system (chunks of 256)
