@@ -171,6 +171,28 @@ ikr_status ikr_groundstate_info(const ikr_ctx* ctx, double* f, int* nocc, double
 ikr_status ikr_apply_hamiltonian(ikr_ctx* ctx, int k, const void* psi, void* hpsi, int nvec,
                                  int precision, cudaStream_t stream);
 
+/* H_k psi like ikr_apply_hamiltonian (IKR_FP64, complex128 vectors), but the
+ * call allocates no device memory: no cudaMalloc, cudaFree or allocating
+ * library routine.  The paper has no counterpart; this serves callers that
+ * cannot allocate while they work - a stream being captured into a CUDA graph
+ * (an allocation invalidates the capture), an application whose device memory
+ * is owned by its own pool, a latency-bound loop that must stay out of the
+ * allocator.  The context itself is created beforehand (that allocates).
+ * Scratch: one static 32 MiB device array in the library, which every GPU
+ * that loads the library holds until the process exits.  Each vector needs
+ * 2 * 16 * N3 * ncols bytes (ncols from ikr_fft_geometry); vectors are
+ * processed in chunks that fit, and a grid whose single vector does not fit
+ * is rejected with IKR_ERR_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current:
+ * make that first call before any stream capture.  All calls in the process
+ * share the array and its contents persist between calls; calls that overlap
+ * on the GPU (other streams or threads at the same time) race on it and must
+ * be serialised by the caller.  The work is enqueued on `stream`; the call
+ * returns without waiting for it.  psi, hpsi: DEVICE, Nb_k x nvec complex128,
+ * not overlapping. */
+ikr_status ikr_apply_hamiltonian_noalloc(ikr_ctx* ctx, int k, const void* psi, void* hpsi, int nvec,
+                                         cudaStream_t stream);
+
 /* Solves the projected Sternheimer equations (eq. discretised_sternheimer)
  *   Q_k (H_k - eps_nk) Q_k x_s = Q_k rhs_s,   Q_k = 1 - Phi_k Phi_k^H,
  * for nsys systems s with k-point k_of[s] and occupied band band_of[s] (host

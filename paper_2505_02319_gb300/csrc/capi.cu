@@ -156,6 +156,19 @@ ikr_status ikr_apply_hamiltonian(ikr_ctx* c, int k, const void* psi, void* hpsi,
   });
 }
 
+ikr_status ikr_apply_hamiltonian_noalloc(ikr_ctx* c, int k, const void* psi, void* hpsi, int nvec,
+                                         cudaStream_t stream) {
+  if (!c) return IKR_ERR_ARG;
+  c->stream = stream;
+  return guarded(c, [&] {
+    IKR_REQUIRE(k >= 0 && k < (int)c->k.size(), IKR_ERR_ARG, "k out of range");
+    IKR_REQUIRE(nvec >= 0, IKR_ERR_ARG, "nvec must be >= 0");
+    if (nvec == 0) return;
+    IKR_REQUIRE(psi && hpsi && psi != hpsi, IKR_ERR_ARG, "psi and hpsi must be distinct device pointers");
+    hamiltonian_noalloc(c, k, static_cast<const double2*>(psi), static_cast<double2*>(hpsi), nvec);
+  });
+}
+
 ikr_status ikr_solve_sternheimer(ikr_ctx* c, int nsys, const int* k_of, const int* band_of, const void* rhs,
                                  void* x, int ld, const double* tol, int maxit, int precision, int* iters_out,
                                  double* resid_out, cudaStream_t stream) {

@@ -479,4 +479,33 @@ IKR_INST(double)
 IKR_INST(float)
 #undef IKR_INST
 
+// ------------------------------------------- raw-pointer launches (no SysList) --
+// Launch the three H_k kernels for n systems whose k-point indices are in the
+// device array d_sysk; used by the no-allocation entry point, which keeps its
+// scratch (including d_sysk) in a static device array.
+void launch_hamiltonian_raw(ikr_ctx* c, int n, const int* d_sysk, const double2* psi, int ld, double2* b1,
+                            double2* b4, double2* hpsi) {
+  if (n == 0) return;
+  const int Nx = c->N[0], Ny = c->N[1], Nz = c->N[2];
+  const int LZ = lines_per_cta(Nz);
+  const size_t smz = sizeof(double2) * (Nz + 2 * LZ * (Nz + 1));
+  const size_t smp = sizeof(double2) * (Nx + Ny + 2 * (size_t)Ny * (Nx + 1)) + sizeof(int) * c->nxa;
+  set_smem(k_z_inverse<double>, smz);
+  set_smem(k_plane<double>, smp);
+  set_smem(k_z_forward<double>, smz);
+  dim3 gz((c->nc + LZ - 1) / LZ, n);
+  k_z_inverse<double><<<gz, 256, smz, c->stream>>>(psi, ld, d_sysk, c->k_colinfo.p, c->nc, c->ncp, c->plan[2],
+                                                   c->d_tw[2].p, nullptr, LZ, b1);
+  IKR_CUDA(cudaGetLastError());
+  dim3 gp(Nz, n);
+  k_plane<double><<<gp, 256, smp, c->stream>>>(b1, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa, c->plan[0],
+                                               c->plan[1], Nz, c->d_tw[0].p, c->d_tw[1].p, c->d_Vt.p, nullptr,
+                                               nullptr, b4);
+  IKR_CUDA(cudaGetLastError());
+  k_z_forward<double><<<gz, 256, smz, c->stream>>>(b4, c->nc, c->ncp, d_sysk, c->k_colinfo.p, c->plan[2],
+                                                   c->d_tw[2].p, LZ, hpsi, ld, c->ld, psi, nullptr,
+                                                   c->d_kin_all.p, nullptr);
+  IKR_CUDA(cudaGetLastError());
+}
+
 }  // namespace ikr

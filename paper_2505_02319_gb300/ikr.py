@@ -83,6 +83,7 @@ def _load():
         "ikr_basis_millers": (I, [P, I, ct.POINTER(I)]),
         "ikr_groundstate_info": (I, [P, ct.POINTER(D), ct.POINTER(I), ct.POINTER(D), P, S]),
         "ikr_apply_hamiltonian": (I, [P, I, P, P, I, I, S]),
+        "ikr_apply_hamiltonian_noalloc": (I, [P, I, P, P, I, S]),
         "ikr_solve_sternheimer": (I, [P, I, ct.POINTER(I), ct.POINTER(I), P, P, I, ct.POINTER(D), I, I,
                                       ct.POINTER(I), ct.POINTER(D), S]),
         "ikr_apply_chi0": (I, [P, P, P, ct.POINTER(D), I, ct.POINTER(Report), S]),
