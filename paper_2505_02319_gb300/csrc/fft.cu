@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(256) k_plane(const C_t<R>* __restrict__ b1, in
                                                const R* __restrict__ pot,
                                                const double* __restrict__ pot_scale,
                                                const int* __restrict__ active,
-                                               C_t<R>* __restrict__ b4) {
+                                               C_t<R>* __restrict__ b4,
+                                               const C_t<R>* __restrict__ real_in) {
   using C = C_t<R>;
   const int s = blockIdx.y, iz = blockIdx.x;
   if (active && !active[s]) return;
@@ -154,16 +155,30 @@ __global__ void __launch_bounds__(256) k_plane(const C_t<R>* __restrict__ b1, in
   for (int i = threadIdx.x; i < Nx; i += blockDim.x) tx[i] = twx[i];
   for (int i = threadIdx.x; i < Ny; i += blockDim.x) ty[i] = twy[i];
   for (int i = threadIdx.x; i < nxa; i += blockDim.x) xp[i] = xpos[i];
-  for (int i = threadIdx.x; i < 2 * Ny * ldp; i += blockDim.x) A[i] = mk<C>(0, 0);
-  __syncthreads();
-  const C* src = b1 + ((size_t)s * Nz + iz) * ncp;
-  for (int col = threadIdx.x; col < nc; col += blockDim.x)
-    A[col_xy[2 * col + 1] * ldp + col_xy[2 * col]] = src[col];
-  __syncthreads();
-  C* P = fft_lines<C, true>(A, B, py, nxa, 0, xp, ldp, ty);          // y-lines, active x
-  C* Q = (P == A) ? B : A;
-  P = fft_lines<C, true>(P, Q, px, Ny, ldp, nullptr, 1, tx);         // x-lines, all rows
-  Q = (P == A) ? B : A;
+  C* P;
+  C* Q;
+  if (real_in) {
+    // the synthesis sum_G c_G e^{iG.r} of this plane is given
+    const C* rp = real_in + ((size_t)s * Nz + iz) * Ny * Nx;
+    for (int e = threadIdx.x; e < Ny * Nx; e += blockDim.x) {
+      const int iy = e / Nx, ix = e - iy * Nx;
+      A[iy * ldp + ix] = rp[e];
+    }
+    __syncthreads();
+    P = A;
+    Q = B;
+  } else {
+    for (int i = threadIdx.x; i < 2 * Ny * ldp; i += blockDim.x) A[i] = mk<C>(0, 0);
+    __syncthreads();
+    const C* src = b1 + ((size_t)s * Nz + iz) * ncp;
+    for (int col = threadIdx.x; col < nc; col += blockDim.x)
+      A[col_xy[2 * col + 1] * ldp + col_xy[2 * col]] = src[col];
+    __syncthreads();
+    P = fft_lines<C, true>(A, B, py, nxa, 0, xp, ldp, ty);          // y-lines, active x
+    Q = (P == A) ? B : A;
+    P = fft_lines<C, true>(P, Q, px, Ny, ldp, nullptr, 1, tx);     // x-lines, all rows
+    Q = (P == A) ? B : A;
+  }
   const R sc = pot_scale ? (R)(*pot_scale) : R(1);
   const R* pp = pot + (size_t)iz * Ny * Nx;
   for (int e = threadIdx.x; e < Ny * Nx; e += blockDim.x) {
@@ -192,7 +207,7 @@ __global__ void __launch_bounds__(kDensThreads) k_density(
     const int* __restrict__ col_xy, const int* __restrict__ xpos, int nxa, FftPlan px, FftPlan py,
     int Nz, const C_t<R>* __restrict__ twx, const C_t<R>* __restrict__ twy,
     const double* __restrict__ coef_a, const double* __restrict__ coef_b, int nsys, int ngroups,
-    double* __restrict__ part) {
+    double* __restrict__ part, const C_t<R>* __restrict__ psi_real) {
   using C = C_t<R>;
   const int iz = blockIdx.x, g = blockIdx.y;
   extern __shared__ unsigned char smem_raw[];
@@ -210,15 +225,26 @@ __global__ void __launch_bounds__(kDensThreads) k_density(
   const int s0 = (int)((long long)g * nsys / ngroups), s1 = (int)((long long)(g + 1) * nsys / ngroups);
   for (int s = s0; s < s1; ++s) {
     // psi plane in buf[0]/buf[1]
-    for (int i = threadIdx.x; i < 2 * np; i += blockDim.x) buf[0][i] = mk<C>(0, 0);
-    __syncthreads();
-    const C* src = b1phi + ((size_t)s * Nz + iz) * ncp;
-    for (int col = threadIdx.x; col < nc; col += blockDim.x)
-      buf[0][col_xy[2 * col + 1] * ldp + col_xy[2 * col]] = src[col];
-    __syncthreads();
-    C* P = fft_lines<C, true>(buf[0], buf[1], py, nxa, 0, xp, ldp, ty);
-    C* Q = (P == buf[0]) ? buf[1] : buf[0];
-    C* psi = fft_lines<C, true>(P, Q, px, Ny, ldp, nullptr, 1, tx);
+    C* psi;
+    if (psi_real) {
+      const C* rp = psi_real + ((size_t)s * Nz + iz) * Ny * Nx;
+      for (int e = threadIdx.x; e < Ny * Nx; e += blockDim.x) {
+        const int iy = e / Nx, ix = e - iy * Nx;
+        buf[0][iy * ldp + ix] = rp[e];
+      }
+      __syncthreads();
+      psi = buf[0];
+    } else {
+      for (int i = threadIdx.x; i < 2 * np; i += blockDim.x) buf[0][i] = mk<C>(0, 0);
+      __syncthreads();
+      const C* src = b1phi + ((size_t)s * Nz + iz) * ncp;
+      for (int col = threadIdx.x; col < nc; col += blockDim.x)
+        buf[0][col_xy[2 * col + 1] * ldp + col_xy[2 * col]] = src[col];
+      __syncthreads();
+      C* P = fft_lines<C, true>(buf[0], buf[1], py, nxa, 0, xp, ldp, ty);
+      C* Q = (P == buf[0]) ? buf[1] : buf[0];
+      psi = fft_lines<C, true>(P, Q, px, Ny, ldp, nullptr, 1, tx);
+    }
     C* D = nullptr;
     if (b1d) {
       C* f0 = buf[2];
@@ -258,6 +284,43 @@ __global__ void __launch_bounds__(kDensThreads) k_density(
   for (int i = 0; i < kDensMaxPerThread; ++i) {
     const int e = threadIdx.x + i * kDensThreads;
     if (e < Ny * Nx) dst[e] = acc[i];
+  }
+}
+
+// Unnormalised syntheses sum_G c_G e^{iG.r} of the z-transformed vectors b1,
+// written plane by plane: out[s][iz][iy][ix].
+template <typename R>
+__global__ void __launch_bounds__(256) k_synth_planes(const C_t<R>* __restrict__ b1, int nc, int ncp,
+                                                      const int* __restrict__ col_xy,
+                                                      const int* __restrict__ xpos, int nxa, FftPlan px,
+                                                      FftPlan py, int Nz, const C_t<R>* __restrict__ twx,
+                                                      const C_t<R>* __restrict__ twy,
+                                                      C_t<R>* __restrict__ out) {
+  using C = C_t<R>;
+  const int s = blockIdx.y, iz = blockIdx.x;
+  extern __shared__ unsigned char smem_raw[];
+  const int Nx = px.n, Ny = py.n, ldp = Nx + 1;
+  C* tx = reinterpret_cast<C*>(smem_raw);
+  C* ty = tx + Nx;
+  C* A = ty + Ny;
+  C* B = A + Ny * ldp;
+  int* xp = reinterpret_cast<int*>(B + Ny * ldp);
+  for (int i = threadIdx.x; i < Nx; i += blockDim.x) tx[i] = twx[i];
+  for (int i = threadIdx.x; i < Ny; i += blockDim.x) ty[i] = twy[i];
+  for (int i = threadIdx.x; i < nxa; i += blockDim.x) xp[i] = xpos[i];
+  for (int i = threadIdx.x; i < 2 * Ny * ldp; i += blockDim.x) A[i] = mk<C>(0, 0);
+  __syncthreads();
+  const C* src = b1 + ((size_t)s * Nz + iz) * ncp;
+  for (int col = threadIdx.x; col < nc; col += blockDim.x)
+    A[col_xy[2 * col + 1] * ldp + col_xy[2 * col]] = src[col];
+  __syncthreads();
+  C* P = fft_lines<C, true>(A, B, py, nxa, 0, xp, ldp, ty);
+  C* Q = (P == A) ? B : A;
+  P = fft_lines<C, true>(P, Q, px, Ny, ldp, nullptr, 1, tx);
+  C* dst = out + ((size_t)s * Nz + iz) * Ny * Nx;
+  for (int e = threadIdx.x; e < Ny * Nx; e += blockDim.x) {
+    const int iy = e / Nx, ix = e - iy * Nx;
+    dst[e] = P[iy * ldp + ix];
   }
 }
 
@@ -365,7 +428,7 @@ void launch_z_inverse(ikr_ctx* c, const SysList& L, const C_t<R>* sphere, int ld
 
 template <typename R>
 void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, const double* pot_scale,
-                  const int* active, C_t<R>* b4) {
+                  const int* active, C_t<R>* b4, const C_t<R>* real_in) {
   if (L.n == 0) return;
   ProfScope ps(c, kKidPlane, 1, active ? c->active_hint : L.n, (int)sizeof(R));
   const int Nx = c->N[0], Ny = c->N[1], Nz = c->N[2];
@@ -374,7 +437,7 @@ void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, 
   dim3 grid(Nz, L.n);
   k_plane<R><<<grid, 256, smem, c->stream>>>(b1, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa,
                                               c->plan[0], c->plan[1], Nz, tw_ptr<R>(c, 0),
-                                              tw_ptr<R>(c, 1), pot, pot_scale, active, b4);
+                                              tw_ptr<R>(c, 1), pot, pot_scale, active, b4, real_in);
   IKR_CUDA(cudaGetLastError());
 }
 
@@ -403,7 +466,8 @@ int density_groups(ikr_ctx* c, int nsys) {
 
 template <typename R>
 void launch_density(ikr_ctx* c, int nsys, const C_t<R>* b1phi, const C_t<R>* b1d,
-                    const double* coef_a, const double* coef_b, double* out, double scale) {
+                    const double* coef_a, const double* coef_b, double* out, double scale,
+                    const C_t<R>* psi_real) {
   const int Nx = c->N[0], Ny = c->N[1], Nz = c->N[2];
   IKR_REQUIRE(Nx * Ny <= kDensThreads * kDensMaxPerThread, IKR_ERR_ARG,
               "grid plane too large for the density kernel");
@@ -417,13 +481,27 @@ void launch_density(ikr_ctx* c, int nsys, const C_t<R>* b1phi, const C_t<R>* b1d
     dim3 grid(Nz, G);
     k_density<R><<<grid, kDensThreads, smem, c->stream>>>(
         b1phi, b1d, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa, c->plan[0], c->plan[1], Nz,
-        tw_ptr<R>(c, 0), tw_ptr<R>(c, 1), coef_a, coef_b, nsys, G, c->ws.dens_part.p);
+        tw_ptr<R>(c, 0), tw_ptr<R>(c, 1), coef_a, coef_b, nsys, G, c->ws.dens_part.p, psi_real);
     IKR_CUDA(cudaGetLastError());
   } else {
     IKR_CUDA(cudaMemsetAsync(c->ws.dens_part.p, 0, sizeof(double) * G * c->Ng, c->stream));
   }
   dim3 tgrid((Nx + 31) / 32, (Nz + 31) / 32, Ny);
   k_planes_to_c<<<tgrid, dim3(32, 8), 0, c->stream>>>(c->ws.dens_part.p, G, Nx, Ny, Nz, scale, out);
+  IKR_CUDA(cudaGetLastError());
+}
+
+template <typename R>
+void launch_synth_planes(ikr_ctx* c, int nsys, const C_t<R>* b1, C_t<R>* out) {
+  if (nsys == 0) return;
+  ProfScope ps(c, kKidPlane, 1, nsys, (int)sizeof(R));
+  const int Nx = c->N[0], Ny = c->N[1], Nz = c->N[2];
+  const size_t smem = sizeof(C_t<R>) * (Nx + Ny + 2 * (size_t)Ny * (Nx + 1)) + sizeof(int) * c->nxa;
+  set_smem(k_synth_planes<R>, smem);
+  dim3 grid(Nz, nsys);
+  k_synth_planes<R><<<grid, 256, smem, c->stream>>>(b1, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa,
+                                                     c->plan[0], c->plan[1], Nz, tw_ptr<R>(c, 0),
+                                                     tw_ptr<R>(c, 1), out);
   IKR_CUDA(cudaGetLastError());
 }
 
@@ -469,11 +547,12 @@ void full_fft(ikr_ctx* c, double2* data, bool inverse) {
   template void launch_z_inverse<R>(ikr_ctx*, const SysList&, const C_t<R>*, int, const int*,     \
                                     C_t<R>*);                                                       \
   template void launch_plane<R>(ikr_ctx*, const SysList&, const C_t<R>*, const R*, const double*,  \
-                                const int*, C_t<R>*);                                               \
+                                const int*, C_t<R>*, const C_t<R>*);                                \
+  template void launch_synth_planes<R>(ikr_ctx*, int, const C_t<R>*, C_t<R>*);                      \
   template void launch_z_forward<R>(ikr_ctx*, const SysList&, const C_t<R>*, C_t<R>*, int,         \
                                     const C_t<R>*, const double*, bool, const int*);                \
   template void launch_density<R>(ikr_ctx*, int, const C_t<R>*, const C_t<R>*,                     \
-                                  const double*, const double*, double*, double);                   \
+                                  const double*, const double*, double*, double, const C_t<R>*);    \
   template void to_plane_layout<R>(ikr_ctx*, const double*, R*, double, const double*);
 IKR_INST(double)
 IKR_INST(float)
@@ -500,7 +579,7 @@ void launch_hamiltonian_raw(ikr_ctx* c, int n, const int* d_sysk, const double2*
   dim3 gp(Nz, n);
   k_plane<double><<<gp, 256, smp, c->stream>>>(b1, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa, c->plan[0],
                                                c->plan[1], Nz, c->d_tw[0].p, c->d_tw[1].p, c->d_Vt.p, nullptr,
-                                               nullptr, b4);
+                                               nullptr, b4, nullptr);
   IKR_CUDA(cudaGetLastError());
   k_z_forward<double><<<gz, 256, smz, c->stream>>>(b4, c->nc, c->ncp, d_sysk, c->k_colinfo.p, c->plan[2],
                                                    c->d_tw[2].p, LZ, hpsi, ld, c->ld, psi, nullptr,

@@ -238,22 +238,28 @@ __global__ void __launch_bounds__(kEC) k_cg_p(int mode, C_t<R>* __restrict__ Pv,
   }
 }
 
-// Scalar steps of the CG recurrences, one thread per system.
+// Scalar steps of the CG recurrences, one thread per system.  Each thread first
+// sums its system's nparts partial dot products in fixed order.
 //   stage 0 (init):  rz = <r, z>;  iters = 0;  status = 0
-//   stage 1 (alpha): alpha = rz / <p, Ap>   (non-positive or non-finite -> numeric stop)
-//   stage 2 (check): iters += 1; stop when ||r||^2 <= tol^2 or iters >= maxit
+//   stage 1 (alpha): alpha = rz / <p, Ap>   (non-positive or non-finite -> numeric stop);
+//                    resets the active counter
+//   stage 2 (check): iters += 1; stop when ||r||^2 <= tol^2 or iters >= maxit;
+//                    counts the systems that stay active
 //   stage 3 (beta):  beta = rz_new / rz; rz = rz_new
-__global__ void k_cg_scalars(int stage, double* __restrict__ sys, const double* __restrict__ val,
-                             int nsys, int maxit, int* __restrict__ active) {
+__global__ void k_cg_scalars(int stage, double* __restrict__ sys, const double* __restrict__ part, int nparts,
+                             int nsys, int maxit, int* __restrict__ active, int* __restrict__ counter) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (stage == 1 && s == 0 && counter) *counter = 0;
   if (s >= nsys || !active[s]) return;
+  double val = 0.0;
+  for (int c = 0; c < nparts; ++c) val += part[(size_t)s * nparts + c];
   double* f = sys;
   if (stage == 0) {
-    f[kSysRz * nsys + s] = val[s];
+    f[kSysRz * nsys + s] = val;
     f[kSysIters * nsys + s] = 0;
     f[kSysStatus * nsys + s] = 0;
   } else if (stage == 1) {
-    const double pap = val[s];
+    const double pap = val;
     f[kSysPap * nsys + s] = pap;
     const double a = f[kSysRz * nsys + s] / pap;
     if (!(pap > 0.0) || !isfinite(a)) {
@@ -264,7 +270,7 @@ __global__ void k_cg_scalars(int stage, double* __restrict__ sys, const double* 
     }
     f[kSysAlpha * nsys + s] = a;
   } else if (stage == 2) {
-    const double rr = val[s];
+    const double rr = val;
     f[kSysRr * nsys + s] = rr;
     const double it = f[kSysIters * nsys + s] + 1;
     f[kSysIters * nsys + s] = it;
@@ -277,9 +283,11 @@ __global__ void k_cg_scalars(int stage, double* __restrict__ sys, const double* 
     } else if (it >= maxit) {
       f[kSysStatus * nsys + s] = 3;
       active[s] = 0;
+    } else if (counter) {
+      atomicAdd(counter, 1);
     }
   } else {
-    const double rz = val[s];
+    const double rz = val;
     const double b = rz / f[kSysRz * nsys + s];
     f[kSysBeta * nsys + s] = isfinite(b) ? b : 0.0;
     f[kSysRz * nsys + s] = rz;
@@ -612,9 +620,10 @@ void cg_p(ikr_ctx* c, const SysList& L, int mode, CgVecs<R>& v, const double* sy
   IKR_CUDA(cudaGetLastError());
 }
 
-void cg_scalars(ikr_ctx* c, int stage, double* sys, const double* val, int nsys, int maxit, int* active) {
+void cg_scalars(ikr_ctx* c, int stage, double* sys, const double* part, int nparts, int nsys, int maxit,
+                int* active, int* counter) {
   ProfScope ps(c, kKidScalar, 1);
-  k_cg_scalars<<<(nsys + 127) / 128, 128, 0, c->stream>>>(stage, sys, val, nsys, maxit, active);
+  k_cg_scalars<<<(nsys + 127) / 128, 128, 0, c->stream>>>(stage, sys, part, nparts, nsys, maxit, active, counter);
   IKR_CUDA(cudaGetLastError());
 }
 

@@ -20,13 +20,15 @@ void launch_z_inverse(ikr_ctx* c, const SysList& L, const C_t<R>* sphere, int ld
                       C_t<R>* b1);
 template <typename R>
 void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, const double* pot_scale,
-                  const int* active, C_t<R>* b4);
+                  const int* active, C_t<R>* b4, const C_t<R>* real_in = nullptr);
+template <typename R> void launch_synth_planes(ikr_ctx* c, int nsys, const C_t<R>* b1, C_t<R>* out);
 template <typename R>
 void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* out, int ld,
                       const C_t<R>* psi, const double* shift, bool kinetic, const int* active);
 template <typename R>
 void launch_density(ikr_ctx* c, int nsys, const C_t<R>* b1phi, const C_t<R>* b1d,
-                    const double* coef_a, const double* coef_b, double* out, double scale);
+                    const double* coef_a, const double* coef_b, double* out, double scale,
+                    const C_t<R>* psi_real = nullptr);
 template <typename R>
 void to_plane_layout(ikr_ctx* c, const double* in, R* out, double scale, const double* dscale);
 void full_fft(ikr_ctx* c, double2* data, bool inverse);
@@ -49,7 +51,8 @@ void cg_xr(ikr_ctx* c, const SysList& L, int mode, CgVecs<R>& v, const double* s
            double* dpart);
 template <typename R>
 void cg_p(ikr_ctx* c, const SysList& L, int mode, CgVecs<R>& v, const double* sys, const int* active);
-void cg_scalars(ikr_ctx* c, int stage, double* sys, const double* val, int nsys, int maxit, int* active);
+void cg_scalars(ikr_ctx* c, int stage, double* sys, const double* part, int nparts, int nsys, int maxit,
+                int* active, int* counter);
 void count_active(ikr_ctx* c, const int* active, int n, int* dout);
 void chi0_sys(ikr_ctx* c, const SysList& L, const double2* M, double* deps, double2* coefP);
 void occupation_response(ikr_ctx* c, const double* deps, double* coef_a, double* coef_b, double* deF);

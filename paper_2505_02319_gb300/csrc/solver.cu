@@ -137,10 +137,10 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
   cg_xr<R>(c, L, 0, v, sys, act, nullptr);
   proj_coef<R>(c, L, v.Z, c->ld, act, coef);
   proj_apply<R>(c, L, coef, v.Z, R(1), R(-1), v.Z, c->ld, v.R, w.dpart.p, act);
-  sys_reduce(c, w.dpart.p, pch, n, act, w.val.p);
-  cg_scalars(c, 0, sys, w.val.p, n, maxit, act);
+  cg_scalars(c, 0, sys, w.dpart.p, pch, n, maxit, act, nullptr);
   cg_p<R>(c, L, 0, v, sys, act);
   c->active_hint = n;
+  int* dcount = reinterpret_cast<int*>(w.scal.p + 40);
   for (int it = 1; it <= maxit; ++it) {
     // W = Q (H - eps) P
     launch_z_inverse<R>(c, L, v.P, c->ld, act, Bufs<R>::b1(c));
@@ -148,20 +148,15 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
     launch_z_forward<R>(c, L, Bufs<R>::b4(c), v.W, c->ld, v.P, sys + kSysShift * n, true, act);
     proj_coef<R>(c, L, v.W, c->ld, act, coef);
     proj_apply<R>(c, L, coef, v.W, R(1), R(-1), v.W, c->ld, v.P, w.dpart.p, act);
-    sys_reduce(c, w.dpart.p, pch, n, act, w.val.p);
-    cg_scalars(c, 1, sys, w.val.p, n, maxit, act);
+    cg_scalars(c, 1, sys, w.dpart.p, pch, n, maxit, act, dcount);
     // x += alpha p, r -= alpha W, z = M^-1 r, ||r||^2, stopping test
     cg_xr<R>(c, L, 1, v, sys, act, w.dpart.p);
-    sys_reduce(c, w.dpart.p, cch, n, act, w.val.p);
-    cg_scalars(c, 2, sys, w.val.p, n, maxit, act);
+    cg_scalars(c, 2, sys, w.dpart.p, cch, n, maxit, act, dcount);
     // z = Q z, beta, p = z + beta p
     proj_coef<R>(c, L, v.Z, c->ld, act, coef);
     proj_apply<R>(c, L, coef, v.Z, R(1), R(-1), v.Z, c->ld, v.R, w.dpart.p, act);
-    sys_reduce(c, w.dpart.p, pch, n, act, w.val.p);
-    cg_scalars(c, 3, sys, w.val.p, n, maxit, act);
+    cg_scalars(c, 3, sys, w.dpart.p, pch, n, maxit, act, nullptr);
     cg_p<R>(c, L, 1, v, sys, act);
-    int* dcount = reinterpret_cast<int*>(w.scal.p + 40);
-    count_active(c, act, n, dcount);
     IKR_CUDA(cudaMemcpyAsync(c->h_pinned, dcount, sizeof(int), cudaMemcpyDeviceToHost, strm));
     IKR_CUDA(cudaStreamSynchronize(strm));
     c->active_hint = c->h_pinned[0];
@@ -202,7 +197,7 @@ void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::
   double2* CP = reinterpret_cast<double2*>(w.coefP.p);
   // y_s = F(u . F^-1 phi_s): plane pass on the cached z-transformed orbitals
   to_plane_layout<double>(c, u, w.grid1.p, 1.0 / (double)c->Ng, pot_scale);
-  launch_plane<double>(c, L, c->d_b1phi.p, w.grid1.p, nullptr, nullptr, w.b4.p);
+  launch_plane<double>(c, L, c->d_b1phi.p, w.grid1.p, nullptr, nullptr, w.b4.p, c->d_psir.p);
   launch_z_forward<double>(c, L, w.b4.p, w.Y.p, ld, nullptr, nullptr, false, nullptr);
   // M = Phi^H Y; deps_s = M[s][n_s]; dphi^P coefficients (metals)
   proj_coef<double>(c, L, w.Y.p, ld, nullptr, M);
@@ -226,7 +221,7 @@ void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::
   // df_s = f'_s (deps_s - deps_F), density coefficients
   occupation_response(c, w.deps.p, w.ca.p, w.cb.p, w.scal.p + 8);
   launch_z_inverse<double>(c, L, w.X.p, ld, nullptr, w.b1b.p);
-  launch_density<double>(c, n, c->d_b1phi.p, w.b1b.p, w.ca.p, w.cb.p, drho, 1.0 / c->volume);
+  launch_density<double>(c, n, c->d_b1phi.p, w.b1b.p, w.ca.p, w.cb.p, drho, 1.0 / c->volume, c->d_psir.p);
 }
 
 // Ev = v - ||Kv|| chi0(Kv/||Kv||)  (eq. op_discretised).  tol_fn receives ||Kv||.
