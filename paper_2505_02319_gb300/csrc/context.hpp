@@ -181,6 +181,7 @@ struct ikr_ctx {
   ikr::DBuf<double2> d_b1phi;   // z-transformed occupied orbitals [s][iz][c]
   ikr::DBuf<float2> d_b1phi32;
   ikr::DBuf<double2> d_psir;    // real-space planes of the occupied orbitals [s][iz][iy][ix] (unnormalised)
+  ikr::DBuf<float2> d_psir32;
   ikr::SysList occ;             // all occupied (k, n) in k-major order
   int noccmax = 0;
   ikr::DBuf<double2> d_phi_all; // occupied orbitals, vector s of occ at s * ld (complex128)

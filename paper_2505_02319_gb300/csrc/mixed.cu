@@ -17,6 +17,7 @@ namespace {
 
 constexpr double kRel = 2e-5;     // relative residual an FP32 CG solve is asked for
 constexpr double kTrust = 1e-2;   // tol >= kTrust ||b||: the FP32 recursive residual is trusted
+constexpr double kGamma = 0.1;    // refined systems must reach ||r||_FP64 <= kGamma tol
 constexpr int kMaxRefine = 8;
 
 // partial sums of |v|^2 per system (chunks of 256)
@@ -115,7 +116,9 @@ CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv
       need[s] = !accepted[s];
       if (need[s]) {
         ++nneed;
-        t32[s] = std::max(tol[s], kRel * rnorm[s]);
+        // a restarted FP32 solve leaves an unstructured residual whose small-gap
+        // components A^-1 amplifies; refined systems therefore aim at kGamma tol
+        t32[s] = (pass == 0) ? std::max(tol[s], kRel * rnorm[s]) : std::max(kGamma * tol[s], kRel * rnorm[s]);
       }
     }
     if (nneed == 0) break;
@@ -179,7 +182,7 @@ CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv
       }
     sys_norms(w.R.p, act, check.data(), rnorm);
     for (int s = 0; s < n; ++s)
-      if (check[s] && rnorm[s] <= tol[s]) accepted[s] = 1;
+      if (check[s] && rnorm[s] <= kGamma * tol[s]) accepted[s] = 1;
   }
   for (int s = 0; s < n; ++s) {
     out.res[s] = rnorm[s];

@@ -389,6 +389,8 @@ void set_eigenpairs(ikr_ctx* c, const ikr_eigenpairs* eig) {
   to_fp32(c, c->d_b1phi.p, b1n, c->d_b1phi32.p);
   c->d_psir.reserve((size_t)S * c->Ng);
   launch_synth_planes<double>(c, S, c->d_b1phi.p, c->d_psir.p);
+  c->d_psir32.reserve((size_t)S * c->Ng);
+  to_fp32(c, c->d_psir.p, (size_t)S * c->Ng, c->d_psir32.p);
   // density rho = sum_k w_k sum_n f_nk |F^-1 phi_nk|^2 and K^xc[rho]
   std::vector<double> wf(S), ones(S, 1.0);
   for (int s = 0; s < S; ++s) wf[s] = w_o[s] * f_o[s];

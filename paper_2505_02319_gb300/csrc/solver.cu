@@ -184,8 +184,11 @@ template CgStats cg_solve<float>(ikr_ctx*, const SysList&, const float2*, float2
 
 // ------------------------------------------------------------------- chi0 --
 // drho = chi0 (pot_scale * u) for the occupied systems (eqs. chi0, kchi0).
+// fp32 = true runs the whole application (right-hand sides, CG, density) in
+// FP32 with FP64 accumulation of the density; the callers choose it only when
+// the error budget of the application is far above FP32 rounding.
 void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::vector<double>& tol,
-               int maxit, int precision, double* drho, RunStats& rs) {
+               int maxit, int precision, double* drho, RunStats& rs, bool fp32) {
   IKR_REQUIRE(c->have_gs, IKR_ERR_STATE, "the ground state is not set");
   const SysList& L = c->occ;
   const int n = L.n;
@@ -195,7 +198,31 @@ void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::
   const int ld = c->ld;
   double2* M = reinterpret_cast<double2*>(w.coefM.p);
   double2* CP = reinterpret_cast<double2*>(w.coefP.p);
-  // y_s = F(u . F^-1 phi_s): plane pass on the cached z-transformed orbitals
+  std::vector<double> shift(n), kappa(n);
+  for (int s = 0; s < n; ++s) {
+    shift[s] = c->k[L.k[s]].eps[L.band[s]];
+    kappa[s] = c->h_kappa_occ[s];
+  }
+  if (fp32) {
+    float* upl = reinterpret_cast<float*>(w.grid1.p);
+    float2* Y = w.W32.p;     // consumed before the CG reuses W32
+    to_plane_layout<float>(c, u, upl, 1.0 / (double)c->Ng, pot_scale);
+    launch_plane<float>(c, L, nullptr, upl, nullptr, nullptr, reinterpret_cast<float2*>(w.b4.p), c->d_psir32.p);
+    launch_z_forward<float>(c, L, reinterpret_cast<float2*>(w.b4.p), Y, ld, nullptr, nullptr, false, nullptr);
+    proj_coef<float>(c, L, Y, ld, nullptr, M);
+    chi0_sys(c, L, M, w.deps.p, CP);
+    proj_apply<float>(c, L, M, Y, -1.0f, 1.0f, w.B32.p, ld, nullptr, nullptr, nullptr);
+    CgStats st = cg_solve<float>(c, L, w.B32.p, w.X32.p, shift, kappa, tol, maxit);
+    st.fp32 = true;
+    rs.add(st);
+    if (c->T > 0.0) proj_apply<float>(c, L, CP, w.X32.p, 1.0f, 1.0f, w.X32.p, ld, nullptr, nullptr, nullptr);
+    occupation_response(c, w.deps.p, w.ca.p, w.cb.p, w.scal.p + 8);
+    float2* b1b = reinterpret_cast<float2*>(w.b1b.p);
+    launch_z_inverse<float>(c, L, w.X32.p, ld, nullptr, b1b);
+    launch_density<float>(c, n, c->d_b1phi32.p, b1b, w.ca.p, w.cb.p, drho, 1.0 / c->volume, c->d_psir32.p);
+    return;
+  }
+  // y_s = F(u . F^-1 phi_s): plane pass on the cached real-space orbitals
   to_plane_layout<double>(c, u, w.grid1.p, 1.0 / (double)c->Ng, pot_scale);
   launch_plane<double>(c, L, c->d_b1phi.p, w.grid1.p, nullptr, nullptr, w.b4.p, c->d_psir.p);
   launch_z_forward<double>(c, L, w.b4.p, w.Y.p, ld, nullptr, nullptr, false, nullptr);
@@ -204,11 +231,6 @@ void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::
   chi0_sys(c, L, M, w.deps.p, CP);
   // b_s = -Q y_s
   proj_apply<double>(c, L, M, w.Y.p, -1.0, 1.0, w.B.p, ld, nullptr, nullptr, nullptr);
-  std::vector<double> shift(n), kappa(n);
-  for (int s = 0; s < n; ++s) {
-    shift[s] = c->k[L.k[s]].eps[L.band[s]];
-    kappa[s] = c->h_kappa_occ[s];
-  }
   CgStats st;
   if (precision == IKR_MIXED) {
     st = mixed_solve(c, L, w.B.p, w.X.p, shift, kappa, tol, maxit);
@@ -225,8 +247,14 @@ void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::
 }
 
 // Ev = v - ||Kv|| chi0(Kv/||Kv||)  (eq. op_discretised).  tol_fn receives ||Kv||.
+// allowed: the absolute error Algorithm 1 grants this application (0: none
+// given).  With IKR_MIXED the application runs entirely in FP32 when its
+// estimated FP32 rounding error, kFp32Rel ||v - Ev|| of the previous
+// application, is at most allowed / 10.
+constexpr double kFp32Rel = 1e-6;
+
 void dielectric_core(ikr_ctx* c, const double* v, double* Ev, const TolFn& tol_fn, int maxit, int precision,
-                     RunStats& rs) {
+                     RunStats& rs, double allowed) {
   Workspace& w = c->ws;
   ensure_workspace(c, c->occ.n);
   double* Kv = w.grid2.p;
@@ -242,8 +270,16 @@ void dielectric_core(ikr_ctx* c, const double* v, double* Ev, const TolFn& tol_f
   }
   IKR_REQUIRE(std::isfinite(h[1]), IKR_ERR_NUMERIC, "non-finite ||Kv||");
   const std::vector<double> tol = tol_fn(h[1]);
-  chi0_core(c, Kv, nrm + 2, tol, maxit, precision, w.grid3.p, rs);
+  const bool fp32 = precision == IKR_MIXED && allowed > 0.0 && rs.last_dEv > 0.0 &&
+                    10.0 * kFp32Rel * rs.last_dEv <= allowed;
+  chi0_core(c, Kv, nrm + 2, tol, maxit, precision, w.grid3.p, rs, fp32);
   axpy(c, v, w.grid3.p, -1.0, nrm + 1, Ev);
+  // ||v - Ev|| = ||Kv|| ||chi0 u|| for the next precision decision
+  norm2(c, w.grid3.p, w.scal.p + 48);
+  double d3[3];
+  IKR_CUDA(cudaMemcpyAsync(d3, w.scal.p + 48, sizeof(d3), cudaMemcpyDeviceToHost, c->stream));
+  IKR_CUDA(cudaStreamSynchronize(c->stream));
+  rs.last_dEv = h[1] * d3[1];
   rs.e_applies++;
 }
 
@@ -375,7 +411,7 @@ void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o
         track(t);
         return t;
       };
-      dielectric_core(c, x, wv, tf, o.cg_maxit, o.precision, rs);
+      dielectric_core(c, x, wv, tf, o.cg_maxit, o.precision, rs, o.tau / 3.0);
       if (kerker) {
         axpy(c, b, wv, -1.0, nullptr, r0);
         apply_kerker(c, r0, r0, o.kerker_alpha);
@@ -412,7 +448,8 @@ void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o
         track(t);
         return t;
       };
-      dielectric_core(c, V + (size_t)(i - 1) * Ng, wv, tf, o.cg_maxit, o.precision, rs);
+      dielectric_core(c, V + (size_t)(i - 1) * Ng, wv, tf, o.cg_maxit, o.precision, rs,
+                      s / (3.0 * m) * o.tau / rprev);
       if (kerker) apply_kerker(c, wv, wv, o.kerker_alpha);
       steps++;
       // classical Gram-Schmidt with one reorthogonalisation pass (FP64)

@@ -21,6 +21,7 @@ struct RunStats {
   int e_applies = 0, e_applies_fp32 = 0;
   int cg_max_iters = 0, cg_noconv = 0, cg_numeric = 0;
   double kv_norm = 0.0, sigma = 0.0;
+  double last_dEv = 0.0;            // ||v - Ev|| of the previous E application
   void add(const CgStats& s) {
     n_ham += s.n_ham;
     n_ham_fp64 += s.fp32 ? s.n_ham_fp64 : s.n_ham;
@@ -43,9 +44,9 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
 CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv, const std::vector<double>& shift,
                     const std::vector<double>& kappa, const std::vector<double>& tol, int maxit);
 void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::vector<double>& tol,
-               int maxit, int precision, double* drho, RunStats& rs);
+               int maxit, int precision, double* drho, RunStats& rs, bool fp32 = false);
 void dielectric_core(ikr_ctx* c, const double* v, double* Ev, const TolFn& tol_fn, int maxit, int precision,
-                     RunStats& rs);
+                     RunStats& rs, double allowed = 0.0);
 std::vector<double> strategy_tolerances(ikr_ctx* c, const ikr_solve_opts& o, int i, double s, double rprev,
                                         double kv_norm, double b_norm);
 void hamiltonian_noalloc(ikr_ctx* c, int k, const double2* psi, double2* hpsi, int nvec);
