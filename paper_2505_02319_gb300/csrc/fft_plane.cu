@@ -1,0 +1,382 @@
+// Plane pass of the batched H_k application with compile-time line lengths.
+//
+// Same computation as k_plane in fft.cu (y-lines of the active x positions,
+// x-lines of all rows, the product with the potential, and back), but each
+// line of length N is transformed by T threads that hold E = N / T elements
+// in registers:
+//   1. thread t loads x[t + T q], q < E, and takes the E-point DFT in
+//      registers (a recursive four-step split E = P Q with P in {4, 2, 3, 5});
+//   2. it multiplies by W_N^{t k2} and writes Y_t[k2] to shared memory;
+//   3. after a warp barrier, thread t takes the T-point DFTs of the k2 = t + T j
+//      and writes X[k2 + E k1] (natural order).
+// With n = p + P q and k = k2 + Q k1 the DFT factorises as
+//   X_{k2 + Q k1} = sum_p W_P^{p k1} W_N^{p k2} sum_q x_{p + P q} W_Q^{q k2},
+// the textbook Cooley-Tukey split, applied at both levels.  All index
+// arithmetic is resolved at compile time; only warp barriers separate the
+// steps of one line, and an x-line runs inverse FFT, potential product and
+// forward FFT without leaving its warp.
+#include "ops.hpp"
+
+namespace ikr {
+
+namespace {
+
+// W_L^x (L = table length) for sub-transform size M, x = index in [0, M)
+template <typename C, int L, int M, bool INV>
+__device__ __forceinline__ C tw(const C* tab, int x) {
+  C w = tab[x * (L / M)];
+  if (INV) w.y = -w.y;
+  return w;
+}
+
+// E = P Q: the base lengths 2..5 are one register DFT (P = E, Q = 1),
+// otherwise the first factor is taken from 4, 2, 3, 5 in that order.
+template <int E> struct Split {
+  static constexpr bool base = (E == 2 || E == 3 || E == 4 || E == 5);
+  static constexpr int P = base ? E : (E % 4 == 0) ? 4 : (E % 2 == 0) ? 2 : (E % 3 == 0) ? 3 : 5;
+  static constexpr int Q = E / P;
+};
+
+// In-register DFT of length E (natural order in and out), twiddles from a
+// table of W_L, E | L.
+template <typename C, int E, int L, bool INV> struct RegFft {
+  __device__ __forceinline__ static void run(C* v, const C* tab) {
+    constexpr int P = Split<E>::P, Q = Split<E>::Q;
+    if constexpr (Q == 1) {
+      Dft<C, E, INV>::run(v);
+    } else {
+      C u[P][Q];
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) u[p][q] = v[p + P * q];
+#pragma unroll
+      for (int p = 0; p < P; ++p) RegFft<C, Q, L, INV>::run(u[p], tab);
+#pragma unroll
+      for (int p = 1; p < P; ++p)
+#pragma unroll
+        for (int k2 = 1; k2 < Q; ++k2) u[p][k2] = cmul(u[p][k2], tw<C, L, E, INV>(tab, p * k2));
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) {
+        C w[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) w[p] = u[p][k2];
+        Dft<C, P, INV>::run(w);
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) v[k2 + Q * k1] = w[k1];
+      }
+    }
+  }
+};
+template <typename C, int L, bool INV> struct RegFft<C, 1, L, INV> {
+  __device__ __forceinline__ static void run(C*, const C*) {}
+};
+
+// Threads per line for a line length N: a power of two T with T^2 | N where
+// that keeps E = N / T <= 32 registers of data (then a thread's inverse-FFT
+// outputs are exactly its forward-FFT inputs, see line_fft_ivf), else the
+// largest power of two dividing N (up to 8).
+template <int N> struct Tpl {
+  static constexpr int v = (N % 64 == 0 && N / 8 <= 32) ? 8
+                         : (N % 16 == 0 && N / 4 <= 32) ? 4
+                         : (N % 4 == 0 && N / 2 <= 32) ? 2
+                         : (N % 8 == 0) ? 8 : (N % 4 == 0) ? 4 : (N % 2 == 0) ? 2 : 1;
+  static constexpr bool fused = (N / v) % v == 0;
+};
+
+// FFT of one line held in shared memory (element stride es) by the T lanes
+// t = 0..T-1 of a group; `mask` holds the lanes of the warp taking part.
+template <typename C, int N, bool INV>
+__device__ __forceinline__ void line_fft(C* line, int es, const C* tab, int t, unsigned mask) {
+  constexpr int T = Tpl<N>::v;
+  constexpr int E = N / T;
+  C v[E];
+#pragma unroll
+  for (int q = 0; q < E; ++q) v[q] = line[(t + T * q) * es];
+  RegFft<C, E, N, INV>::run(v, tab);
+  if constexpr (T == 1) {
+#pragma unroll
+    for (int k = 0; k < E; ++k) line[k * es] = v[k];
+  } else {
+#pragma unroll
+    for (int k2 = 1; k2 < E; ++k2) {
+      C w = tab[t * k2];
+      if (INV) w.y = -w.y;
+      v[k2] = cmul(v[k2], w);
+    }
+    __syncwarp(mask);
+#pragma unroll
+    for (int k2 = 0; k2 < E; ++k2) line[(k2 * T + t) * es] = v[k2];
+    __syncwarp(mask);
+    constexpr int J = (E + T - 1) / T;
+    C w[J][T];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int k2 = t + T * j;
+      if (k2 < E) {
+#pragma unroll
+        for (int tp = 0; tp < T; ++tp) w[j][tp] = line[(k2 * T + tp) * es];
+        RegFft<C, T, N, INV>::run(w[j], tab);
+      }
+    }
+    __syncwarp(mask);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int k2 = t + T * j;
+      if (k2 < E) {
+#pragma unroll
+        for (int k1 = 0; k1 < T; ++k1) line[(k2 + E * k1) * es] = w[j][k1];
+      }
+    }
+    __syncwarp(mask);
+  }
+}
+
+// Row stride: with T lanes per x-line reading T consecutive elements, rows
+// that are 4 elements (8 banks of 8-byte data) apart in bank space let 8
+// lines of a warp share the minimum of 2 wavefronts; odd strides otherwise.
+// Second half of a line FFT (steps 2 and 3 of the header) on values the
+// thread already holds: v[q] = Y_t[k2 = q] after the E-point DFT.  Writes the
+// result X in natural order to the line.
+template <typename C, int N, bool INV>
+__device__ __forceinline__ void line_fft_finish(C* v, C* line, int es, const C* tab, int t, unsigned mask) {
+  constexpr int T = Tpl<N>::v;
+  constexpr int E = N / T;
+#pragma unroll
+  for (int k2 = 1; k2 < E; ++k2) {
+    C w = tab[t * k2];
+    if (INV) w.y = -w.y;
+    v[k2] = cmul(v[k2], w);
+  }
+  __syncwarp(mask);
+#pragma unroll
+  for (int k2 = 0; k2 < E; ++k2) line[(k2 * T + t) * es] = v[k2];
+  __syncwarp(mask);
+  constexpr int J = E / T;
+  C w[J][T];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int k2 = t + T * j;
+#pragma unroll
+    for (int tp = 0; tp < T; ++tp) w[j][tp] = line[(k2 * T + tp) * es];
+    RegFft<C, T, N, INV>::run(w[j], tab);
+  }
+  __syncwarp(mask);
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int k1 = 0; k1 < T; ++k1) line[(t + T * j + E * k1) * es] = w[j][k1];
+  __syncwarp(mask);
+}
+
+// x-line: inverse FFT (unless the line is already in real space), product
+// with the potential row, forward FFT.  Requires T | E: thread t's inverse
+// outputs X[t + T j + E k1] = X[t + T (j + J k1)] are its forward inputs
+// x[t + T q], so the product happens in registers.
+template <typename R, int N>
+__device__ __forceinline__ void line_fft_ivf(C_t<R>* line, const C_t<R>* tab, int t, unsigned mask,
+                                             const R* __restrict__ pot_row, R sc, bool in_real) {
+  using C = C_t<R>;
+  constexpr int T = Tpl<N>::v;
+  constexpr int E = N / T;
+  constexpr int J = E / T;
+  C v[E];
+#pragma unroll
+  for (int q = 0; q < E; ++q) v[q] = line[t + T * q];
+  if (!in_real) {
+    RegFft<C, E, N, true>::run(v, tab);
+#pragma unroll
+    for (int k2 = 1; k2 < E; ++k2) {
+      C w = tab[t * k2];
+      w.y = -w.y;
+      v[k2] = cmul(v[k2], w);
+    }
+    __syncwarp(mask);
+#pragma unroll
+    for (int k2 = 0; k2 < E; ++k2) line[k2 * T + t] = v[k2];
+    __syncwarp(mask);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      C w[T];
+      const int k2 = t + T * j;
+#pragma unroll
+      for (int tp = 0; tp < T; ++tp) w[tp] = line[k2 * T + tp];
+      RegFft<C, T, N, true>::run(w, tab);
+#pragma unroll
+      for (int k1 = 0; k1 < T; ++k1) v[j + J * k1] = w[k1];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < E; ++q) v[q] = cscale(v[q], __ldg(pot_row + t + T * q) * sc);
+  RegFft<C, E, N, false>::run(v, tab);
+  line_fft_finish<C, N, false>(v, line, 1, tab, t, mask);
+}
+
+template <typename C, int NX, int NY>
+struct PlaneGeom {
+  static constexpr int ldp = (NX % 16 == 0) ? NX + 4 : (NX % 2 == 0 ? NX + 1 : NX);
+  static constexpr int plane = NY * ldp;
+  static constexpr int bytes = plane * (int)sizeof(C);
+  static constexpr int PL = (65536 / bytes) >= 3 ? 3 : ((65536 / bytes) >= 2 ? 2 : 1);
+};
+
+}  // namespace
+
+template <typename R, int NX, int NY>
+__global__ void __launch_bounds__(256) k_plane_t(const C_t<R>* __restrict__ b1, int nc, int ncp,
+                                                 const int* __restrict__ col_xy, const int* __restrict__ xpos,
+                                                 int nxa, int Nz, const C_t<R>* __restrict__ twx,
+                                                 const C_t<R>* __restrict__ twy, const R* __restrict__ pot,
+                                                 const double* __restrict__ pot_scale,
+                                                 const int* __restrict__ active, C_t<R>* __restrict__ b4,
+                                                 const C_t<R>* __restrict__ real_in) {
+  using C = C_t<R>;
+  using G = PlaneGeom<C, NX, NY>;
+  constexpr int ldp = G::ldp, PL = G::PL;
+  constexpr int TX = Tpl<NX>::v, TY = Tpl<NY>::v;
+  const int s = blockIdx.y;
+  if (active && !active[s]) return;
+  const int iz0 = blockIdx.x * PL;
+  const int npl = min(PL, Nz - iz0);
+  extern __shared__ unsigned char smem_raw[];
+  C* tx = reinterpret_cast<C*>(smem_raw);
+  C* ty = tx + NX;
+  C* planes = ty + NY;
+  int* xp = reinterpret_cast<int*>(planes + PL * G::plane);
+  for (int i = threadIdx.x; i < NX; i += blockDim.x) tx[i] = twx[i];
+  for (int i = threadIdx.x; i < NY; i += blockDim.x) ty[i] = twy[i];
+  for (int i = threadIdx.x; i < nxa; i += blockDim.x) xp[i] = xpos[i];
+  const int lane = threadIdx.x & 31;
+  if (real_in) {
+    for (int e = threadIdx.x; e < npl * NY * NX; e += blockDim.x) {
+      const int p = e / (NY * NX), r = e - p * (NY * NX);
+      const int iy = r / NX, ix = r - iy * NX;
+      planes[p * G::plane + iy * ldp + ix] = real_in[((size_t)s * Nz + iz0 + p) * NY * NX + r];
+    }
+    __syncthreads();
+  } else {
+    for (int i = threadIdx.x; i < npl * G::plane; i += blockDim.x) planes[i] = mk<C>(0, 0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < npl * nc; e += blockDim.x) {
+      const int p = e / nc, col = e - p * nc;
+      planes[p * G::plane + col_xy[2 * col + 1] * ldp + col_xy[2 * col]] =
+          b1[((size_t)s * Nz + iz0 + p) * ncp + col];
+    }
+    __syncthreads();
+    // inverse y-lines of the active x positions
+    {
+      const int slots = blockDim.x / TY, slot = threadIdx.x / TY, t = threadIdx.x % TY;
+      const int items = npl * nxa;
+      const int rounds = (items + slots - 1) / slots;
+      for (int r = 0; r < rounds; ++r) {
+        const int it = r * slots + slot;
+        const bool ok = it < items;
+        const unsigned mask = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+          const int p = it / nxa, l = it - p * nxa;
+          line_fft<C, NY, true>(planes + p * G::plane + xp[l], ldp, ty, t, mask);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // x-lines: inverse FFT, potential product, forward FFT, all within the line's lanes
+  {
+    const R sc = pot_scale ? (R)(*pot_scale) : R(1);
+    const int slots = blockDim.x / TX, slot = threadIdx.x / TX, t = threadIdx.x % TX;
+    const int items = npl * NY;
+    const int rounds = (items + slots - 1) / slots;
+    for (int r = 0; r < rounds; ++r) {
+      const int it = r * slots + slot;
+      const bool ok = it < items;
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (ok) {
+        const int p = it / NY, iy = it - p * NY;
+        C* line = planes + p * G::plane + iy * ldp;
+        const R* pp = pot + ((size_t)(iz0 + p) * NY + iy) * NX;
+        if constexpr (Tpl<NX>::fused) {
+          line_fft_ivf<R, NX>(line, tx, t, mask, pp, sc, real_in != nullptr);
+        } else {
+          if (!real_in) line_fft<C, NX, true>(line, 1, tx, t, mask);   // real_in: already in real space
+#pragma unroll
+          for (int ix = t; ix < NX; ix += TX) line[ix] = cscale(line[ix], pp[ix] * sc);
+          __syncwarp(mask);
+          line_fft<C, NX, false>(line, 1, tx, t, mask);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // forward y-lines of the active x positions
+  {
+    const int slots = blockDim.x / TY, slot = threadIdx.x / TY, t = threadIdx.x % TY;
+    const int items = npl * nxa;
+    const int rounds = (items + slots - 1) / slots;
+    for (int r = 0; r < rounds; ++r) {
+      const int it = r * slots + slot;
+      const bool ok = it < items;
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (ok) {
+        const int p = it / nxa, l = it - p * nxa;
+        line_fft<C, NY, false>(planes + p * G::plane + xp[l], ldp, ty, t, mask);
+      }
+    }
+  }
+  __syncthreads();
+  (void)lane;
+  for (int e = threadIdx.x; e < npl * nc; e += blockDim.x) {
+    const int p = e / nc, col = e - p * nc;
+    b4[((size_t)s * Nz + iz0 + p) * ncp + col] =
+        planes[p * G::plane + col_xy[2 * col + 1] * ldp + col_xy[2 * col]];
+  }
+}
+
+namespace {
+
+template <typename R> const C_t<R>* twp(ikr_ctx* c, int axis);
+template <> const double2* twp<double>(ikr_ctx* c, int axis) { return c->d_tw[axis].p; }
+template <> const float2* twp<float>(ikr_ctx* c, int axis) { return c->d_tw32[axis].p; }
+
+template <typename R, int NX, int NY>
+bool try_launch(ikr_ctx* c, int nsys, const C_t<R>* b1, const R* pot, const double* pot_scale,
+                const int* active, C_t<R>* b4, const C_t<R>* real_in) {
+  if (c->N[0] != NX || c->N[1] != NY) return false;
+  using G = PlaneGeom<C_t<R>, NX, NY>;
+  const size_t smem = sizeof(C_t<R>) * (NX + NY + (size_t)G::PL * G::plane) + sizeof(int) * c->nxa;
+  if (smem > 227 * 1024) return false;
+  IKR_CUDA(cudaFuncSetAttribute(k_plane_t<R, NX, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int Nz = c->N[2];
+  dim3 grid((Nz + G::PL - 1) / G::PL, nsys);
+  k_plane_t<R, NX, NY><<<grid, 256, smem, c->stream>>>(b1, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa, Nz,
+                                                        twp<R>(c, 0), twp<R>(c, 1), pot, pot_scale, active, b4,
+                                                        real_in);
+  IKR_CUDA(cudaGetLastError());
+  return true;
+}
+
+}  // namespace
+
+// Compile-time plane shapes of the supported grids; false: use the generic kernel.
+template <typename R>
+bool launch_plane_fast(ikr_ctx* c, int nsys, const C_t<R>* b1, const R* pot, const double* pot_scale,
+                       const int* active, C_t<R>* b4, const C_t<R>* real_in) {
+  return try_launch<R, 48, 48>(c, nsys, b1, pot, pot_scale, active, b4, real_in) ||
+         try_launch<R, 32, 32>(c, nsys, b1, pot, pot_scale, active, b4, real_in) ||
+         try_launch<R, 40, 40>(c, nsys, b1, pot, pot_scale, active, b4, real_in) ||
+         try_launch<R, 96, 96>(c, nsys, b1, pot, pot_scale, active, b4, real_in) ||
+         try_launch<R, 12, 12>(c, nsys, b1, pot, pot_scale, active, b4, real_in) ||
+         try_launch<R, 10, 12>(c, nsys, b1, pot, pot_scale, active, b4, real_in) ||
+         try_launch<R, 24, 24>(c, nsys, b1, pot, pot_scale, active, b4, real_in);
+}
+
+// FP64: the register-resident variant leaves the few FP64 units of the part
+// idle more often than the shared-memory Stockham kernel; keep the latter.
+template <>
+bool launch_plane_fast<double>(ikr_ctx*, int, const double2*, const double*, const double*, const int*,
+                               double2*, const double2*) {
+  return false;
+}
+template bool launch_plane_fast<float>(ikr_ctx*, int, const float2*, const float*, const double*, const int*,
+                                       float2*, const float2*);
+
+}  // namespace ikr

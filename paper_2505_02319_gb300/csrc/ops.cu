@@ -8,8 +8,22 @@ namespace ikr {
 // ------------------------------------------------------------ projections --
 // For the systems s of k-point k (grouped: L.kstart[k] .. + L.kcount[k]):
 //   coef[s][m] = <phi_m, y_s> = sum_G conj(Phi_k[m][G]) y_s[G]       (Phi^H Y)
-// in two deterministic stages: per-chunk partials, then a fixed-order sum.
-constexpr int kPC = 32;   // G chunk of the projection kernels
+// as a split-K product: every CTA owns a chunk of kKC plane waves of one
+// k-point and all (m, s) pairs, with the chunk of Phi and Y staged in shared
+// memory and a 2 x 2 register tile of outputs per thread; the per-chunk
+// partial sums are then added in fixed order (deterministic).
+// G chunk of the Phi^H Y kernel: 64 (FP32) or 32 (FP64) keeps the two staged
+// tiles within 48 KB of static shared memory
+template <typename R> struct KC;
+template <> struct KC<float> { static constexpr int v = 64; };
+template <> struct KC<double> { static constexpr int v = 32; };
+// G chunk and systems per thread of the Y - Phi C kernel: FP32 128 x 16,
+// FP64 32 x 4 (more, shorter CTAs: the FP64 rate of the part makes each
+// CTA long, and the last wave must stay short)
+template <typename R> struct AC;
+template <> struct AC<float> { static constexpr int g = 128, sg = 16; };
+template <> struct AC<double> { static constexpr int g = 32, sg = 4; };
+constexpr int kTile = 32;    // output tile (m and s) of the Phi^H Y kernel
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_proj_partial(const C_t<R>* __restrict__ phi_all, int ld,
@@ -26,39 +40,50 @@ __global__ void __launch_bounds__(256) k_proj_partial(const C_t<R>* __restrict__
   const int ns = kcount[k];
   if (ns == 0) return;
   const int nocc = nocc_k[k], nb = nb_k[k];
-  const int g0 = chunk * kPC;
-  extern __shared__ unsigned char smem_raw[];
-  C* ph = reinterpret_cast<C*>(smem_raw);           // [g][m], kPC x nocc
-  C* ys = ph + kPC * nocc;                          // per warp kPC entries
+  constexpr int kKC = KC<R>::v;
+  const int g0 = chunk * kKC;
+  __shared__ C ph[kKC][kTile + 1];
+  __shared__ C ys[kKC][kTile + 1];
   const C* phi = phi_all + (size_t)phi_off[k] * ld;
-  for (int idx = threadIdx.x; idx < kPC * nocc; idx += blockDim.x) {
-    const int m = idx / kPC, g = idx - m * kPC;
-    ph[g * nocc + m] = (g0 + g < nb) ? phi[(size_t)m * ld + g0 + g] : mk<C>(0, 0);
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  C* yw = ys + warp * kPC;
   const int s0 = kstart[k];
-  for (int sl = warp; sl < ns; sl += nw) {
-    const int s = s0 + sl;
-    if (active && !active[s]) continue;
-    yw[lane] = (g0 + lane < nb) ? Y[(size_t)s * ldy + g0 + lane] : mk<C>(0, 0);
-    __syncwarp();
-    for (int m = lane; m < nocc; m += 32) {
-      R ax = 0, ay = 0;
-#pragma unroll 8
-      for (int g = 0; g < kPC; ++g) {
-        const C p = ph[g * nocc + m], y = yw[g];
-        ax += p.x * y.x + p.y * y.y;
-        ay += p.x * y.y - p.y * y.x;
+  const int tm = threadIdx.x & 15, ts = threadIdx.x >> 4;   // 16 x 16 threads, 2 x 2 outputs each
+  for (int mt = 0; mt < nocc; mt += kTile) {
+    for (int st = 0; st < ns; st += kTile) {
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < kKC * kTile; idx += blockDim.x) {
+        const int r = idx / kKC, g = idx - r * kKC;      // r: m (or s) within the tile, g fastest
+        const bool gin = g0 + g < nb;
+        const int m = mt + r, sl = st + r;
+        ph[g][r] = (gin && m < nocc) ? phi[(size_t)m * ld + g0 + g] : mk<C>(0, 0);
+        bool act = sl < ns;
+        if (act && active) act = active[s0 + sl] != 0;
+        ys[g][r] = (gin && act) ? Y[(size_t)(s0 + sl) * ldy + g0 + g] : mk<C>(0, 0);
       }
-      part[((size_t)chunk * nsys + s) * noccmax + m] = make_double2(ax, ay);
+      __syncthreads();
+      R a[2][2][2] = {};
+#pragma unroll 8
+      for (int g = 0; g < kKC; ++g) {
+        const C p0 = ph[g][2 * tm], p1 = ph[g][2 * tm + 1];
+        const C y0 = ys[g][2 * ts], y1 = ys[g][2 * ts + 1];
+        // conj(p) * y
+        a[0][0][0] += p0.x * y0.x + p0.y * y0.y;  a[0][0][1] += p0.x * y0.y - p0.y * y0.x;
+        a[0][1][0] += p0.x * y1.x + p0.y * y1.y;  a[0][1][1] += p0.x * y1.y - p0.y * y1.x;
+        a[1][0][0] += p1.x * y0.x + p1.y * y0.y;  a[1][0][1] += p1.x * y0.y - p1.y * y0.x;
+        a[1][1][0] += p1.x * y1.x + p1.y * y1.y;  a[1][1][1] += p1.x * y1.y - p1.y * y1.x;
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int m = mt + 2 * tm + i, sl = st + 2 * ts + j;
+          if (m < nocc && sl < ns)
+            part[((size_t)chunk * nsys + s0 + sl) * noccmax + m] = make_double2(a[i][j][0], a[i][j][1]);
+        }
     }
-    __syncwarp();
   }
 }
 
-__global__ void k_proj_reduce(const double2* __restrict__ part, int nchunks, int nsys, int noccmax,
+__global__ void k_proj_reduce(const double2* __restrict__ part, int nchunks, int kc, int nsys, int noccmax,
                               const int* __restrict__ sys_k, const int* __restrict__ nocc_k,
                               const int* __restrict__ nb_k, const int* __restrict__ active,
                               double2* __restrict__ coef) {
@@ -68,7 +93,7 @@ __global__ void k_proj_reduce(const double2* __restrict__ part, int nchunks, int
   if (active && !active[s]) return;
   const int k = sys_k[s];
   if (m >= nocc_k[k]) return;
-  const int nch = (nb_k[k] + kPC - 1) / kPC;
+  const int nch = (nb_k[k] + kc - 1) / kc;
   double ax = 0, ay = 0;
   for (int c = 0; c < nch && c < nchunks; ++c) {
     const double2 v = part[((size_t)c * nsys + s) * noccmax + m];
@@ -80,6 +105,8 @@ __global__ void k_proj_reduce(const double2* __restrict__ part, int nchunks, int
 
 // out[s][G] = alpha * in[s][G] + beta * sum_m Phi_k[m][G] coef[s][m]
 // optionally dpart[s][chunk] = sum_{G in chunk} Re(conj(dv[s][G]) out[s][G]).
+// CTA: kAC plane waves of one k-point; thread (g, group) keeps the sums of
+// kSG systems in registers while m runs, coef of the k-point in shared memory.
 template <typename R>
 __global__ void __launch_bounds__(256) k_proj_apply(const C_t<R>* __restrict__ phi_all, int ld,
                                                     const int* __restrict__ phi_off,
@@ -94,58 +121,83 @@ __global__ void __launch_bounds__(256) k_proj_apply(const C_t<R>* __restrict__ p
                                                     double* __restrict__ dpart, int nparts,
                                                     const int* __restrict__ active) {
   using C = C_t<R>;
+  constexpr int kAC = AC<R>::g, kSG = AC<R>::sg, kGR = 256 / kAC;
   const int k = blockIdx.y, chunk = blockIdx.x;
   const int ns = kcount[k];
   if (ns == 0) return;
   const int nocc = nocc_k[k], nb = nb_k[k];
-  const int g0 = chunk * kPC;
-  if (g0 >= nb) {
-    // chunk beyond this k-point's basis: still define the dot partials
-    if (dpart)
-      for (int sl = threadIdx.x; sl < ns; sl += blockDim.x) dpart[(size_t)(kstart[k] + sl) * nparts + chunk] = 0.0;
-    return;
-  }
-  extern __shared__ unsigned char smem_raw[];
-  C* ph = reinterpret_cast<C*>(smem_raw);           // [m][g]
-  const C* phi = phi_all + (size_t)phi_off[k] * ld;
-  for (int idx = threadIdx.x; idx < kPC * nocc; idx += blockDim.x) {
-    const int m = idx / kPC, g = idx - m * kPC;
-    ph[m * kPC + g] = (g0 + g < nb) ? phi[(size_t)m * ld + g0 + g] : mk<C>(0, 0);
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int s0 = kstart[k];
-  for (int sl = warp; sl < ns; sl += nw) {
-    const int s = s0 + sl;
-    if (active && !active[s]) continue;
-    const double2* cf = coef + (size_t)s * noccmax;
-    R ax = 0, ay = 0;
-    for (int m = 0; m < nocc; ++m) {
-      const double2 cd = cf[m];
-      const C p = ph[m * kPC + lane];
-      const R cx = (R)cd.x, cy = (R)cd.y;
-      ax += p.x * cx - p.y * cy;
-      ay += p.x * cy + p.y * cx;
-    }
-    const int g = g0 + lane;
-    double d = 0.0;
-    if (g < nb) {
-      const size_t o = (size_t)s * ldy + g;
-      C v = mk<C>(beta * ax, beta * ay);
-      if (alpha != R(0)) {
-        const C x = in[o];
-        v.x += alpha * x.x;
-        v.y += alpha * x.y;
+  const int g0 = chunk * kAC;
+  extern __shared__ unsigned char smem_raw[];
+  C* cf = reinterpret_cast<C*>(smem_raw);                 // [kGR * kSG][nocc] coefficients of a system block
+  __shared__ double red[kGR][kSG][kAC / 32];
+  const int gl = threadIdx.x % kAC, grp = threadIdx.x / kAC;   // kGR groups of kSG systems
+  const int g = g0 + gl;
+  const bool gin = g < nb;
+  const C* phi = phi_all + (size_t)phi_off[k] * ld;
+  const int lane = threadIdx.x & 31, wig = gl >> 5;
+  for (int sb = 0; sb < ns; sb += kGR * kSG) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kGR * kSG * nocc; idx += blockDim.x) {
+      const int sl = idx / nocc, m = idx - sl * nocc;
+      const int s = sb + sl;
+      C v = mk<C>(0, 0);
+      if (s < ns) {
+        const double2 d = coef[(size_t)(s0 + s) * noccmax + m];
+        v = mk<C>((R)d.x, (R)d.y);
       }
-      out[o] = v;
-      if (dv) {
-        const C w = dv[o];
-        d = (double)w.x * v.x + (double)w.y * v.y;
+      cf[sl * nocc + m] = v;
+    }
+    __syncthreads();
+    R ax[kSG], ay[kSG];
+#pragma unroll
+    for (int j = 0; j < kSG; ++j) ax[j] = ay[j] = R(0);
+    const C* cg = cf + grp * kSG * nocc;
+    for (int m = 0; m < nocc; ++m) {
+      const C p = gin ? phi[(size_t)m * ld + g] : mk<C>(0, 0);
+#pragma unroll
+      for (int j = 0; j < kSG; ++j) {
+        const C c = cg[j * nocc + m];
+        ax[j] += p.x * c.x - p.y * c.y;
+        ay[j] += p.x * c.y + p.y * c.x;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kSG; ++j) {
+      const int sl = sb + grp * kSG + j;
+      const int s = s0 + sl;
+      const bool live = sl < ns && (!active || active[s]);
+      double d = 0.0;
+      if (live && gin) {
+        const size_t o = (size_t)s * ldy + g;
+        C v = mk<C>(beta * ax[j], beta * ay[j]);
+        if (alpha != R(0)) {
+          const C x = in[o];
+          v.x += alpha * x.x;
+          v.y += alpha * x.y;
+        }
+        out[o] = v;
+        if (dv) {
+          const C w = dv[o];
+          d = (double)w.x * v.x + (double)w.y * v.y;
+        }
+      }
+      if (dpart) {
+        d = warp_sum(d);
+        if (lane == 0) red[grp][j][wig] = d;
       }
     }
     if (dpart) {
-      d = warp_sum(d);
-      if (lane == 0) dpart[(size_t)s * nparts + chunk] = d;
+      __syncthreads();
+      if (threadIdx.x < kGR * kSG) {
+        const int gg = threadIdx.x / kSG, j = threadIdx.x % kSG;
+        const int sl = sb + gg * kSG + j;
+        if (sl < ns && (!active || active[s0 + sl])) {
+          double t = 0.0;
+          for (int w = 0; w < kAC / 32; ++w) t += red[gg][j][w];
+          dpart[(size_t)(s0 + sl) * nparts + chunk] = t;
+        }
+      }
     }
   }
 }
@@ -553,25 +605,28 @@ static void set_smem_attr(const void* f, size_t bytes) {
   IKR_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
 
-int proj_chunks(ikr_ctx* c) { return (c->ld + kPC - 1) / kPC; }
+int proj_chunks(ikr_ctx* c, int fp_bytes) {
+  const int g = fp_bytes == 4 ? AC<float>::g : AC<double>::g;
+  return (c->ld + g - 1) / g;
+}
+int proj_chunks(ikr_ctx* c) { return std::max(proj_chunks(c, 4), proj_chunks(c, 8)); }
 int cg_chunks(ikr_ctx* c) { return (c->ld + kEC - 1) / kEC; }
 
 template <typename R>
 void proj_coef(ikr_ctx* c, const SysList& L, const C_t<R>* Y, int ldy, const int* active, double2* coef) {
-  ProfScope ps(c, kKidProjCoef, 2);
-  const int nch = proj_chunks(c);
+  ProfScope ps(c, kKidProjCoef, 2, L.n, (int)sizeof(R));
+  const int kc = KC<R>::v;
+  const int nch = (c->ld + kc - 1) / kc;
   const int nm = c->noccmax;
   c->ws.cpart.reserve((size_t)nch * L.n * nm * 2);
   double2* part = reinterpret_cast<double2*>(c->ws.cpart.p);
-  const size_t smem = sizeof(C_t<R>) * (kPC * nm + 8 * kPC);
-  set_smem_attr((const void*)k_proj_partial<R>, smem);
   dim3 grid(nch, (unsigned)c->k.size());
-  k_proj_partial<R><<<grid, 256, smem, c->stream>>>(phi_ptr<R>(c), c->ld, c->d_phi_off.p, c->d_nocc.p,
-                                                     c->d_nb.p, L.d_kstart.p, L.d_kcount.p, Y, ldy,
-                                                     active, L.n, nm, part);
+  k_proj_partial<R><<<grid, 256, 0, c->stream>>>(phi_ptr<R>(c), c->ld, c->d_phi_off.p, c->d_nocc.p,
+                                                  c->d_nb.p, L.d_kstart.p, L.d_kcount.p, Y, ldy,
+                                                  active, L.n, nm, part);
   IKR_CUDA(cudaGetLastError());
   const int tot = L.n * nm;
-  k_proj_reduce<<<(tot + 255) / 256, 256, 0, c->stream>>>(part, nch, L.n, nm, L.d_k.p, c->d_nocc.p,
+  k_proj_reduce<<<(tot + 255) / 256, 256, 0, c->stream>>>(part, nch, kc, L.n, nm, L.d_k.p, c->d_nocc.p,
                                                           c->d_nb.p, active, coef);
   IKR_CUDA(cudaGetLastError());
 }
@@ -579,9 +634,9 @@ void proj_coef(ikr_ctx* c, const SysList& L, const C_t<R>* Y, int ldy, const int
 template <typename R>
 void proj_apply(ikr_ctx* c, const SysList& L, const double2* coef, const C_t<R>* in, R alpha, R beta,
                 C_t<R>* out, int ldy, const C_t<R>* dv, double* dpart, const int* active) {
-  ProfScope ps(c, kKidProjApply, 1);
-  const int nch = proj_chunks(c);
-  const size_t smem = sizeof(C_t<R>) * (kPC * c->noccmax);
+  ProfScope ps(c, kKidProjApply, 1, L.n, (int)sizeof(R));
+  const int nch = proj_chunks(c, (int)sizeof(R));
+  const size_t smem = sizeof(C_t<R>) * (256 / AC<R>::g * AC<R>::sg * std::max(c->noccmax, 1));
   set_smem_attr((const void*)k_proj_apply<R>, smem);
   dim3 grid(nch, (unsigned)c->k.size());
   k_proj_apply<R><<<grid, 256, smem, c->stream>>>(phi_ptr<R>(c), c->ld, c->d_phi_off.p, c->d_nocc.p,

@@ -23,6 +23,9 @@ void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, 
                   const int* active, C_t<R>* b4, const C_t<R>* real_in = nullptr);
 template <typename R> void launch_synth_planes(ikr_ctx* c, int nsys, const C_t<R>* b1, C_t<R>* out);
 template <typename R>
+bool launch_plane_fast(ikr_ctx* c, int nsys, const C_t<R>* b1, const R* pot, const double* pot_scale,
+                       const int* active, C_t<R>* b4, const C_t<R>* real_in);
+template <typename R>
 void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* out, int ld,
                       const C_t<R>* psi, const double* shift, bool kinetic, const int* active);
 template <typename R>
@@ -38,7 +41,8 @@ template <> inline const double* kin_all_ptr<double>(ikr_ctx* c) { return c->d_k
 template <> inline const float* kin_all_ptr<float>(ikr_ctx* c) { return c->d_kin_all32.p; }
 
 // ops.cu
-int proj_chunks(ikr_ctx* c);
+int proj_chunks(ikr_ctx* c);                  // the largest count (workspace sizing)
+int proj_chunks(ikr_ctx* c, int fp_bytes);    // dot partials per system written by proj_apply
 int cg_chunks(ikr_ctx* c);
 template <typename R>
 void proj_coef(ikr_ctx* c, const SysList& L, const C_t<R>* Y, int ldy, const int* active, double2* coef);

@@ -131,7 +131,7 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
   IKR_CUDA(cudaMemcpyAsync(w.active.p, ones.data(), sizeof(int) * n, cudaMemcpyHostToDevice, strm));
   double* sys = w.sys.p;
   int* act = w.active.p;
-  const int pch = proj_chunks(c), cch = cg_chunks(c);
+  const int pch = proj_chunks(c, (int)sizeof(R)), cch = cg_chunks(c);
   double2* coef = reinterpret_cast<double2*>(w.coef.p);
   // initial state: x = 0, r = b, z = Q M^-1 r, p = z
   cg_xr<R>(c, L, 0, v, sys, act, nullptr);
