@@ -324,6 +324,28 @@ __global__ void __launch_bounds__(256) k_synth_planes(const C_t<R>* __restrict__
   }
 }
 
+// sum over n systems of |psi_s(r)|^2 and (Re psi_s(r))^2 at every grid point
+// (planes of the cached real-space orbitals; the order of r does not matter)
+__global__ void k_orbital_sq_sums(const double2* __restrict__ psir, int nsys, size_t ng,
+                                  double* __restrict__ abs2, double* __restrict__ re2) {
+  for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < ng; r += (size_t)gridDim.x * blockDim.x) {
+    double a = 0.0, b = 0.0;
+    for (int s = 0; s < nsys; ++s) {
+      const double2 v = psir[(size_t)s * ng + r];
+      a += v.x * v.x + v.y * v.y;
+      b += v.x * v.x;
+    }
+    abs2[r] = a;
+    re2[r] = b;
+  }
+}
+
+void orbital_sq_sums(ikr_ctx* c, const double2* psir, int nsys, double* abs2, double* re2) {
+  ProfScope ps(c, kKidGridOps, 1);
+  k_orbital_sq_sums<<<152 * 8, 256, 0, c->stream>>>(psir, nsys, c->Ng, abs2, re2);
+  IKR_CUDA(cudaGetLastError());
+}
+
 // plane layout [iz][iy][ix] (summed over ngroups partial planes) -> C order
 // [ix][iy][iz]; tiles of 32 (ix) x 32 (iz) per fixed iy.
 __global__ void k_planes_to_c(const double* __restrict__ part, int ngroups, int Nx, int Ny, int Nz,

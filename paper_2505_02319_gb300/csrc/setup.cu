@@ -392,28 +392,29 @@ void set_eigenpairs(ikr_ctx* c, const ikr_eigenpairs* eig) {
   c->d_psir32.reserve((size_t)S * c->Ng);
   to_fp32(c, c->d_psir.p, (size_t)S * c->Ng, c->d_psir32.p);
   // density rho = sum_k w_k sum_n f_nk |F^-1 phi_nk|^2 and K^xc[rho]
-  std::vector<double> wf(S), ones(S, 1.0);
+  std::vector<double> wf(S);
   for (int s = 0; s < S; ++s) wf[s] = w_o[s] * f_o[s];
-  DBuf<double> d_wf, d_ones;
+  DBuf<double> d_wf;
   upload(d_wf, wf, st);
-  upload(d_ones, ones, st);
   c->d_rho.reserve(c->Ng);
   c->d_kxc.reserve(c->Ng);
   launch_density<double>(c, S, c->d_b1phi.p, nullptr, nullptr, d_wf.p, c->d_rho.p, 1.0 / c->volume);
   exchange_kernel(c);
-  // ||F_k^-1 Phi_k||_{2,inf} per k-point
+  // ||F_k^-1 Phi_k||_{2,inf} and ||Re F_k^-1 Phi_k||_{2,inf} per k-point (largest
+  // row norm over grid points; F^-1 phi = psi / sqrt|Omega| for the unnormalised
+  // syntheses psi of the cached planes)
   c->ws.grid1.reserve(c->Ng);
-  c->ws.scal.reserve(16);
+  c->ws.grid2.reserve(c->Ng);
+  c->ws.scal.reserve(64);
   for (int ik = 0; ik < nk; ++ik) {
-    const size_t o = (size_t)off[ik] * c->N[2] * c->ncp;
-    launch_density<double>(c, noccs[ik], c->d_b1phi.p + o, nullptr, nullptr, d_ones.p, c->ws.grid1.p,
-                           1.0 / c->volume);
+    orbital_sq_sums(c, c->d_psir.p + (size_t)off[ik] * c->Ng, noccs[ik], c->ws.grid1.p, c->ws.grid2.p);
     grid_max(c, c->ws.grid1.p, c->Ng, c->ws.scal.p);
-    double mx = 0;
-    IKR_CUDA(cudaMemcpyAsync(&mx, c->ws.scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    grid_max(c, c->ws.grid2.p, c->Ng, c->ws.scal.p + 1);
+    double mx[2] = {0, 0};
+    IKR_CUDA(cudaMemcpyAsync(mx, c->ws.scal.p, sizeof(mx), cudaMemcpyDeviceToHost, st));
     IKR_CUDA(cudaStreamSynchronize(st));
-    c->k[ik].rownorm = std::sqrt(mx);
-    c->k[ik].rownorm_re = std::sqrt(mx);
+    c->k[ik].rownorm = std::sqrt(mx[0] / c->volume);
+    c->k[ik].rownorm_re = std::sqrt(mx[1] / c->volume);
   }
   IKR_CUDA(cudaStreamSynchronize(st));
   c->have_gs = true;

@@ -131,3 +131,44 @@ def test_mixed_precision_reaches_tau(name):
     xm, _ = ctx.solve_response(dev(b), tau=1e-8, strategy="bal", precision="mixed")
     xd, _ = ctx.solve_response(dev(b), tau=1e-8, strategy="bal", precision="fp64")
     assert true_res(xm) <= 2.0 * true_res(xd) + 1e-9
+
+
+@pytest.mark.parametrize("strategy", ["agr", "bal", "grt", "D10", "D100", "D10n", "grt_exact"])
+def test_strategies(strategy):
+    """Every tolerance rule of Table strategies (k-form Table strategies_k)
+    drives Algorithm 1 to ||r~|| <= tau/3; the smallest CG tolerance of the
+    solve is the oracle's rule at the first step (s = 1, ||r~_0|| = ||b||)."""
+    from oracle import gmres, response
+    from workloads import perturbation
+    name = "tiny_ortho_k"
+    s, gs, ctx = system(name), oracle_state(name), context(name)
+    b = response.chi0(gs, perturbation(s))
+    b /= np.linalg.norm(b)
+    tau, m = 1e-8, 10
+    x, rep = ctx.solve_response(dev(b), tau=tau, strategy=strategy, m=m)
+    r = rep[0]
+    assert r["status"] == 0 and r["est_residual"] <= tau / 3
+    true = np.linalg.norm(b - response.dielectric(gs, x.cpu().numpy().reshape(s.dims)))
+    assert true <= (tau if strategy == "grt_exact" else 100 * tau)
+    if strategy in ("agr", "bal", "D10", "D100", "D10n"):
+        first = gmres.cg_tolerances(gs, strategy, tau, 1, m, 1.0, 1.0, 1.0, 1.0)
+        assert abs(r["min_cg_tol"] - first.min()) <= 1e-12 * first.min()
+
+
+def test_kerker_preconditioned_solve():
+    """Left Kerker preconditioning (eq. precond_dyson): the solution of
+    T E x = T b is the solution of E x = b (T is invertible, Lemma
+    kerker_properties); the preconditioned residual meets tau."""
+    from oracle import gmres, response
+    from workloads import perturbation
+    name = "tiny_metal"
+    s, gs, ctx = system(name), oracle_state(name), context(name)
+    b = response.chi0(gs, perturbation(s))
+    b /= np.linalg.norm(b)
+    alpha = 0.8
+    x, rep = ctx.solve_response(dev(b), tau=1e-11, strategy="bal", kerker_alpha=alpha)
+    x = x.cpu().numpy().reshape(s.dims)
+    r = b - response.dielectric(gs, x)
+    assert np.linalg.norm(response.kerker(r, gs.lattice, gs.dims, alpha)) <= 1e-10
+    ref, _ = gmres.gmres(lambda v: response.dielectric(gs, v), b, tol=1e-13, m=30)
+    assert rel(x, ref) < 1e-8
