@@ -167,7 +167,7 @@ def run_ours(args, rank, world, local_rank):
     # timed steps: the dominant class is timed live with CUDA events on the stream
     clocks = Clocks(local_rank)
     times = []
-    ctx.profile_start(timed=(dominant,))
+    ctx.profile_start(timed=("plane",))
     clocks.start()
     for _ in range(args.steps):
         flush.fill_(1.0)                                  # L2 flush between timed steps
@@ -228,13 +228,11 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         barrier()
         e2e_times.append(e0.elapsed_time(e1) / 1e3)
-    # roofline of the dominant kernel class
+    # roofline of the plane kernel (the dominant class of the solve)
     g = ctx.fft_geometry()
     geom = (s.dims[0], s.dims[1], s.dims[2], g["ncols"], g["nxa"])
     peaks, src = measured_peaks()
-    d = prof[dominant]
-    avg_ms = d["ms"] / max(d["timed_calls"], 1)
-    roof = roofline(dominant, d, avg_ms, geom, rep, peaks, src, ctx)
+    roof = roofline(prof["plane"], geom, peaks)
     value = t_max / args.steps
     out = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -253,7 +251,9 @@ def run_ours(args, rank, world, local_rank):
                   "true_residual": true_res, "step_times_s": times},
         "fp64": fp64,
         "speedup_vs_fp64": (fp64["time_s"] / value) if fp64 else None,
-        "kernel_ms_one_solve": {k: round(v["ms"], 3) for k, v in shares.items()},
+        "kernel_ms_one_solve": {k: {"fp32": round(v["ms_fp32"], 3), "fp64": round(v["ms_fp64"], 3)}
+                                for k, v in shares.items()},
+        "dominant_class": dominant,
         "setup_s": setup_s,
     }
     if rank == 0:
@@ -263,28 +263,42 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-def roofline(name, d, avg_ms, geom, rep, peaks, src, ctx):
-    """Achieved = algorithmic work per launch / average launch duration."""
-    units = d.get("units", 0)
-    calls = max(d["timed_calls"], 1)
-    if name == "plane" and units:
-        # mixed path: FP32 and FP64 plane launches; account each unit at its precision
-        u32, u64 = d.get("units_fp32", units), d.get("units_fp64", 0)
-        b32, f32 = plane_pass_work(geom, 4)
-        b64, f64 = plane_pass_work(geom, 8)
-        flops = (u32 * f32 + u64 * f64) / calls
-        byts = (u32 * b32 + u64 * b64) / calls
-        tfl = flops / (avg_ms * 1e-3) / 1e12
-        # FP32 peak derived from unit counts and clocks: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
-        peak = 152 * 128 * 2 * 2.07e9 / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": tfl, "peak": peak, "unit": "TFLOP/s",
-                "frac": tfl / peak, "traffic": None, "peak_source": "derived (FP32 lanes x clock)",
-                "hbm_gbs": byts / (avg_ms * 1e-3) / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
-                "hbm_frac": byts / (avg_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                "algorithmic_bytes_per_launch": byts, "algorithmic_flops_per_launch": flops,
-                "avg_launch_ms": avg_ms, "units_per_launch": units / calls}
-    return {"kernel": name, "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": None, "traffic": None, "avg_launch_ms": avg_ms}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flops x max SM clock
+FP64_PEAK_TFLOPS = 1.20                              # FMA-chain probe on this machine's GB300
+
+
+def roofline(d, geom, peaks):
+    """Roofline of the plane kernel (the H_k pass of the Sternheimer CG), from
+    the library's CUDA events over the timed steps: achieved = algorithmic
+    flops of the units (system-plane passes) the launches processed / their
+    summed duration, separately for the FP32 (CG) and FP64 (right-hand side,
+    defect-correction residual) launches."""
+    b32, f32 = plane_pass_work(geom, 4)
+    b64, f64 = plane_pass_work(geom, 8)
+    out = None
+    if d["ms_fp32"] > 0 and d["units_fp32"]:
+        t = d["ms_fp32"] * 1e-3
+        calls = max(d["calls_fp32"], 1)
+        tfl = d["units_fp32"] * f32 / t / 1e12
+        gbs = d["units_fp32"] * b32 / t / 1e9
+        out = {"kernel": "k_plane_t<float,48,48> (H_k plane pass, FP32 CG)", "bound": "alu",
+               "achieved": tfl, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tfl / FP32_PEAK_TFLOPS,
+               "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+               "avg_launch_ms": d["ms_fp32"] / calls, "units_per_launch": d["units_fp32"] / calls,
+               "algorithmic_flops_per_unit": f32, "algorithmic_bytes_per_unit": b32,
+               "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / peaks["hbm_gbs"]}
+    if d["ms_fp64"] > 0 and d["units_fp64"]:
+        t = d["ms_fp64"] * 1e-3
+        tfl = d["units_fp64"] * f64 / t / 1e12
+        r64 = {"kernel": "k_plane<double> (H_k plane pass, FP64)", "bound": "alu", "achieved": tfl,
+               "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tfl / FP64_PEAK_TFLOPS,
+               "avg_launch_ms": d["ms_fp64"] / max(d["calls_fp64"], 1),
+               "units_per_launch": d["units_fp64"] / max(d["calls_fp64"], 1)}
+        if out is None:
+            out = r64
+        else:
+            out["fp64_launches"] = r64
+    return out
 
 
 # ------------------------------------------------------------ CPU baseline --

@@ -254,6 +254,8 @@ typedef struct {
   double ms;                   /* summed event time of those calls */
   long long units_fp32;        /* systems processed by FP32 launches of the class */
   long long units_fp64;        /* systems processed by FP64 launches of the class */
+  double ms_fp32, ms_fp64;     /* event time split by the precision of the calls */
+  long long timed_calls_fp32, timed_calls_fp64;
 } ikr_kernel_stat;
 ikr_status ikr_profile_start(ikr_ctx* ctx, unsigned mask);
 int ikr_profile_read(ikr_ctx* ctx, ikr_kernel_stat* out, int cap);

@@ -326,6 +326,7 @@ ikr_status ikr_profile_start(ikr_ctx* c, unsigned mask) {
     c->prof.units32[i] = 0;
     c->prof.units64[i] = 0;
     c->prof.used[i] = 0;
+    c->prof.used[kNumKid + i] = 0;
   }
   c->prof.mask = mask;
   return IKR_OK;
@@ -340,14 +341,23 @@ int ikr_profile_read(ikr_ctx* c, ikr_kernel_stat* out, int cap) {
   for (int i = 0; i < n && out; ++i) {
     out[i].name = names[i];
     out[i].launches = c->prof.launches[i];
-    double ms = 0.0;
-    const size_t pairs = c->prof.used[i] / 2;
-    for (size_t j = 0; j < pairs; ++j) {
-      float t = 0.f;
-      if (cudaEventElapsedTime(&t, c->prof.ev[i][2 * j], c->prof.ev[i][2 * j + 1]) == cudaSuccess) ms += t;
+    double ms[2] = {0.0, 0.0};
+    long long calls[2] = {0, 0};
+    for (int prec = 0; prec < 2; ++prec) {
+      const int id = i + prec * kNumKid;
+      const size_t pairs = c->prof.used[id] / 2;
+      for (size_t j = 0; j < pairs; ++j) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, c->prof.ev[id][2 * j], c->prof.ev[id][2 * j + 1]) == cudaSuccess) ms[prec] += t;
+      }
+      calls[prec] = (long long)pairs;
     }
-    out[i].timed_calls = (long long)pairs;
-    out[i].ms = ms;
+    out[i].timed_calls = calls[0] + calls[1];
+    out[i].ms = ms[0] + ms[1];
+    out[i].ms_fp32 = ms[0];
+    out[i].ms_fp64 = ms[1];
+    out[i].timed_calls_fp32 = calls[0];
+    out[i].timed_calls_fp64 = calls[1];
     out[i].units_fp32 = c->prof.units32[i];
     out[i].units_fp64 = c->prof.units64[i];
   }

@@ -137,8 +137,8 @@ struct Profiler {
   long long launches[kNumKid] = {};
   long long units32[kNumKid] = {};      // work units (systems) launched in FP32
   long long units64[kNumKid] = {};      // ... and in FP64
-  std::vector<cudaEvent_t> ev[kNumKid];
-  size_t used[kNumKid] = {};
+  std::vector<cudaEvent_t> ev[2 * kNumKid];   // [class] FP32 calls, [kNumKid + class] FP64 calls
+  size_t used[2 * kNumKid] = {};
 };
 
 }  // namespace ikr
@@ -218,6 +218,7 @@ struct ProfScope {
     if (fp_bytes == 4) c->prof.units32[id] += units;
     else c->prof.units64[id] += units;
     timed = (c->prof.mask >> id) & 1u;
+    if (fp_bytes != 4) id += kNumKid;
     if (timed) record();
   }
   ~ProfScope() {

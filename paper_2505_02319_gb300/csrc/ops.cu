@@ -21,7 +21,7 @@ template <> struct KC<double> { static constexpr int v = 32; };
 // FP64 32 x 4 (more, shorter CTAs: the FP64 rate of the part makes each
 // CTA long, and the last wave must stay short)
 template <typename R> struct AC;
-template <> struct AC<float> { static constexpr int g = 128, sg = 16; };
+template <> struct AC<float> { static constexpr int g = 64, sg = 8; };
 template <> struct AC<double> { static constexpr int g = 32, sg = 4; };
 constexpr int kTile = 32;    // output tile (m and s) of the Phi^H Y kernel
 
@@ -83,27 +83,157 @@ __global__ void __launch_bounds__(256) k_proj_partial(const C_t<R>* __restrict__
   }
 }
 
+// coef[s][m] = sum over the chunk partials, one warp per (s, m): lanes take
+// chunks lane, lane + 32, ... and a fixed shuffle tree adds them.
 __global__ void k_proj_reduce(const double2* __restrict__ part, int nchunks, int kc, int nsys, int noccmax,
                               const int* __restrict__ sys_k, const int* __restrict__ nocc_k,
                               const int* __restrict__ nb_k, const int* __restrict__ active,
                               double2* __restrict__ coef) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nsys * noccmax) return;
-  const int s = idx / noccmax, m = idx - s * noccmax;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= nsys * noccmax) return;
+  const int s = warp / noccmax, m = warp - s * noccmax;
   if (active && !active[s]) return;
   const int k = sys_k[s];
   if (m >= nocc_k[k]) return;
-  const int nch = (nb_k[k] + kc - 1) / kc;
+  const int nch = min((nb_k[k] + kc - 1) / kc, nchunks);
   double ax = 0, ay = 0;
-  for (int c = 0; c < nch && c < nchunks; ++c) {
+  for (int c = lane; c < nch; c += 32) {
     const double2 v = part[((size_t)c * nsys + s) * noccmax + m];
     ax += v.x;
     ay += v.y;
   }
-  coef[idx] = make_double2(ax, ay);
+  ax = warp_sum(ax);
+  ay = warp_sum(ay);
+  if (lane == 0) coef[warp] = make_double2(ax, ay);
 }
 
+// FP64 variants: one warp per system, lanes over m (Phi^H Y) or over G (Y - Phi C),
+// chunks of 32 plane waves; on this part's FP64 pipe they run faster than the
+// register-tiled FP32 kernels below.
+constexpr int kPC = 32;
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_proj_partial_w(const C_t<R>* __restrict__ phi_all, int ld,
+                                                      const int* __restrict__ phi_off,
+                                                      const int* __restrict__ nocc_k,
+                                                      const int* __restrict__ nb_k,
+                                                      const int* __restrict__ kstart,
+                                                      const int* __restrict__ kcount,
+                                                      const C_t<R>* __restrict__ Y, int ldy,
+                                                      const int* __restrict__ active, int nsys,
+                                                      int noccmax, double2* __restrict__ part) {
+  using C = C_t<R>;
+  const int k = blockIdx.y, chunk = blockIdx.x;
+  const int ns = kcount[k];
+  if (ns == 0) return;
+  const int nocc = nocc_k[k], nb = nb_k[k];
+  const int g0 = chunk * kPC;
+  extern __shared__ unsigned char smem_raw[];
+  C* ph = reinterpret_cast<C*>(smem_raw);           // [g][m], kPC x nocc
+  C* ys = ph + kPC * nocc;                          // per warp kPC entries
+  const C* phi = phi_all + (size_t)phi_off[k] * ld;
+  for (int idx = threadIdx.x; idx < kPC * nocc; idx += blockDim.x) {
+    const int m = idx / kPC, g = idx - m * kPC;
+    ph[g * nocc + m] = (g0 + g < nb) ? phi[(size_t)m * ld + g0 + g] : mk<C>(0, 0);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  C* yw = ys + warp * kPC;
+  const int s0 = kstart[k];
+  for (int sl = warp; sl < ns; sl += nw) {
+    const int s = s0 + sl;
+    if (active && !active[s]) continue;
+    yw[lane] = (g0 + lane < nb) ? Y[(size_t)s * ldy + g0 + lane] : mk<C>(0, 0);
+    __syncwarp();
+    for (int m = lane; m < nocc; m += 32) {
+      R ax = 0, ay = 0;
+#pragma unroll 8
+      for (int g = 0; g < kPC; ++g) {
+        const C p = ph[g * nocc + m], y = yw[g];
+        ax += p.x * y.x + p.y * y.y;
+        ay += p.x * y.y - p.y * y.x;
+      }
+      part[((size_t)chunk * nsys + s) * noccmax + m] = make_double2(ax, ay);
+    }
+    __syncwarp();
+  }
+}
+
+
 // out[s][G] = alpha * in[s][G] + beta * sum_m Phi_k[m][G] coef[s][m]
+// optionally dpart[s][chunk] = sum_{G in chunk} Re(conj(dv[s][G]) out[s][G]).
+template <typename R>
+__global__ void __launch_bounds__(256) k_proj_apply_w(const C_t<R>* __restrict__ phi_all, int ld,
+                                                    const int* __restrict__ phi_off,
+                                                    const int* __restrict__ nocc_k,
+                                                    const int* __restrict__ nb_k,
+                                                    const int* __restrict__ kstart,
+                                                    const int* __restrict__ kcount,
+                                                    const double2* __restrict__ coef, int noccmax,
+                                                    const C_t<R>* in, R alpha, R beta,
+                                                    C_t<R>* out, int ldy,
+                                                    const C_t<R>* __restrict__ dv,
+                                                    double* __restrict__ dpart, int nparts,
+                                                    const int* __restrict__ active) {
+  using C = C_t<R>;
+  const int k = blockIdx.y, chunk = blockIdx.x;
+  const int ns = kcount[k];
+  if (ns == 0) return;
+  const int nocc = nocc_k[k], nb = nb_k[k];
+  const int g0 = chunk * kPC;
+  if (g0 >= nb) {
+    // chunk beyond this k-point's basis: still define the dot partials
+    if (dpart)
+      for (int sl = threadIdx.x; sl < ns; sl += blockDim.x) dpart[(size_t)(kstart[k] + sl) * nparts + chunk] = 0.0;
+    return;
+  }
+  extern __shared__ unsigned char smem_raw[];
+  C* ph = reinterpret_cast<C*>(smem_raw);           // [m][g]
+  const C* phi = phi_all + (size_t)phi_off[k] * ld;
+  for (int idx = threadIdx.x; idx < kPC * nocc; idx += blockDim.x) {
+    const int m = idx / kPC, g = idx - m * kPC;
+    ph[m * kPC + g] = (g0 + g < nb) ? phi[(size_t)m * ld + g0 + g] : mk<C>(0, 0);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int s0 = kstart[k];
+  for (int sl = warp; sl < ns; sl += nw) {
+    const int s = s0 + sl;
+    if (active && !active[s]) continue;
+    const double2* cf = coef + (size_t)s * noccmax;
+    R ax = 0, ay = 0;
+    for (int m = 0; m < nocc; ++m) {
+      const double2 cd = cf[m];
+      const C p = ph[m * kPC + lane];
+      const R cx = (R)cd.x, cy = (R)cd.y;
+      ax += p.x * cx - p.y * cy;
+      ay += p.x * cy + p.y * cx;
+    }
+    const int g = g0 + lane;
+    double d = 0.0;
+    if (g < nb) {
+      const size_t o = (size_t)s * ldy + g;
+      C v = mk<C>(beta * ax, beta * ay);
+      if (alpha != R(0)) {
+        const C x = in[o];
+        v.x += alpha * x.x;
+        v.y += alpha * x.y;
+      }
+      out[o] = v;
+      if (dv) {
+        const C w = dv[o];
+        d = (double)w.x * v.x + (double)w.y * v.y;
+      }
+    }
+    if (dpart) {
+      d = warp_sum(d);
+      if (lane == 0) dpart[(size_t)s * nparts + chunk] = d;
+    }
+  }
+}
+
+
+// FP32: // out[s][G] = alpha * in[s][G] + beta * sum_m Phi_k[m][G] coef[s][m]
 // optionally dpart[s][chunk] = sum_{G in chunk} Re(conj(dv[s][G]) out[s][G]).
 // CTA: kAC plane waves of one k-point; thread (g, group) keeps the sums of
 // kSG systems in registers while m runs, coef of the k-point in shared memory.
@@ -153,13 +283,21 @@ __global__ void __launch_bounds__(256) k_proj_apply(const C_t<R>* __restrict__ p
 #pragma unroll
     for (int j = 0; j < kSG; ++j) ax[j] = ay[j] = R(0);
     const C* cg = cf + grp * kSG * nocc;
-    for (int m = 0; m < nocc; ++m) {
-      const C p = gin ? phi[(size_t)m * ld + g] : mk<C>(0, 0);
+    for (int m0 = 0; m0 < nocc; m0 += 16) {
+      // the next 16 orbitals at this G are loaded together before use
+      C p[16];
 #pragma unroll
-      for (int j = 0; j < kSG; ++j) {
-        const C c = cg[j * nocc + m];
-        ax[j] += p.x * c.x - p.y * c.y;
-        ay[j] += p.x * c.y + p.y * c.x;
+      for (int i = 0; i < 16; ++i) p[i] = (gin && m0 + i < nocc) ? phi[(size_t)(m0 + i) * ld + g] : mk<C>(0, 0);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (m0 + i < nocc) {
+#pragma unroll
+          for (int j = 0; j < kSG; ++j) {
+            const C c = cg[j * nocc + m0 + i];
+            ax[j] += p[i].x * c.x - p[i].y * c.y;
+            ay[j] += p[i].x * c.y + p[i].y * c.x;
+          }
+        }
       }
     }
 #pragma unroll
@@ -606,7 +744,7 @@ static void set_smem_attr(const void* f, size_t bytes) {
 }
 
 int proj_chunks(ikr_ctx* c, int fp_bytes) {
-  const int g = fp_bytes == 4 ? AC<float>::g : AC<double>::g;
+  const int g = fp_bytes == 4 ? AC<float>::g : kPC;
   return (c->ld + g - 1) / g;
 }
 int proj_chunks(ikr_ctx* c) { return std::max(proj_chunks(c, 4), proj_chunks(c, 8)); }
@@ -615,6 +753,24 @@ int cg_chunks(ikr_ctx* c) { return (c->ld + kEC - 1) / kEC; }
 template <typename R>
 void proj_coef(ikr_ctx* c, const SysList& L, const C_t<R>* Y, int ldy, const int* active, double2* coef) {
   ProfScope ps(c, kKidProjCoef, 2, L.n, (int)sizeof(R));
+  if (sizeof(R) == 8) {
+    const int nch = (c->ld + kPC - 1) / kPC;
+    const int nm = c->noccmax;
+    c->ws.cpart.reserve((size_t)nch * L.n * nm * 2);
+    double2* part = reinterpret_cast<double2*>(c->ws.cpart.p);
+    const size_t smem = sizeof(C_t<R>) * (kPC * nm + 8 * kPC);
+    set_smem_attr((const void*)k_proj_partial_w<R>, smem);
+    dim3 grid(nch, (unsigned)c->k.size());
+    k_proj_partial_w<R><<<grid, 256, smem, c->stream>>>(phi_ptr<R>(c), c->ld, c->d_phi_off.p, c->d_nocc.p,
+                                                         c->d_nb.p, L.d_kstart.p, L.d_kcount.p, Y, ldy, active,
+                                                         L.n, nm, part);
+    IKR_CUDA(cudaGetLastError());
+    const long long threads = 32LL * L.n * nm;
+    k_proj_reduce<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(part, nch, kPC, L.n, nm, L.d_k.p,
+                                                                            c->d_nocc.p, c->d_nb.p, active, coef);
+    IKR_CUDA(cudaGetLastError());
+    return;
+  }
   const int kc = KC<R>::v;
   const int nch = (c->ld + kc - 1) / kc;
   const int nm = c->noccmax;
@@ -625,9 +781,9 @@ void proj_coef(ikr_ctx* c, const SysList& L, const C_t<R>* Y, int ldy, const int
                                                   c->d_nb.p, L.d_kstart.p, L.d_kcount.p, Y, ldy,
                                                   active, L.n, nm, part);
   IKR_CUDA(cudaGetLastError());
-  const int tot = L.n * nm;
-  k_proj_reduce<<<(tot + 255) / 256, 256, 0, c->stream>>>(part, nch, kc, L.n, nm, L.d_k.p, c->d_nocc.p,
-                                                          c->d_nb.p, active, coef);
+  const long long threads = 32LL * L.n * nm;
+  k_proj_reduce<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(part, nch, kc, L.n, nm, L.d_k.p,
+                                                                          c->d_nocc.p, c->d_nb.p, active, coef);
   IKR_CUDA(cudaGetLastError());
 }
 
@@ -635,6 +791,17 @@ template <typename R>
 void proj_apply(ikr_ctx* c, const SysList& L, const double2* coef, const C_t<R>* in, R alpha, R beta,
                 C_t<R>* out, int ldy, const C_t<R>* dv, double* dpart, const int* active) {
   ProfScope ps(c, kKidProjApply, 1, L.n, (int)sizeof(R));
+  if (sizeof(R) == 8) {
+    const int nch = proj_chunks(c, 8);
+    const size_t smem = sizeof(C_t<R>) * (kPC * c->noccmax);
+    set_smem_attr((const void*)k_proj_apply_w<R>, smem);
+    dim3 grid(nch, (unsigned)c->k.size());
+    k_proj_apply_w<R><<<grid, 256, smem, c->stream>>>(phi_ptr<R>(c), c->ld, c->d_phi_off.p, c->d_nocc.p,
+                                                       c->d_nb.p, L.d_kstart.p, L.d_kcount.p, coef, c->noccmax, in,
+                                                       alpha, beta, out, ldy, dv, dpart, nch, active);
+    IKR_CUDA(cudaGetLastError());
+    return;
+  }
   const int nch = proj_chunks(c, (int)sizeof(R));
   const size_t smem = sizeof(C_t<R>) * (256 / AC<R>::g * AC<R>::sg * std::max(c->noccmax, 1));
   set_smem_attr((const void*)k_proj_apply<R>, smem);

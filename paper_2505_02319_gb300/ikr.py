@@ -66,7 +66,9 @@ class SolveOpts(ct.Structure):
 
 class KernelStat(ct.Structure):
     _fields_ = [("name", ct.c_char_p), ("launches", ct.c_longlong), ("timed_calls", ct.c_longlong),
-                ("ms", ct.c_double), ("units_fp32", ct.c_longlong), ("units_fp64", ct.c_longlong)]
+                ("ms", ct.c_double), ("units_fp32", ct.c_longlong), ("units_fp64", ct.c_longlong),
+                ("ms_fp32", ct.c_double), ("ms_fp64", ct.c_double), ("timed_calls_fp32", ct.c_longlong),
+                ("timed_calls_fp64", ct.c_longlong)]
 
 
 def _load():
@@ -216,7 +218,10 @@ class Context:
         return {arr[i].name.decode(): dict(launches=arr[i].launches, timed_calls=arr[i].timed_calls,
                                            ms=arr[i].ms, units_fp32=arr[i].units_fp32,
                                            units_fp64=arr[i].units_fp64,
-                                           units=arr[i].units_fp32 + arr[i].units_fp64) for i in range(n)}
+                                           units=arr[i].units_fp32 + arr[i].units_fp64,
+                                           ms_fp32=arr[i].ms_fp32, ms_fp64=arr[i].ms_fp64,
+                                           calls_fp32=arr[i].timed_calls_fp32,
+                                           calls_fp64=arr[i].timed_calls_fp64) for i in range(n)}
 
     def fft_geometry(self):
         g = (ct.c_int * 5)()
