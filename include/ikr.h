@@ -263,6 +263,20 @@ int ikr_profile_read(ikr_ctx* ctx, ikr_kernel_stat* out, int cap);
  * of sphere columns (j1, j2) transformed along z, and of active x positions. */
 ikr_status ikr_fft_geometry(const ikr_ctx* ctx, int* out);
 
+/* The dielectric operator 1 - K chi0, the transpose of E for the symmetric chi0
+ * and K (Sec. 2.2): E^T v = v - ||v|| K chi0(v/||v||).  It serves the adjoint
+ * (backward) solve of a loss of drho.  Arguments as ikr_apply_dielectric. */
+ikr_status ikr_apply_dielectric_adjoint(ikr_ctx* ctx, const double* v, double* Etv, const double* tol,
+                                        int precision, ikr_report* report, cudaStream_t stream);
+
+/* Solves E^T lambda = g by Algorithm 1 (the adjoint of ikr_solve_response: for
+ * a loss L(drho) with drho = E^-1 chi0 dV, dL/d dV = chi0 E^-T dL/d drho).  The
+ * tolerance rules are those of ikr_solve_response with ||K v_i|| replaced by
+ * the bound ||K|| <= max 4 pi/|G|^2 + max |K^xc| (the Sternheimer error enters
+ * through K after chi0).  Arguments as ikr_solve_response. */
+ikr_status ikr_solve_response_adjoint(ikr_ctx* ctx, int nrhs, const double* g, double* lambda,
+                                      const ikr_solve_opts* opts, ikr_report* report, cudaStream_t stream);
+
 /* Frees the context and all device memory it owns.  NULL is allowed. */
 void ikr_destroy(ikr_ctx* ctx);
 

@@ -144,6 +144,12 @@ def dielectric(gs, v: np.ndarray, kxc=None) -> np.ndarray:
     return v - nrm * chi0(gs, Kv / nrm)
 
 
+def dielectric_adjoint(gs, v: np.ndarray, kxc=None) -> np.ndarray:
+    """E^T v = v - K chi0 v: the dielectric operator, the transpose of E = 1 - chi0 K
+    for symmetric chi0 and K (Sec. 2.2)."""
+    return v - apply_K(chi0(gs, v), gs, kxc)
+
+
 def dense_operator(apply, dims) -> np.ndarray:
     """Columns apply(e_j) for every grid point (tiny grids only)."""
     ng = int(np.prod(dims))

@@ -59,6 +59,33 @@ double wall_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+ikr_status solve_any(ikr_ctx* c, int nrhs, const double* b, double* x, const ikr_solve_opts* opts,
+                            ikr_report* report, cudaStream_t stream, bool adjoint) {
+  if (!c) return IKR_ERR_ARG;
+  c->stream = stream;
+  ikr_status worst = IKR_OK;
+  ikr_status s = guarded(c, [&] {
+    IKR_REQUIRE(nrhs >= 0 && (nrhs == 0 || (b && x)), IKR_ERR_ARG, "invalid right-hand sides");
+    ikr_solve_opts o;
+    if (opts) o = *opts; else ikr_default_opts(&o);
+    IKR_REQUIRE(o.strategy >= IKR_AGR && o.strategy <= IKR_FIXED, IKR_ERR_ARG, "unknown strategy");
+    IKR_REQUIRE(o.precision == IKR_FP64 || o.precision == IKR_MIXED, IKR_ERR_ARG, "unknown precision");
+    IKR_REQUIRE(o.cg_maxit >= 1, IKR_ERR_ARG, "cg_maxit must be >= 1");
+    for (int r = 0; r < nrhs; ++r) {
+      ikr_report* rep = report ? report + r : nullptr;
+      try {
+        gmres_solve(c, b + (size_t)r * c->Ng, x + (size_t)r * c->Ng, o, rep, adjoint);
+      } catch (const Error& e) {
+        if (e.status != IKR_ERR_NOCONV && e.status != IKR_ERR_TIMEOUT) throw;
+        c->err = e.what();
+        if (worst == IKR_OK) worst = e.status;
+      }
+    }
+  });
+  if (s != IKR_OK) return s;
+  return worst;
+}
+
 }  // namespace
 
 extern "C" {
@@ -269,29 +296,32 @@ ikr_status ikr_apply_dielectric(ikr_ctx* c, const double* v, double* Ev, const d
 
 ikr_status ikr_solve_response(ikr_ctx* c, int nrhs, const double* b, double* x, const ikr_solve_opts* opts,
                               ikr_report* report, cudaStream_t stream) {
+  return solve_any(c, nrhs, b, x, opts, report, stream, false);
+}
+
+ikr_status ikr_apply_dielectric_adjoint(ikr_ctx* c, const double* v, double* Ev, const double* tol, int precision,
+                                        ikr_report* report, cudaStream_t stream) {
   if (!c) return IKR_ERR_ARG;
   c->stream = stream;
-  ikr_status worst = IKR_OK;
+  RunStats rs;
+  const double t0 = wall_ms();
   ikr_status s = guarded(c, [&] {
-    IKR_REQUIRE(nrhs >= 0 && (nrhs == 0 || (b && x)), IKR_ERR_ARG, "invalid right-hand sides");
-    ikr_solve_opts o;
-    if (opts) o = *opts; else ikr_default_opts(&o);
-    IKR_REQUIRE(o.strategy >= IKR_AGR && o.strategy <= IKR_FIXED, IKR_ERR_ARG, "unknown strategy");
-    IKR_REQUIRE(o.precision == IKR_FP64 || o.precision == IKR_MIXED, IKR_ERR_ARG, "unknown precision");
-    IKR_REQUIRE(o.cg_maxit >= 1, IKR_ERR_ARG, "cg_maxit must be >= 1");
-    for (int r = 0; r < nrhs; ++r) {
-      ikr_report* rep = report ? report + r : nullptr;
-      try {
-        gmres_solve(c, b + (size_t)r * c->Ng, x + (size_t)r * c->Ng, o, rep);
-      } catch (const Error& e) {
-        if (e.status != IKR_ERR_NOCONV && e.status != IKR_ERR_TIMEOUT) throw;
-        c->err = e.what();
-        if (worst == IKR_OK) worst = e.status;
-      }
-    }
+    IKR_REQUIRE(c->have_gs, IKR_ERR_STATE, "the ground state is not set");
+    IKR_REQUIRE(v && Ev && v != Ev, IKR_ERR_ARG, "v and Ev must be distinct device pointers");
+    const std::vector<double> t = tol_vector(c, tol);
+    dielectric_adjoint_core(c, v, Ev, [&](double) { return t; }, 1000, precision, rs);
+    IKR_CUDA(cudaStreamSynchronize(stream));
   });
-  if (s != IKR_OK) return s;
-  return worst;
+  fill_report(report, rs, wall_ms() - t0);
+  if (report) report->status = s;
+  if (s == IKR_OK && rs.cg_numeric) s = IKR_ERR_NUMERIC;
+  if (s == IKR_OK && rs.cg_noconv) s = IKR_ERR_NOCONV;
+  return s;
+}
+
+ikr_status ikr_solve_response_adjoint(ikr_ctx* c, int nrhs, const double* g, double* lambda,
+                                      const ikr_solve_opts* opts, ikr_report* report, cudaStream_t stream) {
+  return solve_any(c, nrhs, g, lambda, opts, report, stream, true);
 }
 
 void ikr_destroy(ikr_ctx* c) {

@@ -174,6 +174,7 @@ struct ikr_ctx {
   ikr::DBuf<int> d_nb;          // nk basis sizes
   ikr::DBuf<double> d_coul;     // 4 pi/|G|^2 / Ng (G = 0 -> 0), C order
   ikr::DBuf<double> d_G2;       // |G|^2 of every grid frequency, C order
+  double knorm = 0.0;           // ||K|| = max_G 4 pi/|G|^2 + max_r |K^xc(r)| (bound, set with the ground state)
   // ground state
   bool have_gs = false;
   double eF = 0.0;

@@ -400,6 +400,20 @@ void set_eigenpairs(ikr_ctx* c, const ikr_eigenpairs* eig) {
   c->d_kxc.reserve(c->Ng);
   launch_density<double>(c, S, c->d_b1phi.p, nullptr, nullptr, d_wf.p, c->d_rho.p, 1.0 / c->volume);
   exchange_kernel(c);
+  {
+    // ||K|| <= max 4 pi/|G|^2 + max |K^xc| (K^H and K^xc symmetric; K^xc <= 0)
+    std::vector<double> kx(c->Ng);
+    IKR_CUDA(cudaMemcpyAsync(kx.data(), c->d_kxc.p, sizeof(double) * c->Ng, cudaMemcpyDeviceToHost, st));
+    IKR_CUDA(cudaStreamSynchronize(st));
+    double kmax = 0.0, g2min = 1e300;
+    for (double v : kx) kmax = std::max(kmax, std::fabs(v));
+    const double* B = c->recip;
+    for (int i = 0; i < 3; ++i) {
+      const double bi2 = B[i] * B[i] + B[3 + i] * B[3 + i] + B[6 + i] * B[6 + i];
+      g2min = std::min(g2min, bi2);
+    }
+    c->knorm = 4.0 * M_PI / g2min + kmax;
+  }
   // ||F_k^-1 Phi_k||_{2,inf} and ||Re F_k^-1 Phi_k||_{2,inf} per k-point (largest
   // row norm over grid points; F^-1 phi = psi / sqrt|Omega| for the unnormalised
   // syntheses psi of the cached planes)

@@ -283,6 +283,38 @@ void dielectric_core(ikr_ctx* c, const double* v, double* Ev, const TolFn& tol_f
   rs.e_applies++;
 }
 
+// E^T v = v - K chi0 v = v - ||v|| K chi0(v / ||v||): the dielectric operator
+// 1 - K chi0, the transpose of E for symmetric chi0 and K (Sec. 2.2).  The
+// Sternheimer error enters through K after chi0, so the error bound of Lemma
+// cgtol_E holds with ||K v_i|| replaced by ||K|| ||v_i||; tol_fn receives ||K||.
+void dielectric_adjoint_core(ikr_ctx* c, const double* v, double* Ev, const TolFn& tol_fn, int maxit,
+                             int precision, RunStats& rs, double allowed) {
+  Workspace& w = c->ws;
+  ensure_workspace(c, c->occ.n);
+  double* nrm = w.scal.p;          // {||v||^2, ||v||, 1/||v||}
+  norm2(c, v, nrm);
+  double h[3];
+  IKR_CUDA(cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  IKR_CUDA(cudaStreamSynchronize(c->stream));
+  if (!(h[1] > 0.0)) {
+    IKR_CUDA(cudaMemcpyAsync(Ev, v, sizeof(double) * c->Ng, cudaMemcpyDeviceToDevice, c->stream));
+    return;
+  }
+  IKR_REQUIRE(std::isfinite(h[1]), IKR_ERR_NUMERIC, "non-finite ||v||");
+  rs.kv_norm = c->knorm;
+  const std::vector<double> tol = tol_fn(c->knorm);
+  const bool fp32 = precision == IKR_MIXED && allowed > 0.0 && rs.last_dEv > 0.0 &&
+                    10.0 * kFp32Rel * rs.last_dEv <= allowed;
+  chi0_core(c, v, nrm + 2, tol, maxit, precision, w.grid3.p, rs, fp32);
+  apply_K(c, w.grid3.p, w.grid2.p, w.scal.p + 48);          // K chi0(v/||v||)
+  axpy(c, v, w.grid2.p, -1.0, nrm + 1, Ev);
+  double d3[3];
+  IKR_CUDA(cudaMemcpyAsync(d3, w.scal.p + 48, sizeof(d3), cudaMemcpyDeviceToHost, c->stream));
+  IKR_CUDA(cudaStreamSynchronize(c->stream));
+  rs.last_dEv = h[1] * d3[1];
+  rs.e_applies++;
+}
+
 // ---------------------------------------------------------- Algorithm 1 --
 
 namespace {
@@ -359,7 +391,7 @@ std::vector<double> strategy_tolerances(ikr_ctx* c, const ikr_solve_opts& o, int
   return t;
 }
 
-void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o, ikr_report* rep) {
+void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o, ikr_report* rep, bool adjoint) {
   IKR_REQUIRE(c->have_gs, IKR_ERR_STATE, "the ground state is not set");
   IKR_REQUIRE(o.tau > 0 && o.m >= 1 && o.m <= 200, IKR_ERR_ARG, "invalid tau or m");
   const double t0 = now_ms();
@@ -411,7 +443,8 @@ void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o
         track(t);
         return t;
       };
-      dielectric_core(c, x, wv, tf, o.cg_maxit, o.precision, rs, o.tau / 3.0);
+      if (adjoint) dielectric_adjoint_core(c, x, wv, tf, o.cg_maxit, o.precision, rs, o.tau / 3.0);
+      else dielectric_core(c, x, wv, tf, o.cg_maxit, o.precision, rs, o.tau / 3.0);
       if (kerker) {
         axpy(c, b, wv, -1.0, nullptr, r0);
         apply_kerker(c, r0, r0, o.kerker_alpha);
@@ -448,8 +481,12 @@ void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o
         track(t);
         return t;
       };
-      dielectric_core(c, V + (size_t)(i - 1) * Ng, wv, tf, o.cg_maxit, o.precision, rs,
-                      s / (3.0 * m) * o.tau / rprev);
+      if (adjoint)
+        dielectric_adjoint_core(c, V + (size_t)(i - 1) * Ng, wv, tf, o.cg_maxit, o.precision, rs,
+                                s / (3.0 * m) * o.tau / rprev);
+      else
+        dielectric_core(c, V + (size_t)(i - 1) * Ng, wv, tf, o.cg_maxit, o.precision, rs,
+                        s / (3.0 * m) * o.tau / rprev);
       if (kerker) apply_kerker(c, wv, wv, o.kerker_alpha);
       steps++;
       // classical Gram-Schmidt with one reorthogonalisation pass (FP64)

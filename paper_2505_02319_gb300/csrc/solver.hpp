@@ -50,6 +50,9 @@ void dielectric_core(ikr_ctx* c, const double* v, double* Ev, const TolFn& tol_f
 std::vector<double> strategy_tolerances(ikr_ctx* c, const ikr_solve_opts& o, int i, double s, double rprev,
                                         double kv_norm, double b_norm);
 void hamiltonian_noalloc(ikr_ctx* c, int k, const double2* psi, double2* hpsi, int nvec);
-void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o, ikr_report* rep);
+void dielectric_adjoint_core(ikr_ctx* c, const double* v, double* Ev, const TolFn& tol_fn, int maxit,
+                             int precision, RunStats& rs, double allowed = 0.0);
+void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o, ikr_report* rep,
+                 bool adjoint = false);
 
 }  // namespace ikr

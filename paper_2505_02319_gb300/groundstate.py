@@ -45,4 +45,5 @@ def context_for(system, nbands=None) -> ikr.Context:
     ctx.set_eigenpairs(ev, vecs)
     ctx.nbands = nb
     ctx.ngrid = int(np.prod(system.dims))
+    ctx.groundstate_nsys = int(ctx.groundstate_info(nb, ctx.ngrid)["nocc"].sum())
     return ctx

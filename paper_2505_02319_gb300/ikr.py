@@ -91,6 +91,8 @@ def _load():
         "ikr_apply_chi0": (I, [P, P, P, ct.POINTER(D), I, ct.POINTER(Report), S]),
         "ikr_apply_dielectric": (I, [P, P, P, ct.POINTER(D), I, ct.POINTER(Report), S]),
         "ikr_solve_response": (I, [P, I, P, P, ct.POINTER(SolveOpts), ct.POINTER(Report), S]),
+        "ikr_apply_dielectric_adjoint": (I, [P, P, P, ct.POINTER(D), I, ct.POINTER(Report), S]),
+        "ikr_solve_response_adjoint": (I, [P, I, P, P, ct.POINTER(SolveOpts), ct.POINTER(Report), S]),
         "ikr_destroy": (None, [P]),
         "ikr_last_error": (ct.c_char_p, [P]),
         "ikr_status_string": (ct.c_char_p, [I]),
@@ -298,8 +300,26 @@ class Context:
         self._check(st, allow=(IKR_ERR_NOCONV,))
         return out, rep.as_dict()
 
+    def apply_dielectric_adjoint(self, v, tol=None, precision=FP64):
+        out = torch.empty_like(v)
+        rep = Report()
+        tp = None
+        if tol is not None:
+            tarr, tp = _dbl(tol)
+        st = _LIB.ikr_apply_dielectric_adjoint(self._h, _dptr(v), _dptr(out), tp, precision, ct.byref(rep),
+                                               _stream())
+        self._check(st, allow=(IKR_ERR_NOCONV,))
+        return out, rep.as_dict()
+
+    def solve_response_adjoint(self, g, x0=None, opts=None, history=64, **kw):
+        """Solve E^T lambda = g (the adjoint solve).  Arguments as solve_response."""
+        return self._solve(_LIB.ikr_solve_response_adjoint, g, x0, opts, history, kw)
+
     def solve_response(self, b, x0=None, opts=None, history=64, **kw):
         """Solve E x = b (Algorithm 1).  b: (Ng,) or (nrhs, Ng) float64 CUDA tensor."""
+        return self._solve(_LIB.ikr_solve_response, b, x0, opts, history, kw)
+
+    def _solve(self, fn, b, x0, opts, history, kw):
         o = opts if opts is not None else default_opts(**kw)
         bb = b.reshape(-1, b.shape[-1]) if b.dim() > 1 else b.reshape(1, -1)
         nrhs = bb.shape[0]
@@ -313,8 +333,7 @@ class Context:
         for r in range(nrhs):
             reps[r].history = hists[r].ctypes.data_as(ct.POINTER(ct.c_double))
             reps[r].history_cap = history
-        st = _LIB.ikr_solve_response(self._h, nrhs, _dptr(bb.contiguous()), _dptr(x), ct.byref(o), reps,
-                                     _stream())
+        st = fn(self._h, nrhs, _dptr(bb.contiguous()), _dptr(x), ct.byref(o), reps, _stream())
         self._check(st, allow=(IKR_ERR_NOCONV, IKR_ERR_TIMEOUT))
         out = x.reshape(b.shape)
         return out, [reps[r].as_dict() for r in range(nrhs)]
@@ -356,3 +375,11 @@ def apply_dielectric(ctx, v, tol=None, precision=FP64):
 
 def solve_response(ctx, b, **kw):
     return ctx.solve_response(b, **kw)
+
+
+def apply_dielectric_adjoint(ctx, v, tol=None, precision=FP64):
+    return ctx.apply_dielectric_adjoint(v, tol, precision)
+
+
+def solve_response_adjoint(ctx, g, **kw):
+    return ctx.solve_response_adjoint(g, **kw)

@@ -38,6 +38,15 @@ def test_adjoint_is_the_dielectric_operator(ins):
     assert abs(lhs - rhs) < 1e-12 * abs(lhs)
 
 
+def test_adjoint_function_is_the_transpose(metal):
+    """dielectric_adjoint is the transpose of the dense E (metal, k-points)."""
+    s, gs = metal
+    E = response.dense_operator(lambda v: response.dielectric(gs, v), s.dims)
+    rng = np.random.default_rng(4)
+    v = rng.normal(size=s.dims)
+    np.testing.assert_allclose(response.dielectric_adjoint(gs, v).ravel(), E.T @ v.ravel(), atol=1e-12)
+
+
 @pytest.mark.parametrize("which", ["ins", "metal"])
 def test_gmres_matches_dense_solve(which, ins, metal):
     s, gs = ins if which == "ins" else metal

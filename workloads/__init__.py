@@ -8,8 +8,8 @@ Monkhorst-Pack k-points.  Every quantity the method computes (plane-wave
 spheres, Fourier transforms, Hamiltonians, eigenpairs, occupations, densities,
 kernels, responses) is computed separately by each side.
 """
-from .systems import (System, make_system, perturbation, CONFIGS, TEST_SYSTEMS,
-                      monkhorst_pack, gaussian_sum_on_grid)
+from .systems import (System, make_system, perturbation, response_batch, loss_weights, CONFIGS,
+                      TEST_SYSTEMS, monkhorst_pack, gaussian_sum_on_grid)
 
-__all__ = ["System", "make_system", "perturbation", "CONFIGS", "TEST_SYSTEMS",
-           "monkhorst_pack", "gaussian_sum_on_grid"]
+__all__ = ["System", "make_system", "perturbation", "response_batch", "loss_weights", "CONFIGS",
+           "TEST_SYSTEMS", "monkhorst_pack", "gaussian_sum_on_grid"]

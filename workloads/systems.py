@@ -142,14 +142,48 @@ def make_system(name: str) -> System:
 
 
 def perturbation(system: System, kind: str = "bump", seed: int = 0,
-                 amplitude: float = 0.1, width: float = 1.0) -> np.ndarray:
-    """A seeded local perturbation dV0 on the grid: a periodic Gaussian bump of
-    the given amplitude [Ha] and width [bohr] at a random centre."""
+                 amplitude: float = 0.1, width: float = 1.0, atom: int = 0, axis: int = 0) -> np.ndarray:
+    """A seeded local perturbation dV0 on the grid.
+
+    kind="bump": a periodic Gaussian bump of the given amplitude [Ha] and width
+    [bohr] at a random centre.  kind="displacement": the change of the external
+    potential per unit displacement of pseudo-atom `atom` along Cartesian
+    `axis`, i.e. d/dR_axis of -D exp(-|r - R|^2 / (2 sigma^2)) summed over images,
+    = -D exp(...) (r - R)_axis / sigma^2 (the perturbation of Sec. 4.1.2, where
+    atoms are displaced)."""
     rng = np.random.default_rng(10_000 + seed)
-    if kind != "bump":
-        raise ValueError(kind)
-    c = system.lattice @ rng.random(3)
-    return gaussian_sum_on_grid(system.lattice, system.dims, c[None, :], amplitude, width)
+    if kind == "bump":
+        c = system.lattice @ rng.random(3)
+        return gaussian_sum_on_grid(system.lattice, system.dims, c[None, :], amplitude, width)
+    if kind == "displacement":
+        lattice, dims = system.lattice, system.dims
+        R = system.positions[atom]
+        sig = system.width
+        r = _grid_points(lattice, dims)
+        out = np.zeros(dims)
+        reach = 9.0 * sig
+        nimg = [int(math.ceil(reach / np.linalg.norm(lattice[:, i]))) + 1 for i in range(3)]
+        for n in itertools.product(*[range(-m, m + 1) for m in nimg]):
+            d = r - (R + lattice @ np.array(n, dtype=np.float64))
+            d2 = np.einsum("...i,...i->...", d, d)
+            out += -system.depth * np.exp(-d2 / (2 * sig * sig)) * d[..., axis] / (sig * sig)
+        return out
+    raise ValueError(kind)
+
+
+def response_batch(system: System, n_bumps: int = 16, n_displacements: int = 16) -> np.ndarray:
+    """The differentiated batch of right-hand sides: seeded Gaussian bumps and
+    atom-displacement derivatives of the pseudo-atom potentials, shape (n, N1, N2, N3)."""
+    out = [perturbation(system, "bump", seed=i) for i in range(n_bumps)]
+    natoms = len(system.positions)
+    for j in range(n_displacements):
+        out.append(perturbation(system, "displacement", atom=j % natoms, axis=(j // natoms) % 3))
+    return np.array(out)
+
+
+def loss_weights(system: System, seed: int = 5) -> np.ndarray:
+    """W = diag(U(0.5, 1.5)) on the grid, for the loss ||W drho||^2."""
+    return np.random.default_rng(20_000 + seed).uniform(0.5, 1.5, size=system.dims)
 
 
 # name -> recipe.  "cfg*" follow the five workload descriptions; "tiny*" are
