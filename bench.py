@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
+    p.add_argument("--strategies", action="store_true",
+                   help="also run every tolerance rule once (N_ham, true residual, eta_rel)")
     p.add_argument("--profile-run", action="store_true",
                    help="only setup, warm-up and the timed steps (for ncu); prints no bench line")
     return p.parse_args()
@@ -120,6 +122,40 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest value over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    if dist is None:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def efficiency(r0, r_end, n_ham):
+    """eta = -log10(||r_end|| / ||r_0||) / N_ham (Sec. 4.1.3)."""
+    import math
+    return -math.log10(r_end / r0) / n_ham
+
+
+def strategy_sweep(ctx, b, nsys, tau, m, precision):
+    """Every tolerance rule on the same Dyson equation: N_ham, true residual
+    ||b - E x|| (tight E), eta and eta_rel against D10 (Sec. 4.1.3)."""
+    import numpy as np
+    import torch
+    out = {}
+    r0 = float(torch.linalg.norm(b))
+    for name in ("agr", "bal", "grt", "D10", "D100", "D10n"):
+        x, rep = ctx.solve_response(b, tau=tau, m=m, strategy=name, precision=precision)
+        Ex, _ = ctx.apply_dielectric(x, tol=np.full(nsys, 1e-12))
+        tr = float(torch.linalg.norm(b - Ex))
+        out[name] = {"n_ham": rep[0]["n_ham"], "true_residual": tr, "outer_iters": rep[0]["outer_iters"],
+                     "eta": efficiency(r0, max(tr, 1e-300), rep[0]["n_ham"])}
+    for name in out:
+        out[name]["eta_rel_vs_D10"] = out[name]["eta"] / out["D10"]["eta"]
+    return out
+
+
 # ------------------------------------------------------------------- ours --
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -186,11 +222,7 @@ def run_ours(args, rank, world, local_rank):
     if args.profile_run:
         return
     launches = sum(v["launches"] for v in prof.values())
-    t_local = sum(times)
-    t_tensor = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
-    t_max = float(t_tensor.item())
+    t_max = max_over_ranks(sum(times), dist, device="cuda")
     rep = rep[0]
     # FP64 path, same problem
     fp64 = None
@@ -256,6 +288,8 @@ def run_ours(args, rank, world, local_rank):
         "dominant_class": dominant,
         "setup_s": setup_s,
     }
+    if args.strategies:
+        out["strategies"] = strategy_sweep(ctx, b, nsys, TAU, M, ikr.MIXED)
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(s, rep["e_applies"])
         print(json.dumps(out))
