@@ -85,11 +85,13 @@ __global__ void __launch_bounds__(256) k_z_forward(const C_t<R>* __restrict__ b4
                                                    const C_t<R>* __restrict__ psi,
                                                    const double* __restrict__ shift,
                                                    const R* __restrict__ kin_all,
-                                                   const int* __restrict__ active) {
+                                                   const int* __restrict__ active,
+                                                   double* __restrict__ dpart) {
   using C = C_t<R>;
   const int s = blockIdx.y;
   if (active && !active[s]) return;
   extern __shared__ unsigned char smem_raw[];
+  __shared__ double red[8];
   const int Nz = pz.n, lds = Nz + 1;
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* A = tw + Nz;
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(256) k_z_forward(const C_t<R>* __restrict__ b4
   const C* ps = psi ? psi + (size_t)s * ld : nullptr;
   const R sh = shift ? (R)shift[s] : R(0);
   const R* kin = kin_all ? kin_all + (size_t)k * ldk : nullptr;
+  double dot = 0.0;
   for (int idx = threadIdx.x; idx < LZ * Nz; idx += blockDim.x) {
     const int l = idx / Nz, z = idx - l * Nz;
     const int col = c0 + l;
@@ -124,8 +127,14 @@ __global__ void __launch_bounds__(256) k_z_forward(const C_t<R>* __restrict__ b4
       const C p = ps[i];
       v.x += d * p.x;
       v.y += d * p.y;
+      dot += (double)p.x * v.x + (double)p.y * v.y;
     }
     dst[i] = v;
+  }
+  if (dpart) {
+    // Re <psi, out> over this CTA's plane waves (fixed-order block reduction)
+    dot = block_sum(dot, red);
+    if (threadIdx.x == 0) dpart[(size_t)s * gridDim.x + blockIdx.x] = dot;
   }
 }
 
@@ -464,9 +473,15 @@ void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, 
   IKR_CUDA(cudaGetLastError());
 }
 
+int zf_chunks(ikr_ctx* c) {
+  const int LZ = lines_per_cta(c->N[2]);
+  return (c->nc + LZ - 1) / LZ;
+}
+
 template <typename R>
 void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* out, int ld,
-                      const C_t<R>* psi, const double* shift, bool kinetic, const int* active) {
+                      const C_t<R>* psi, const double* shift, bool kinetic, const int* active,
+                      double* dpart) {
   if (L.n == 0) return;
   ProfScope ps(c, kKidZFwd, 1, active ? c->active_hint : L.n, (int)sizeof(R));
   const int Nz = c->N[2];
@@ -477,7 +492,7 @@ void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* ou
   const R* kin = kinetic ? kin_all_ptr<R>(c) : nullptr;
   k_z_forward<R><<<grid, 256, smem, c->stream>>>(b4, c->nc, c->ncp, L.d_k.p, c->k_colinfo.p,
                                                   c->plan[2], tw_ptr<R>(c, 2), LZ, out, ld, c->ld,
-                                                  psi, shift, kin, active);
+                                                  psi, shift, kin, active, dpart);
   IKR_CUDA(cudaGetLastError());
 }
 
@@ -573,7 +588,7 @@ void full_fft(ikr_ctx* c, double2* data, bool inverse) {
                                 const int*, C_t<R>*, const C_t<R>*);                                \
   template void launch_synth_planes<R>(ikr_ctx*, int, const C_t<R>*, C_t<R>*);                      \
   template void launch_z_forward<R>(ikr_ctx*, const SysList&, const C_t<R>*, C_t<R>*, int,         \
-                                    const C_t<R>*, const double*, bool, const int*);                \
+                                    const C_t<R>*, const double*, bool, const int*, double*);       \
   template void launch_density<R>(ikr_ctx*, int, const C_t<R>*, const C_t<R>*,                     \
                                   const double*, const double*, double*, double, const C_t<R>*);    \
   template void to_plane_layout<R>(ikr_ctx*, const double*, R*, double, const double*);
@@ -606,7 +621,7 @@ void launch_hamiltonian_raw(ikr_ctx* c, int n, const int* d_sysk, const double2*
   IKR_CUDA(cudaGetLastError());
   k_z_forward<double><<<gz, 256, smz, c->stream>>>(b4, c->nc, c->ncp, d_sysk, c->k_colinfo.p, c->plan[2],
                                                    c->d_tw[2].p, LZ, hpsi, ld, c->ld, psi, nullptr,
-                                                   c->d_kin_all.p, nullptr);
+                                                   c->d_kin_all.p, nullptr, nullptr);
   IKR_CUDA(cudaGetLastError());
 }
 

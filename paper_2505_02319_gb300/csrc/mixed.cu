@@ -167,9 +167,7 @@ CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv
     IKR_CUDA(cudaMemcpyAsync(w.val.p, shift.data(), sizeof(double) * n, cudaMemcpyHostToDevice, strm));
     launch_z_inverse<double>(c, L, Xv, ld, act, w.b1.p);
     launch_plane<double>(c, L, w.b1.p, c->d_Vt.p, nullptr, act, w.b4.p);
-    launch_z_forward<double>(c, L, w.b4.p, w.W.p, ld, Xv, w.val.p, true, act);
-    proj_coef<double>(c, L, w.W.p, ld, act, coef);
-    proj_apply<double>(c, L, coef, w.W.p, 1.0, -1.0, w.W.p, ld, nullptr, nullptr, act);
+    launch_z_forward<double>(c, L, w.b4.p, w.W.p, ld, Xv, w.val.p, true, act);   // in range(Q): x is
     {
       ProfScope ps(c, kKidCgVec, 1);
       k_residual<<<egrid, 256, 0, strm>>>(Bv, w.W.p, ld, L.d_k.p, c->d_nb.p, act, w.R.p, w.B32.p);

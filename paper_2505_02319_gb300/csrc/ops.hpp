@@ -27,7 +27,9 @@ bool launch_plane_fast(ikr_ctx* c, int nsys, const C_t<R>* b1, const R* pot, con
                        const int* active, C_t<R>* b4, const C_t<R>* real_in);
 template <typename R>
 void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* out, int ld,
-                      const C_t<R>* psi, const double* shift, bool kinetic, const int* active);
+                      const C_t<R>* psi, const double* shift, bool kinetic, const int* active,
+                      double* dpart = nullptr);
+int zf_chunks(ikr_ctx* c);    // dot partials per system written by launch_z_forward
 template <typename R>
 void launch_density(ikr_ctx* c, int nsys, const C_t<R>* b1phi, const C_t<R>* b1d,
                     const double* coef_a, const double* coef_b, double* out, double scale,

@@ -51,7 +51,7 @@ void ensure_workspace(ikr_ctx* c, int n) {
   w.coef.reserve(2 * nm);
   w.coefM.reserve(2 * nm);
   w.coefP.reserve(2 * nm);
-  const int np = std::max(proj_chunks(c), cg_chunks(c));
+  const int np = std::max(std::max(proj_chunks(c), cg_chunks(c)), zf_chunks(c));
   w.dpart.reserve((size_t)std::max(n, 1) * np);
   w.sys.reserve((size_t)kSysFields * std::max(n, 1));
   w.val.reserve(std::max(n, 1));
@@ -100,10 +100,11 @@ template void hamiltonian<float>(ikr_ctx*, int, const float2*, float2*, int, int
 // ---------------------------------------------------------- Sternheimer CG --
 // Preconditioned CG on A_s = Q_k (H_k - eps_s) Q_k for every system s of L
 // (eq. discretised_sternheimer), x0 = 0, >= 1 iteration, absolute stopping
-// rule ||r|| <= tol_s.  Residual, search direction and preconditioned
-// residual are re-projected by Q every iteration (Remark
-// rmk:sternheimer_solution).  Preconditioner: z = Q diag(1/(kappa_s +
-// |k+G|^2/2)) r.  B must be in range(Q).
+// rule ||r|| <= tol_s.  The preconditioned residual z is re-projected by Q
+// every iteration, which keeps the search direction p and the iterate x in
+// range(Q) (Remark rmk:sternheimer_solution); A p = (H - eps) p then already
+// lies in range(Q) up to the eigenpair residual.  Preconditioner:
+// z = Q diag(1/(kappa_s + |k+G|^2/2)) r.  B must be in range(Q).
 template <typename R>
 CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, const std::vector<double>& shift,
                  const std::vector<double>& kappa, const std::vector<double>& tol, int maxit) {
@@ -142,13 +143,13 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
   c->active_hint = n;
   int* dcount = reinterpret_cast<int*>(w.scal.p + 40);
   for (int it = 1; it <= maxit; ++it) {
-    // W = Q (H - eps) P
+    // W = (H - eps) P and <P, W>.  P is in range(Q) (z is projected below), and
+    // Phi^H (H - eps) P = (Lambda - eps) Phi^H P = 0 for the eigenvectors Phi, so
+    // Q W = W up to the eigenpair residual: W is not projected again.
     launch_z_inverse<R>(c, L, v.P, c->ld, act, Bufs<R>::b1(c));
     launch_plane<R>(c, L, Bufs<R>::b1(c), Bufs<R>::pot(c), nullptr, act, Bufs<R>::b4(c));
-    launch_z_forward<R>(c, L, Bufs<R>::b4(c), v.W, c->ld, v.P, sys + kSysShift * n, true, act);
-    proj_coef<R>(c, L, v.W, c->ld, act, coef);
-    proj_apply<R>(c, L, coef, v.W, R(1), R(-1), v.W, c->ld, v.P, w.dpart.p, act);
-    cg_scalars(c, 1, sys, w.dpart.p, pch, n, maxit, act, dcount);
+    launch_z_forward<R>(c, L, Bufs<R>::b4(c), v.W, c->ld, v.P, sys + kSysShift * n, true, act, w.dpart.p);
+    cg_scalars(c, 1, sys, w.dpart.p, zf_chunks(c), n, maxit, act, dcount);
     // x += alpha p, r -= alpha W, z = M^-1 r, ||r||^2, stopping test
     cg_xr<R>(c, L, 1, v, sys, act, w.dpart.p);
     cg_scalars(c, 2, sys, w.dpart.p, cch, n, maxit, act, dcount);
