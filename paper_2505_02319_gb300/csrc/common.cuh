@@ -16,10 +16,85 @@
 
 namespace ikr {
 
+// Double-float ("df64") real: an unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi)/2, about 48 significant bits, computed on the FP32 units.
+// Arithmetic from the error-free transformations: TwoSum (Knuth) for a + b,
+// the FMA residual a*b - fl(a*b) for products (Dekker's product with a fused
+// multiply-add), renormalised by a fast two-sum; additions drop the O(2^-48)
+// second-order terms, so each operation has an error of a few 2^-48 relative
+// to its operands.  Used where the mixed-precision path needs FP64 accuracy.
+struct dfloat {
+  float hi, lo;
+  __host__ __device__ constexpr dfloat() : hi(0.f), lo(0.f) {}
+  __host__ __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr dfloat(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ constexpr dfloat(int i) : hi((float)i), lo(0.f) {}
+};
+
+__device__ __forceinline__ dfloat df_fast2sum(float a, float b) {
+  const float s = a + b;
+  return dfloat(s, b - (s - a));
+}
+__device__ __forceinline__ dfloat df_2sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return dfloat(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+  const dfloat s = df_2sum(a.hi, b.hi);
+  return df_fast2sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_fast2sum(p, e);
+}
+__device__ __forceinline__ dfloat& operator+=(dfloat& a, dfloat b) { return a = a + b; }
+__device__ __forceinline__ dfloat& operator-=(dfloat& a, dfloat b) { return a = a - b; }
+__device__ __forceinline__ double df_to_double(dfloat a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dfloat df_from_double(double d) {
+  const float h = __double2float_rn(d);
+  return dfloat(h, __double2float_rn(d - (double)h));
+}
+
+struct dfloat2 {
+  dfloat x, y;
+};
+
 template <typename R> struct cplx;
 template <> struct cplx<double> { using type = double2; };
 template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<dfloat> { using type = dfloat2; };
 template <typename R> using C_t = typename cplx<R>::type;
+
+// conversions between the storage types and the arithmetic types
+template <typename C> __device__ __forceinline__ C to_c(double2 v);
+template <> __device__ __forceinline__ double2 to_c<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ dfloat2 to_c<dfloat2>(double2 v) {
+  dfloat2 r;
+  r.x = df_from_double(v.x);
+  r.y = df_from_double(v.y);
+  return r;
+}
+template <typename C> __device__ __forceinline__ C to_c(float2 v);
+template <> __device__ __forceinline__ float2 to_c<float2>(float2 v) { return v; }
+__device__ __forceinline__ double2 from_c(double2 v) { return v; }
+__device__ __forceinline__ float2 from_c(float2 v) { return v; }
+__device__ __forceinline__ double2 from_c(dfloat2 v) { return make_double2(df_to_double(v.x), df_to_double(v.y)); }
+template <typename R> __device__ __forceinline__ R to_r(double v) { return (R)v; }
+template <> __device__ __forceinline__ dfloat to_r<dfloat>(double v) { return df_from_double(v); }
+template <typename R> __device__ __forceinline__ R to_r(float v) { return (R)v; }
+template <> __device__ __forceinline__ dfloat to_r<dfloat>(float v) { return dfloat(v, 0.f); }
+
+// storage type of the arithmetic type R (what global buffers hold)
+template <typename R> struct io;
+template <> struct io<float> { using real = float; using cx = float2; };
+template <> struct io<double> { using real = double; using cx = double2; };
+template <> struct io<dfloat> { using real = double; using cx = double2; };
 
 template <typename C> __host__ __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
   C c; c.x = a; c.y = b; return c;

@@ -197,6 +197,7 @@ struct ikr_ctx {
   size_t pinned_bytes = 0;
   ikr::Profiler prof;
   int active_hint = 0;          // systems active in the next masked launch (for accounting)
+  bool emulate_fp64 = false;    // FP64 plane passes in double-float on the FP32 units (mixed path)
   ~ikr_ctx() {
     if (h_pinned) cudaFreeHost(h_pinned);
     for (auto& v : prof.ev)

@@ -462,6 +462,13 @@ void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, 
                   const int* active, C_t<R>* b4, const C_t<R>* real_in) {
   if (L.n == 0) return;
   ProfScope ps(c, kKidPlane, 1, active ? c->active_hint : L.n, (int)sizeof(R));
+  if (sizeof(R) == 8 && c->emulate_fp64) {
+    // FP64-accurate pass of the mixed path on the FP32 units (double-float)
+    if (launch_plane_fast<dfloat>(c, L.n, reinterpret_cast<const double2*>(b1),
+                                  reinterpret_cast<const double*>(pot), pot_scale, active,
+                                  reinterpret_cast<double2*>(b4), reinterpret_cast<const double2*>(real_in)))
+      return;
+  }
   if (launch_plane_fast<R>(c, L.n, b1, pot, pot_scale, active, b4, real_in)) return;
   const int Nx = c->N[0], Ny = c->N[1], Nz = c->N[2];
   const size_t smem = sizeof(C_t<R>) * (Nx + Ny + 2 * (size_t)Ny * (Nx + 1)) + sizeof(int) * c->nxa;

@@ -175,7 +175,8 @@ __device__ __forceinline__ void line_fft_finish(C* v, C* line, int es, const C* 
 // x[t + T q], so the product happens in registers.
 template <typename R, int N>
 __device__ __forceinline__ void line_fft_ivf(C_t<R>* line, const C_t<R>* tab, int t, unsigned mask,
-                                             const R* __restrict__ pot_row, R sc, bool in_real) {
+                                             const typename io<R>::real* __restrict__ pot_row, R sc,
+                                             bool in_real) {
   using C = C_t<R>;
   constexpr int T = Tpl<N>::v;
   constexpr int E = N / T;
@@ -207,7 +208,7 @@ __device__ __forceinline__ void line_fft_ivf(C_t<R>* line, const C_t<R>* tab, in
     }
   }
 #pragma unroll
-  for (int q = 0; q < E; ++q) v[q] = cscale(v[q], __ldg(pot_row + t + T * q) * sc);
+  for (int q = 0; q < E; ++q) v[q] = cscale(v[q], to_r<R>(__ldg(pot_row + t + T * q)) * sc);
   RegFft<C, E, N, false>::run(v, tab);
   line_fft_finish<C, N, false>(v, line, 1, tab, t, mask);
 }
@@ -223,13 +224,14 @@ struct PlaneGeom {
 }  // namespace
 
 template <typename R, int NX, int NY>
-__global__ void __launch_bounds__(256) k_plane_t(const C_t<R>* __restrict__ b1, int nc, int ncp,
+__global__ void __launch_bounds__(256) k_plane_t(const typename io<R>::cx* __restrict__ b1, int nc, int ncp,
                                                  const int* __restrict__ col_xy, const int* __restrict__ xpos,
-                                                 int nxa, int Nz, const C_t<R>* __restrict__ twx,
-                                                 const C_t<R>* __restrict__ twy, const R* __restrict__ pot,
+                                                 int nxa, int Nz, const typename io<R>::cx* __restrict__ twx,
+                                                 const typename io<R>::cx* __restrict__ twy,
+                                                 const typename io<R>::real* __restrict__ pot,
                                                  const double* __restrict__ pot_scale,
-                                                 const int* __restrict__ active, C_t<R>* __restrict__ b4,
-                                                 const C_t<R>* __restrict__ real_in) {
+                                                 const int* __restrict__ active, typename io<R>::cx* __restrict__ b4,
+                                                 const typename io<R>::cx* __restrict__ real_in) {
   using C = C_t<R>;
   using G = PlaneGeom<C, NX, NY>;
   constexpr int ldp = G::ldp, PL = G::PL;
@@ -243,15 +245,15 @@ __global__ void __launch_bounds__(256) k_plane_t(const C_t<R>* __restrict__ b1, 
   C* ty = tx + NX;
   C* planes = ty + NY;
   int* xp = reinterpret_cast<int*>(planes + PL * G::plane);
-  for (int i = threadIdx.x; i < NX; i += blockDim.x) tx[i] = twx[i];
-  for (int i = threadIdx.x; i < NY; i += blockDim.x) ty[i] = twy[i];
+  for (int i = threadIdx.x; i < NX; i += blockDim.x) tx[i] = to_c<C>(twx[i]);
+  for (int i = threadIdx.x; i < NY; i += blockDim.x) ty[i] = to_c<C>(twy[i]);
   for (int i = threadIdx.x; i < nxa; i += blockDim.x) xp[i] = xpos[i];
   const int lane = threadIdx.x & 31;
   if (real_in) {
     for (int e = threadIdx.x; e < npl * NY * NX; e += blockDim.x) {
       const int p = e / (NY * NX), r = e - p * (NY * NX);
       const int iy = r / NX, ix = r - iy * NX;
-      planes[p * G::plane + iy * ldp + ix] = real_in[((size_t)s * Nz + iz0 + p) * NY * NX + r];
+      planes[p * G::plane + iy * ldp + ix] = to_c<C>(real_in[((size_t)s * Nz + iz0 + p) * NY * NX + r]);
     }
     __syncthreads();
   } else {
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(256) k_plane_t(const C_t<R>* __restrict__ b1, 
     for (int e = threadIdx.x; e < npl * nc; e += blockDim.x) {
       const int p = e / nc, col = e - p * nc;
       planes[p * G::plane + col_xy[2 * col + 1] * ldp + col_xy[2 * col]] =
-          b1[((size_t)s * Nz + iz0 + p) * ncp + col];
+          to_c<C>(b1[((size_t)s * Nz + iz0 + p) * ncp + col]);
     }
     __syncthreads();
     // inverse y-lines of the active x positions
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(256) k_plane_t(const C_t<R>* __restrict__ b1, 
   }
   // x-lines: inverse FFT, potential product, forward FFT, all within the line's lanes
   {
-    const R sc = pot_scale ? (R)(*pot_scale) : R(1);
+    const R sc = pot_scale ? to_r<R>(*pot_scale) : R(1);
     const int slots = blockDim.x / TX, slot = threadIdx.x / TX, t = threadIdx.x % TX;
     const int items = npl * NY;
     const int rounds = (items + slots - 1) / slots;
@@ -293,13 +295,13 @@ __global__ void __launch_bounds__(256) k_plane_t(const C_t<R>* __restrict__ b1, 
       if (ok) {
         const int p = it / NY, iy = it - p * NY;
         C* line = planes + p * G::plane + iy * ldp;
-        const R* pp = pot + ((size_t)(iz0 + p) * NY + iy) * NX;
+        const typename io<R>::real* pp = pot + ((size_t)(iz0 + p) * NY + iy) * NX;
         if constexpr (Tpl<NX>::fused) {
           line_fft_ivf<R, NX>(line, tx, t, mask, pp, sc, real_in != nullptr);
         } else {
           if (!real_in) line_fft<C, NX, true>(line, 1, tx, t, mask);   // real_in: already in real space
 #pragma unroll
-          for (int ix = t; ix < NX; ix += TX) line[ix] = cscale(line[ix], pp[ix] * sc);
+          for (int ix = t; ix < NX; ix += TX) line[ix] = cscale(line[ix], to_r<R>(pp[ix]) * sc);
           __syncwarp(mask);
           line_fft<C, NX, false>(line, 1, tx, t, mask);
         }
@@ -327,19 +329,21 @@ __global__ void __launch_bounds__(256) k_plane_t(const C_t<R>* __restrict__ b1, 
   for (int e = threadIdx.x; e < npl * nc; e += blockDim.x) {
     const int p = e / nc, col = e - p * nc;
     b4[((size_t)s * Nz + iz0 + p) * ncp + col] =
-        planes[p * G::plane + col_xy[2 * col + 1] * ldp + col_xy[2 * col]];
+        from_c(planes[p * G::plane + col_xy[2 * col + 1] * ldp + col_xy[2 * col]]);
   }
 }
 
 namespace {
 
-template <typename R> const C_t<R>* twp(ikr_ctx* c, int axis);
+template <typename R> const typename io<R>::cx* twp(ikr_ctx* c, int axis);
 template <> const double2* twp<double>(ikr_ctx* c, int axis) { return c->d_tw[axis].p; }
+template <> const double2* twp<dfloat>(ikr_ctx* c, int axis) { return c->d_tw[axis].p; }
 template <> const float2* twp<float>(ikr_ctx* c, int axis) { return c->d_tw32[axis].p; }
 
 template <typename R, int NX, int NY>
-bool try_launch(ikr_ctx* c, int nsys, const C_t<R>* b1, const R* pot, const double* pot_scale,
-                const int* active, C_t<R>* b4, const C_t<R>* real_in) {
+bool try_launch(ikr_ctx* c, int nsys, const typename io<R>::cx* b1, const typename io<R>::real* pot,
+                const double* pot_scale, const int* active, typename io<R>::cx* b4,
+                const typename io<R>::cx* real_in) {
   if (c->N[0] != NX || c->N[1] != NY) return false;
   using G = PlaneGeom<C_t<R>, NX, NY>;
   const size_t smem = sizeof(C_t<R>) * (NX + NY + (size_t)G::PL * G::plane) + sizeof(int) * c->nxa;
@@ -358,8 +362,9 @@ bool try_launch(ikr_ctx* c, int nsys, const C_t<R>* b1, const R* pot, const doub
 
 // Compile-time plane shapes of the supported grids; false: use the generic kernel.
 template <typename R>
-bool launch_plane_fast(ikr_ctx* c, int nsys, const C_t<R>* b1, const R* pot, const double* pot_scale,
-                       const int* active, C_t<R>* b4, const C_t<R>* real_in) {
+bool launch_plane_fast(ikr_ctx* c, int nsys, const typename io<R>::cx* b1, const typename io<R>::real* pot,
+                       const double* pot_scale, const int* active, typename io<R>::cx* b4,
+                       const typename io<R>::cx* real_in) {
   return try_launch<R, 48, 48>(c, nsys, b1, pot, pot_scale, active, b4, real_in) ||
          try_launch<R, 32, 32>(c, nsys, b1, pot, pot_scale, active, b4, real_in) ||
          try_launch<R, 40, 40>(c, nsys, b1, pot, pot_scale, active, b4, real_in) ||
@@ -369,13 +374,10 @@ bool launch_plane_fast(ikr_ctx* c, int nsys, const C_t<R>* b1, const R* pot, con
          try_launch<R, 24, 24>(c, nsys, b1, pot, pot_scale, active, b4, real_in);
 }
 
-// FP64: the register-resident variant leaves the few FP64 units of the part
-// idle more often than the shared-memory Stockham kernel; keep the latter.
-template <>
-bool launch_plane_fast<double>(ikr_ctx*, int, const double2*, const double*, const double*, const int*,
-                               double2*, const double2*) {
-  return false;
-}
+template bool launch_plane_fast<double>(ikr_ctx*, int, const double2*, const double*, const double*, const int*,
+                                        double2*, const double2*);
+template bool launch_plane_fast<dfloat>(ikr_ctx*, int, const double2*, const double*, const double*, const int*,
+                                        double2*, const double2*);
 template bool launch_plane_fast<float>(ikr_ctx*, int, const float2*, const float*, const double*, const int*,
                                        float2*, const float2*);
 

@@ -23,8 +23,9 @@ void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, 
                   const int* active, C_t<R>* b4, const C_t<R>* real_in = nullptr);
 template <typename R> void launch_synth_planes(ikr_ctx* c, int nsys, const C_t<R>* b1, C_t<R>* out);
 template <typename R>
-bool launch_plane_fast(ikr_ctx* c, int nsys, const C_t<R>* b1, const R* pot, const double* pot_scale,
-                       const int* active, C_t<R>* b4, const C_t<R>* real_in);
+bool launch_plane_fast(ikr_ctx* c, int nsys, const typename io<R>::cx* b1, const typename io<R>::real* pot,
+                       const double* pot_scale, const int* active, typename io<R>::cx* b4,
+                       const typename io<R>::cx* real_in);
 template <typename R>
 void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* out, int ld,
                       const C_t<R>* psi, const double* shift, bool kinetic, const int* active,

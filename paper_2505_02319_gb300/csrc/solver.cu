@@ -188,9 +188,19 @@ template CgStats cg_solve<float>(ikr_ctx*, const SysList&, const float2*, float2
 // fp32 = true runs the whole application (right-hand sides, CG, density) in
 // FP32 with FP64 accumulation of the density; the callers choose it only when
 // the error budget of the application is far above FP32 rounding.
+namespace {
+struct EmulateScope {   // FP64-accurate passes of the mixed path run in double-float
+  ikr_ctx* c;
+  bool old;
+  EmulateScope(ikr_ctx* c_, bool on) : c(c_), old(c_->emulate_fp64) { c->emulate_fp64 = on; }
+  ~EmulateScope() { c->emulate_fp64 = old; }
+};
+}  // namespace
+
 void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::vector<double>& tol,
                int maxit, int precision, double* drho, RunStats& rs, bool fp32) {
   IKR_REQUIRE(c->have_gs, IKR_ERR_STATE, "the ground state is not set");
+  EmulateScope em(c, precision == IKR_MIXED);
   const SysList& L = c->occ;
   const int n = L.n;
   IKR_REQUIRE((int)tol.size() == n, IKR_ERR_ARG, "one tolerance per occupied system is required");
