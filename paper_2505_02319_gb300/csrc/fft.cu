@@ -521,8 +521,17 @@ void launch_density(ikr_ctx* c, int nsys, const C_t<R>* b1phi, const C_t<R>* b1d
   c->ws.dens_part.reserve((size_t)G * c->Ng);
   const size_t np = (size_t)Ny * (Nx + 1);
   const size_t smem = sizeof(C_t<R>) * (Nx + Ny + 3 * np) + sizeof(int) * c->nxa;
-  set_smem(k_density<R>, smem);
-  if (nsys > 0) {
+  bool fast = false;
+  if (nsys > 0 && psi_real && b1d) {
+    if (sizeof(R) == 8 && c->emulate_fp64)
+      fast = launch_density_fast<dfloat>(c, nsys, G, reinterpret_cast<const double2*>(b1d),
+                                         reinterpret_cast<const double2*>(psi_real), coef_a, coef_b,
+                                         c->ws.dens_part.p);
+    if (!fast) fast = launch_density_fast<R>(c, nsys, G, b1d, psi_real, coef_a, coef_b, c->ws.dens_part.p);
+  }
+  if (fast) {
+  } else if (nsys > 0) {
+    set_smem(k_density<R>, smem);
     dim3 grid(Nz, G);
     k_density<R><<<grid, kDensThreads, smem, c->stream>>>(
         b1phi, b1d, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa, c->plan[0], c->plan[1], Nz,

@@ -333,6 +333,105 @@ __global__ void __launch_bounds__(256) k_plane_t(const typename io<R>::cx* __res
   }
 }
 
+// Density accumulation with compile-time line lengths (same result as
+// k_density in fft.cu, which it replaces for the supported grids):
+//   part[g][iz][iy][ix] = sum_{s in group g} a_s Re(conj(psi_s) dpsi_s) + b_s |psi_s|^2,
+// psi_s the cached real-space orbital planes, dpsi_s synthesised here from the
+// z-transformed responses b1d (y-lines of the active x positions, then x-lines),
+// PL systems at a time; accumulation in FP64 registers.
+template <typename R, int NX, int NY>
+__global__ void __launch_bounds__(256) k_density_t(const typename io<R>::cx* __restrict__ b1d, int nc, int ncp,
+                                                   const int* __restrict__ col_xy, const int* __restrict__ xpos,
+                                                   int nxa, int Nz, const typename io<R>::cx* __restrict__ twx,
+                                                   const typename io<R>::cx* __restrict__ twy,
+                                                   const typename io<R>::cx* __restrict__ psir,
+                                                   const double* __restrict__ coef_a,
+                                                   const double* __restrict__ coef_b, int nsys, int ngroups,
+                                                   double* __restrict__ part) {
+  using C = C_t<R>;
+  using G = PlaneGeom<C, NX, NY>;
+  constexpr int ldp = G::ldp, PL = G::PL;
+  constexpr int TX = Tpl<NX>::v, TY = Tpl<NY>::v;
+  constexpr int NE = (NX * NY + 255) / 256;
+  const int iz = blockIdx.x, g = blockIdx.y;
+  extern __shared__ unsigned char smem_raw[];
+  C* tx = reinterpret_cast<C*>(smem_raw);
+  C* ty = tx + NX;
+  C* planes = ty + NY;
+  int* xp = reinterpret_cast<int*>(planes + PL * G::plane);
+  for (int i = threadIdx.x; i < NX; i += blockDim.x) tx[i] = to_c<C>(twx[i]);
+  for (int i = threadIdx.x; i < NY; i += blockDim.x) ty[i] = to_c<C>(twy[i]);
+  for (int i = threadIdx.x; i < nxa; i += blockDim.x) xp[i] = xpos[i];
+  double acc[NE];
+#pragma unroll
+  for (int i = 0; i < NE; ++i) acc[i] = 0.0;
+  const int s0 = (int)((long long)g * nsys / ngroups), s1 = (int)((long long)(g + 1) * nsys / ngroups);
+  for (int sb = s0; sb < s1; sb += PL) {
+    const int npl = min(PL, s1 - sb);
+    __syncthreads();
+    for (int i = threadIdx.x; i < npl * G::plane; i += blockDim.x) planes[i] = mk<C>(0, 0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < npl * nc; e += blockDim.x) {
+      const int p = e / nc, col = e - p * nc;
+      planes[p * G::plane + col_xy[2 * col + 1] * ldp + col_xy[2 * col]] =
+          to_c<C>(b1d[((size_t)(sb + p) * Nz + iz) * ncp + col]);
+    }
+    __syncthreads();
+    {
+      const int slots = blockDim.x / TY, slot = threadIdx.x / TY, t = threadIdx.x % TY;
+      const int items = npl * nxa;
+      const int rounds = (items + slots - 1) / slots;
+      for (int r = 0; r < rounds; ++r) {
+        const int it = r * slots + slot;
+        const bool ok = it < items;
+        const unsigned mask = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+          const int p = it / nxa, l = it - p * nxa;
+          line_fft<C, NY, true>(planes + p * G::plane + xp[l], ldp, ty, t, mask);
+        }
+      }
+    }
+    __syncthreads();
+    {
+      const int slots = blockDim.x / TX, slot = threadIdx.x / TX, t = threadIdx.x % TX;
+      const int items = npl * NY;
+      const int rounds = (items + slots - 1) / slots;
+      for (int r = 0; r < rounds; ++r) {
+        const int it = r * slots + slot;
+        const bool ok = it < items;
+        const unsigned mask = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+          const int p = it / NY, iy = it - p * NY;
+          line_fft<C, NX, true>(planes + p * G::plane + iy * ldp, 1, tx, t, mask);
+        }
+      }
+    }
+    __syncthreads();
+    for (int p = 0; p < npl; ++p) {
+      const int s = sb + p;
+      const double a = coef_a[s], b = coef_b[s];
+      const typename io<R>::cx* ps = psir + ((size_t)s * Nz + iz) * NX * NY;
+#pragma unroll
+      for (int i = 0; i < NE; ++i) {
+        const int e = threadIdx.x + 256 * i;
+        if (e < NX * NY) {
+          const int iy = e / NX, ix = e - iy * NX;
+          const auto d = from_c(planes[p * G::plane + iy * ldp + ix]);
+          const typename io<R>::cx q = ps[e];
+          const double px = (double)q.x, py = (double)q.y;
+          acc[i] += a * (px * (double)d.x + py * (double)d.y) + b * (px * px + py * py);
+        }
+      }
+    }
+  }
+  double* dst = part + ((size_t)g * Nz + iz) * NX * NY;
+#pragma unroll
+  for (int i = 0; i < NE; ++i) {
+    const int e = threadIdx.x + 256 * i;
+    if (e < NX * NY) dst[e] = acc[i];
+  }
+}
+
 namespace {
 
 template <typename R> const typename io<R>::cx* twp(ikr_ctx* c, int axis);
@@ -358,7 +457,41 @@ bool try_launch(ikr_ctx* c, int nsys, const typename io<R>::cx* b1, const typena
   return true;
 }
 
+template <typename R, int NX, int NY>
+bool try_density(ikr_ctx* c, int nsys, int ngroups, const typename io<R>::cx* b1d,
+                 const typename io<R>::cx* psir, const double* ca, const double* cb, double* part) {
+  if (c->N[0] != NX || c->N[1] != NY) return false;
+  using G = PlaneGeom<C_t<R>, NX, NY>;
+  const size_t smem = sizeof(C_t<R>) * (NX + NY + (size_t)G::PL * G::plane) + sizeof(int) * c->nxa;
+  if (smem > 227 * 1024) return false;
+  IKR_CUDA(cudaFuncSetAttribute(k_density_t<R, NX, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(c->N[2], ngroups);
+  k_density_t<R, NX, NY><<<grid, 256, smem, c->stream>>>(b1d, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa,
+                                                          c->N[2], twp<R>(c, 0), twp<R>(c, 1), psir, ca, cb,
+                                                          nsys, ngroups, part);
+  IKR_CUDA(cudaGetLastError());
+  return true;
+}
+
 }  // namespace
+
+template <typename R>
+bool launch_density_fast(ikr_ctx* c, int nsys, int ngroups, const typename io<R>::cx* b1d,
+                         const typename io<R>::cx* psir, const double* ca, const double* cb, double* part) {
+  return try_density<R, 48, 48>(c, nsys, ngroups, b1d, psir, ca, cb, part) ||
+         try_density<R, 32, 32>(c, nsys, ngroups, b1d, psir, ca, cb, part) ||
+         try_density<R, 40, 40>(c, nsys, ngroups, b1d, psir, ca, cb, part) ||
+         try_density<R, 96, 96>(c, nsys, ngroups, b1d, psir, ca, cb, part) ||
+         try_density<R, 12, 12>(c, nsys, ngroups, b1d, psir, ca, cb, part) ||
+         try_density<R, 10, 12>(c, nsys, ngroups, b1d, psir, ca, cb, part) ||
+         try_density<R, 24, 24>(c, nsys, ngroups, b1d, psir, ca, cb, part);
+}
+template bool launch_density_fast<float>(ikr_ctx*, int, int, const float2*, const float2*, const double*,
+                                         const double*, double*);
+template bool launch_density_fast<double>(ikr_ctx*, int, int, const double2*, const double2*, const double*,
+                                          const double*, double*);
+template bool launch_density_fast<dfloat>(ikr_ctx*, int, int, const double2*, const double2*, const double*,
+                                          const double*, double*);
 
 // Compile-time plane shapes of the supported grids; false: use the generic kernel.
 template <typename R>

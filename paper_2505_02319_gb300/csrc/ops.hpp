@@ -32,6 +32,9 @@ void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* ou
                       double* dpart = nullptr);
 int zf_chunks(ikr_ctx* c);    // dot partials per system written by launch_z_forward
 template <typename R>
+bool launch_density_fast(ikr_ctx* c, int nsys, int ngroups, const typename io<R>::cx* b1d,
+                         const typename io<R>::cx* psir, const double* ca, const double* cb, double* part);
+template <typename R>
 void launch_density(ikr_ctx* c, int nsys, const C_t<R>* b1phi, const C_t<R>* b1d,
                     const double* coef_a, const double* coef_b, double* out, double scale,
                     const C_t<R>* psi_real = nullptr);
