@@ -90,6 +90,10 @@ template <> __device__ __forceinline__ dfloat to_r<dfloat>(double v) { return df
 template <typename R> __device__ __forceinline__ R to_r(float v) { return (R)v; }
 template <> __device__ __forceinline__ dfloat to_r<dfloat>(float v) { return dfloat(v, 0.f); }
 
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(float v) { return (double)v; }
+__device__ __forceinline__ double to_d(dfloat v) { return df_to_double(v); }
+
 // storage type of the arithmetic type R (what global buffers hold)
 template <typename R> struct io;
 template <> struct io<float> { using real = float; using cx = float2; };

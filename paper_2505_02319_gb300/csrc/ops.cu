@@ -113,15 +113,15 @@ __global__ void k_proj_reduce(const double2* __restrict__ part, int nchunks, int
 constexpr int kPC = 32;
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_proj_partial_w(const C_t<R>* __restrict__ phi_all, int ld,
-                                                      const int* __restrict__ phi_off,
-                                                      const int* __restrict__ nocc_k,
-                                                      const int* __restrict__ nb_k,
-                                                      const int* __restrict__ kstart,
-                                                      const int* __restrict__ kcount,
-                                                      const C_t<R>* __restrict__ Y, int ldy,
-                                                      const int* __restrict__ active, int nsys,
-                                                      int noccmax, double2* __restrict__ part) {
+__global__ void __launch_bounds__(256) k_proj_partial_w(const typename io<R>::cx* __restrict__ phi_all, int ld,
+                                                        const int* __restrict__ phi_off,
+                                                        const int* __restrict__ nocc_k,
+                                                        const int* __restrict__ nb_k,
+                                                        const int* __restrict__ kstart,
+                                                        const int* __restrict__ kcount,
+                                                        const typename io<R>::cx* __restrict__ Y, int ldy,
+                                                        const int* __restrict__ active, int nsys,
+                                                        int noccmax, double2* __restrict__ part) {
   using C = C_t<R>;
   const int k = blockIdx.y, chunk = blockIdx.x;
   const int ns = kcount[k];
@@ -131,10 +131,10 @@ __global__ void __launch_bounds__(256) k_proj_partial_w(const C_t<R>* __restrict
   extern __shared__ unsigned char smem_raw[];
   C* ph = reinterpret_cast<C*>(smem_raw);           // [g][m], kPC x nocc
   C* ys = ph + kPC * nocc;                          // per warp kPC entries
-  const C* phi = phi_all + (size_t)phi_off[k] * ld;
+  const typename io<R>::cx* phi = phi_all + (size_t)phi_off[k] * ld;
   for (int idx = threadIdx.x; idx < kPC * nocc; idx += blockDim.x) {
     const int m = idx / kPC, g = idx - m * kPC;
-    ph[g * nocc + m] = (g0 + g < nb) ? phi[(size_t)m * ld + g0 + g] : mk<C>(0, 0);
+    ph[g * nocc + m] = (g0 + g < nb) ? to_c<C>(phi[(size_t)m * ld + g0 + g]) : mk<C>(0, 0);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -143,38 +143,37 @@ __global__ void __launch_bounds__(256) k_proj_partial_w(const C_t<R>* __restrict
   for (int sl = warp; sl < ns; sl += nw) {
     const int s = s0 + sl;
     if (active && !active[s]) continue;
-    yw[lane] = (g0 + lane < nb) ? Y[(size_t)s * ldy + g0 + lane] : mk<C>(0, 0);
+    yw[lane] = (g0 + lane < nb) ? to_c<C>(Y[(size_t)s * ldy + g0 + lane]) : mk<C>(0, 0);
     __syncwarp();
     for (int m = lane; m < nocc; m += 32) {
-      R ax = 0, ay = 0;
+      R ax = R(0), ay = R(0);
 #pragma unroll 8
       for (int g = 0; g < kPC; ++g) {
         const C p = ph[g * nocc + m], y = yw[g];
         ax += p.x * y.x + p.y * y.y;
         ay += p.x * y.y - p.y * y.x;
       }
-      part[((size_t)chunk * nsys + s) * noccmax + m] = make_double2(ax, ay);
+      part[((size_t)chunk * nsys + s) * noccmax + m] = make_double2(to_d(ax), to_d(ay));
     }
     __syncwarp();
   }
 }
 
-
 // out[s][G] = alpha * in[s][G] + beta * sum_m Phi_k[m][G] coef[s][m]
 // optionally dpart[s][chunk] = sum_{G in chunk} Re(conj(dv[s][G]) out[s][G]).
 template <typename R>
-__global__ void __launch_bounds__(256) k_proj_apply_w(const C_t<R>* __restrict__ phi_all, int ld,
-                                                    const int* __restrict__ phi_off,
-                                                    const int* __restrict__ nocc_k,
-                                                    const int* __restrict__ nb_k,
-                                                    const int* __restrict__ kstart,
-                                                    const int* __restrict__ kcount,
-                                                    const double2* __restrict__ coef, int noccmax,
-                                                    const C_t<R>* in, R alpha, R beta,
-                                                    C_t<R>* out, int ldy,
-                                                    const C_t<R>* __restrict__ dv,
-                                                    double* __restrict__ dpart, int nparts,
-                                                    const int* __restrict__ active) {
+__global__ void __launch_bounds__(256) k_proj_apply_w(const typename io<R>::cx* __restrict__ phi_all, int ld,
+                                                      const int* __restrict__ phi_off,
+                                                      const int* __restrict__ nocc_k,
+                                                      const int* __restrict__ nb_k,
+                                                      const int* __restrict__ kstart,
+                                                      const int* __restrict__ kcount,
+                                                      const double2* __restrict__ coef, int noccmax,
+                                                      const typename io<R>::cx* in, double alpha, double beta,
+                                                      typename io<R>::cx* out, int ldy,
+                                                      const typename io<R>::cx* __restrict__ dv,
+                                                      double* __restrict__ dpart, int nparts,
+                                                      const int* __restrict__ active) {
   using C = C_t<R>;
   const int k = blockIdx.y, chunk = blockIdx.x;
   const int ns = kcount[k];
@@ -189,40 +188,49 @@ __global__ void __launch_bounds__(256) k_proj_apply_w(const C_t<R>* __restrict__
   }
   extern __shared__ unsigned char smem_raw[];
   C* ph = reinterpret_cast<C*>(smem_raw);           // [m][g]
-  const C* phi = phi_all + (size_t)phi_off[k] * ld;
+  C* cwall = ph + kPC * nocc;                       // per warp: the coefficients of its system
+  const typename io<R>::cx* phi = phi_all + (size_t)phi_off[k] * ld;
   for (int idx = threadIdx.x; idx < kPC * nocc; idx += blockDim.x) {
     const int m = idx / kPC, g = idx - m * kPC;
-    ph[m * kPC + g] = (g0 + g < nb) ? phi[(size_t)m * ld + g0 + g] : mk<C>(0, 0);
+    ph[m * kPC + g] = (g0 + g < nb) ? to_c<C>(phi[(size_t)m * ld + g0 + g]) : mk<C>(0, 0);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  C* cw = cwall + warp * nocc;
   const int s0 = kstart[k];
+  const R ra = to_r<R>(alpha), rb = to_r<R>(beta);
   for (int sl = warp; sl < ns; sl += nw) {
     const int s = s0 + sl;
     if (active && !active[s]) continue;
     const double2* cf = coef + (size_t)s * noccmax;
-    R ax = 0, ay = 0;
-    for (int m = 0; m < nocc; ++m) {
+    // each coefficient is converted once, by one lane
+    for (int m = lane; m < nocc; m += 32) {
       const double2 cd = cf[m];
-      const C p = ph[m * kPC + lane];
-      const R cx = (R)cd.x, cy = (R)cd.y;
-      ax += p.x * cx - p.y * cy;
-      ay += p.x * cy + p.y * cx;
+      cw[m] = mk<C>(to_r<R>(cd.x), to_r<R>(cd.y));
     }
+    __syncwarp();
+    R ax = R(0), ay = R(0);
+    for (int m = 0; m < nocc; ++m) {
+      const C p = ph[m * kPC + lane];
+      const C cc = cw[m];
+      ax += p.x * cc.x - p.y * cc.y;
+      ay += p.x * cc.y + p.y * cc.x;
+    }
+    __syncwarp();
     const int g = g0 + lane;
     double d = 0.0;
     if (g < nb) {
       const size_t o = (size_t)s * ldy + g;
-      C v = mk<C>(beta * ax, beta * ay);
-      if (alpha != R(0)) {
-        const C x = in[o];
-        v.x += alpha * x.x;
-        v.y += alpha * x.y;
+      C v = mk<C>(rb * ax, rb * ay);
+      if (alpha != 0.0) {
+        const C x = to_c<C>(in[o]);
+        v.x += ra * x.x;
+        v.y += ra * x.y;
       }
-      out[o] = v;
+      out[o] = from_c(v);
       if (dv) {
-        const C w = dv[o];
-        d = (double)w.x * v.x + (double)w.y * v.y;
+        const auto w = dv[o];
+        d = (double)w.x * to_d(v.x) + (double)w.y * to_d(v.y);
       }
     }
     if (dpart) {
@@ -231,7 +239,6 @@ __global__ void __launch_bounds__(256) k_proj_apply_w(const C_t<R>* __restrict__
     }
   }
 }
-
 
 // FP32: // out[s][G] = alpha * in[s][G] + beta * sum_m Phi_k[m][G] coef[s][m]
 // optionally dpart[s][chunk] = sum_{G in chunk} Re(conj(dv[s][G]) out[s][G]).
@@ -758,12 +765,20 @@ void proj_coef(ikr_ctx* c, const SysList& L, const C_t<R>* Y, int ldy, const int
     const int nm = c->noccmax;
     c->ws.cpart.reserve((size_t)nch * L.n * nm * 2);
     double2* part = reinterpret_cast<double2*>(c->ws.cpart.p);
-    const size_t smem = sizeof(C_t<R>) * (kPC * nm + 8 * kPC);
-    set_smem_attr((const void*)k_proj_partial_w<R>, smem);
+    const size_t smem = sizeof(double2) * (kPC * nm + 8 * kPC);
     dim3 grid(nch, (unsigned)c->k.size());
-    k_proj_partial_w<R><<<grid, 256, smem, c->stream>>>(phi_ptr<R>(c), c->ld, c->d_phi_off.p, c->d_nocc.p,
-                                                         c->d_nb.p, L.d_kstart.p, L.d_kcount.p, Y, ldy, active,
-                                                         L.n, nm, part);
+    const double2* Yd = reinterpret_cast<const double2*>(Y);
+    if (c->emulate_fp64) {   // FP64-accurate products of the mixed path on the FP32 units
+      set_smem_attr((const void*)k_proj_partial_w<dfloat>, smem);
+      k_proj_partial_w<dfloat><<<grid, 256, smem, c->stream>>>(c->d_phi_all.p, c->ld, c->d_phi_off.p, c->d_nocc.p,
+                                                                c->d_nb.p, L.d_kstart.p, L.d_kcount.p, Yd, ldy,
+                                                                active, L.n, nm, part);
+    } else {
+      set_smem_attr((const void*)k_proj_partial_w<double>, smem);
+      k_proj_partial_w<double><<<grid, 256, smem, c->stream>>>(c->d_phi_all.p, c->ld, c->d_phi_off.p, c->d_nocc.p,
+                                                                c->d_nb.p, L.d_kstart.p, L.d_kcount.p, Yd, ldy,
+                                                                active, L.n, nm, part);
+    }
     IKR_CUDA(cudaGetLastError());
     const long long threads = 32LL * L.n * nm;
     k_proj_reduce<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(part, nch, kPC, L.n, nm, L.d_k.p,
@@ -793,12 +808,24 @@ void proj_apply(ikr_ctx* c, const SysList& L, const double2* coef, const C_t<R>*
   ProfScope ps(c, kKidProjApply, 1, L.n, (int)sizeof(R));
   if (sizeof(R) == 8) {
     const int nch = proj_chunks(c, 8);
-    const size_t smem = sizeof(C_t<R>) * (kPC * c->noccmax);
-    set_smem_attr((const void*)k_proj_apply_w<R>, smem);
+    const size_t smem = sizeof(double2) * ((kPC + 8) * c->noccmax);
     dim3 grid(nch, (unsigned)c->k.size());
-    k_proj_apply_w<R><<<grid, 256, smem, c->stream>>>(phi_ptr<R>(c), c->ld, c->d_phi_off.p, c->d_nocc.p,
-                                                       c->d_nb.p, L.d_kstart.p, L.d_kcount.p, coef, c->noccmax, in,
-                                                       alpha, beta, out, ldy, dv, dpart, nch, active);
+    const double2* ind = reinterpret_cast<const double2*>(in);
+    double2* outd = reinterpret_cast<double2*>(out);
+    const double2* dvd = reinterpret_cast<const double2*>(dv);
+    if (c->emulate_fp64) {
+      set_smem_attr((const void*)k_proj_apply_w<dfloat>, smem);
+      k_proj_apply_w<dfloat><<<grid, 256, smem, c->stream>>>(c->d_phi_all.p, c->ld, c->d_phi_off.p, c->d_nocc.p,
+                                                              c->d_nb.p, L.d_kstart.p, L.d_kcount.p, coef, c->noccmax,
+                                                              ind, (double)alpha, (double)beta, outd, ldy, dvd, dpart,
+                                                              nch, active);
+    } else {
+      set_smem_attr((const void*)k_proj_apply_w<double>, smem);
+      k_proj_apply_w<double><<<grid, 256, smem, c->stream>>>(c->d_phi_all.p, c->ld, c->d_phi_off.p, c->d_nocc.p,
+                                                              c->d_nb.p, L.d_kstart.p, L.d_kcount.p, coef, c->noccmax,
+                                                              ind, (double)alpha, (double)beta, outd, ldy, dvd, dpart,
+                                                              nch, active);
+    }
     IKR_CUDA(cudaGetLastError());
     return;
   }
