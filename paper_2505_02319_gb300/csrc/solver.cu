@@ -431,6 +431,7 @@ void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o
   if (kerker) apply_kerker(c, b, bb, o.kerker_alpha);
   else IKR_CUDA(cudaMemcpyAsync(bb, b, sizeof(double) * Ng, cudaMemcpyDeviceToDevice, strm));
   const double b_norm = norm(b);
+  IKR_REQUIRE(std::isfinite(b_norm), IKR_ERR_NUMERIC, "non-finite right-hand side");
   bool x0_nonzero = o.use_x0 != 0;
   if (!x0_nonzero) IKR_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * Ng, strm));
   double s = o.s0 > 0 ? o.s0 : 1.0;
@@ -467,8 +468,8 @@ void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o
     }
     const double beta = norm(r0);
     est = beta;
-    if (!(beta > 0.0)) break;
     IKR_REQUIRE(std::isfinite(beta), IKR_ERR_NUMERIC, "non-finite residual");
+    if (!(beta > 0.0)) break;
     // v_1 = r0 / beta
     w.scal.reserve(64);
     {
