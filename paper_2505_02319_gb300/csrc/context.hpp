@@ -92,6 +92,7 @@ struct Workspace {
   DBuf<double> sys;             // per-system CG scalars (see SysField)
   DBuf<double> val;             // per-system reduced dot products
   DBuf<int> active;
+  DBuf<int> alist;              // compacted indices of the active CG systems
   DBuf<double> deps, ca, cb;    // deps_s and the density coefficients
   DBuf<double> rn;              // per-system residual norms (mixed precision)
   DBuf<double> grid1, grid2, grid3, grid4, grid5, grid6;   // Ng-sized real scratch
@@ -146,6 +147,7 @@ struct Profiler {
 struct ikr_ctx {
   std::string err;
   int N[3] = {0, 0, 0};
+  int nsm = 152;                // streaming multiprocessors of the device
   size_t Ng = 0;
   double lattice[9];            // columns are cell vectors
   double recip[9];              // columns are b_i
@@ -162,6 +164,12 @@ struct ikr_ctx {
   int nxa = 0;
   std::vector<int> xpos;        // active x positions
   ikr::DBuf<int> d_xpos;
+  // one-thread-per-line plane pass: 3 per active x position, ordered by
+  // (x + N0/2) mod N0: that shifted position, the first y of the column's
+  // cyclic y-interval and the interval length - 1; bit x of xmask = x active
+  ikr::DBuf<int> d_xr;
+  unsigned long long xmask = 0;
+  bool reg_plane_ok = false;    // every active column's y-set is one cyclic interval
   ikr::FftPlan plan[3];
   ikr::DBuf<double2> d_tw[3];
   ikr::DBuf<float2> d_tw32[3];

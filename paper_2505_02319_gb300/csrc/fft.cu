@@ -459,7 +459,7 @@ void launch_z_inverse(ikr_ctx* c, const SysList& L, const C_t<R>* sphere, int ld
 
 template <typename R>
 void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, const double* pot_scale,
-                  const int* active, C_t<R>* b4, const C_t<R>* real_in) {
+                  const int* active, C_t<R>* b4, const C_t<R>* real_in, const int* list, int nlist) {
   if (L.n == 0) return;
   ProfScope ps(c, kKidPlane, 1, active ? c->active_hint : L.n, (int)sizeof(R));
   if (sizeof(R) == 8 && c->emulate_fp64) {
@@ -468,6 +468,9 @@ void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, 
                                   reinterpret_cast<const double*>(pot), pot_scale, active,
                                   reinterpret_cast<double2*>(b4), reinterpret_cast<const double2*>(real_in)))
       return;
+  }
+  if constexpr (sizeof(R) == 4) {
+    if (launch_plane_reg(c, L.n, b1, pot, pot_scale, active, b4, real_in, list, nlist)) return;
   }
   if (launch_plane_fast<R>(c, L.n, b1, pot, pot_scale, active, b4, real_in)) return;
   const int Nx = c->N[0], Ny = c->N[1], Nz = c->N[2];
@@ -503,10 +506,23 @@ void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* ou
   IKR_CUDA(cudaGetLastError());
 }
 
-int density_groups(ikr_ctx* c, int nsys) {
-  int g = (2 * 152 + c->N[2] - 1) / c->N[2];
-  if (g > nsys) g = nsys;
-  return g < 1 ? 1 : g;
+// Number of system groups G of a density launch (grid Nz x G, each block
+// walking nsys/G systems): the G that minimises (waves of blocks) x (systems
+// per block) for per_sm resident blocks on each SM, the smaller on ties.
+int density_groups(ikr_ctx* c, int nsys, int per_sm) {
+  const int slots = std::max(1, c->nsm * std::max(per_sm, 1));
+  const int Nz = c->N[2];
+  const int gmax = std::max(1, std::min(nsys, 64));
+  int best = 1;
+  long long best_t = -1;
+  for (int g = 1; g <= gmax; ++g) {
+    const long long t = (long long)((Nz * g + slots - 1) / slots) * ((nsys + g - 1) / g);
+    if (best_t < 0 || t < best_t) {
+      best_t = t;
+      best = g;
+    }
+  }
+  return best;
 }
 
 template <typename R>
@@ -517,27 +533,30 @@ void launch_density(ikr_ctx* c, int nsys, const C_t<R>* b1phi, const C_t<R>* b1d
   IKR_REQUIRE(Nx * Ny <= kDensThreads * kDensMaxPerThread, IKR_ERR_ARG,
               "grid plane too large for the density kernel");
   ProfScope ps(c, kKidDensity, 2, nsys, (int)sizeof(R));
-  const int G = density_groups(c, nsys);
-  c->ws.dens_part.reserve((size_t)G * c->Ng);
   const size_t np = (size_t)Ny * (Nx + 1);
   const size_t smem = sizeof(C_t<R>) * (Nx + Ny + 3 * np) + sizeof(int) * c->nxa;
   bool fast = false;
+  int G = 1;
   if (nsys > 0 && psi_real && b1d) {
     if (sizeof(R) == 8 && c->emulate_fp64)
-      fast = launch_density_fast<dfloat>(c, nsys, G, reinterpret_cast<const double2*>(b1d),
-                                         reinterpret_cast<const double2*>(psi_real), coef_a, coef_b,
-                                         c->ws.dens_part.p);
-    if (!fast) fast = launch_density_fast<R>(c, nsys, G, b1d, psi_real, coef_a, coef_b, c->ws.dens_part.p);
+      fast = launch_density_fast<dfloat>(c, nsys, reinterpret_cast<const double2*>(b1d),
+                                         reinterpret_cast<const double2*>(psi_real), coef_a, coef_b, &G);
+    if (!fast) fast = launch_density_fast<R>(c, nsys, b1d, psi_real, coef_a, coef_b, &G);
   }
   if (fast) {
   } else if (nsys > 0) {
     set_smem(k_density<R>, smem);
+    int per_sm = 1;
+    IKR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_density<R>, kDensThreads, smem));
+    G = density_groups(c, nsys, per_sm);
+    c->ws.dens_part.reserve((size_t)G * c->Ng);
     dim3 grid(Nz, G);
     k_density<R><<<grid, kDensThreads, smem, c->stream>>>(
         b1phi, b1d, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa, c->plan[0], c->plan[1], Nz,
         tw_ptr<R>(c, 0), tw_ptr<R>(c, 1), coef_a, coef_b, nsys, G, c->ws.dens_part.p, psi_real);
     IKR_CUDA(cudaGetLastError());
   } else {
+    c->ws.dens_part.reserve(c->Ng);
     IKR_CUDA(cudaMemsetAsync(c->ws.dens_part.p, 0, sizeof(double) * G * c->Ng, c->stream));
   }
   dim3 tgrid((Nx + 31) / 32, (Nz + 31) / 32, Ny);
@@ -601,7 +620,7 @@ void full_fft(ikr_ctx* c, double2* data, bool inverse) {
   template void launch_z_inverse<R>(ikr_ctx*, const SysList&, const C_t<R>*, int, const int*,     \
                                     C_t<R>*);                                                       \
   template void launch_plane<R>(ikr_ctx*, const SysList&, const C_t<R>*, const R*, const double*,  \
-                                const int*, C_t<R>*, const C_t<R>*);                                \
+                                const int*, C_t<R>*, const C_t<R>*, const int*, int);               \
   template void launch_synth_planes<R>(ikr_ctx*, int, const C_t<R>*, C_t<R>*);                      \
   template void launch_z_forward<R>(ikr_ctx*, const SysList&, const C_t<R>*, C_t<R>*, int,         \
                                     const C_t<R>*, const double*, bool, const int*, double*);       \

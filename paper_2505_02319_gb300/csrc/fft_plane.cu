@@ -458,13 +458,19 @@ bool try_launch(ikr_ctx* c, int nsys, const typename io<R>::cx* b1, const typena
 }
 
 template <typename R, int NX, int NY>
-bool try_density(ikr_ctx* c, int nsys, int ngroups, const typename io<R>::cx* b1d,
-                 const typename io<R>::cx* psir, const double* ca, const double* cb, double* part) {
+bool try_density(ikr_ctx* c, int nsys, const typename io<R>::cx* b1d, const typename io<R>::cx* psir,
+                 const double* ca, const double* cb, int* ngroups_out) {
   if (c->N[0] != NX || c->N[1] != NY) return false;
   using G = PlaneGeom<C_t<R>, NX, NY>;
   const size_t smem = sizeof(C_t<R>) * (NX + NY + (size_t)G::PL * G::plane) + sizeof(int) * c->nxa;
   if (smem > 227 * 1024) return false;
   IKR_CUDA(cudaFuncSetAttribute(k_density_t<R, NX, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 1;
+  IKR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_density_t<R, NX, NY>, 256, smem));
+  const int ngroups = density_groups(c, nsys, per_sm);
+  c->ws.dens_part.reserve((size_t)ngroups * c->Ng);
+  double* part = c->ws.dens_part.p;
+  *ngroups_out = ngroups;
   dim3 grid(c->N[2], ngroups);
   k_density_t<R, NX, NY><<<grid, 256, smem, c->stream>>>(b1d, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa,
                                                           c->N[2], twp<R>(c, 0), twp<R>(c, 1), psir, ca, cb,
@@ -476,22 +482,22 @@ bool try_density(ikr_ctx* c, int nsys, int ngroups, const typename io<R>::cx* b1
 }  // namespace
 
 template <typename R>
-bool launch_density_fast(ikr_ctx* c, int nsys, int ngroups, const typename io<R>::cx* b1d,
-                         const typename io<R>::cx* psir, const double* ca, const double* cb, double* part) {
-  return try_density<R, 48, 48>(c, nsys, ngroups, b1d, psir, ca, cb, part) ||
-         try_density<R, 32, 32>(c, nsys, ngroups, b1d, psir, ca, cb, part) ||
-         try_density<R, 40, 40>(c, nsys, ngroups, b1d, psir, ca, cb, part) ||
-         try_density<R, 96, 96>(c, nsys, ngroups, b1d, psir, ca, cb, part) ||
-         try_density<R, 12, 12>(c, nsys, ngroups, b1d, psir, ca, cb, part) ||
-         try_density<R, 10, 12>(c, nsys, ngroups, b1d, psir, ca, cb, part) ||
-         try_density<R, 24, 24>(c, nsys, ngroups, b1d, psir, ca, cb, part);
+bool launch_density_fast(ikr_ctx* c, int nsys, const typename io<R>::cx* b1d, const typename io<R>::cx* psir,
+                         const double* ca, const double* cb, int* ngroups) {
+  return try_density<R, 48, 48>(c, nsys, b1d, psir, ca, cb, ngroups) ||
+         try_density<R, 32, 32>(c, nsys, b1d, psir, ca, cb, ngroups) ||
+         try_density<R, 40, 40>(c, nsys, b1d, psir, ca, cb, ngroups) ||
+         try_density<R, 96, 96>(c, nsys, b1d, psir, ca, cb, ngroups) ||
+         try_density<R, 12, 12>(c, nsys, b1d, psir, ca, cb, ngroups) ||
+         try_density<R, 10, 12>(c, nsys, b1d, psir, ca, cb, ngroups) ||
+         try_density<R, 24, 24>(c, nsys, b1d, psir, ca, cb, ngroups);
 }
-template bool launch_density_fast<float>(ikr_ctx*, int, int, const float2*, const float2*, const double*,
-                                         const double*, double*);
-template bool launch_density_fast<double>(ikr_ctx*, int, int, const double2*, const double2*, const double*,
-                                          const double*, double*);
-template bool launch_density_fast<dfloat>(ikr_ctx*, int, int, const double2*, const double2*, const double*,
-                                          const double*, double*);
+template bool launch_density_fast<float>(ikr_ctx*, int, const float2*, const float2*, const double*,
+                                         const double*, int*);
+template bool launch_density_fast<double>(ikr_ctx*, int, const double2*, const double2*, const double*,
+                                          const double*, int*);
+template bool launch_density_fast<dfloat>(ikr_ctx*, int, const double2*, const double2*, const double*,
+                                          const double*, int*);
 
 // Compile-time plane shapes of the supported grids; false: use the generic kernel.
 template <typename R>

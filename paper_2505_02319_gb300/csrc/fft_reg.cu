@@ -1,0 +1,276 @@
+// FP32 plane pass of the batched H_k application with one thread per line.
+//
+// Same result as k_plane_t (fft_plane.cu): for each system and z-plane,
+// the inverse y-transforms of the active x positions, the inverse x-transforms
+// of every row, the product with the potential row, and the forward
+// transforms back, restricted to the sphere columns (the y/x part of the
+// pruned F^-1 V F of eq. fft_ifft).  Here a whole line of length N <= 48 lives
+// in the registers of one thread, so a transform needs no exchange between
+// threads: the shared-memory traffic is one load and one store per element and
+// phase, and every twiddle factor is a compile-time constant (ct_trig.hpp).
+// Loads and stores are also pruned to the elements that can be non-zero:
+//   - a y-line reads only the y-interval of its sphere column and writes back
+//     only that interval after the forward transform;
+//   - an x-line reads and writes only the active x positions (all positions
+//     when the input is a real-space plane).
+// One block holds one z-plane of PL systems and the potential plane, staged
+// once for the PL systems.  Shared-memory layout (bank-conflict free for all
+// phases with PL = 16 / (lanes per row group)): column x of a row is stored
+// at (x + NX/2) mod NX, which makes the active x positions of a centred sphere
+// contiguous; the row stride ldp is odd and the plane stride is 16/PL modulo
+// 16 elements.
+#include "ct_trig.hpp"
+#include "ops.hpp"
+
+namespace ikr {
+
+namespace {
+
+// a * W_N^X (forward W = e^{-2 pi i/N}; conjugate for the inverse)
+template <typename C, int N, int X, bool INV>
+__device__ __forceinline__ C twmul(C a) {
+  constexpr int x = X % N;
+  if constexpr (x == 0) {
+    return a;
+  } else if constexpr (2 * x == N) {
+    return mk<C>(-a.x, -a.y);
+  } else if constexpr (4 * x == N) {
+    return rot<C, INV>(a);
+  } else if constexpr (4 * x == 3 * N) {
+    return rot<C, !INV>(a);
+  } else {
+    using R = decltype(C::x);
+    constexpr double c = CtTwiddle<N, x>::c;
+    constexpr double s = INV ? CtTwiddle<N, x>::s : -CtTwiddle<N, x>::s;
+    const R cr = R(c), sr = R(s);
+    return mk<C>(a.x * cr - a.y * sr, a.x * sr + a.y * cr);
+  }
+}
+
+// u[p][k2] *= W_E^{p k2} for p in [p0, P), k2 in [k, Q), unrolled at compile time
+template <typename C, int E, int P, int Q, bool INV, int p, int k>
+struct TwiddlePass {
+  __device__ __forceinline__ static void run(C (&u)[P][Q]) {
+    if constexpr (p < P) {
+      if constexpr (k < Q) {
+        u[p][k] = twmul<C, E, p * k, INV>(u[p][k]);
+        TwiddlePass<C, E, P, Q, INV, p, k + 1>::run(u);
+      } else {
+        TwiddlePass<C, E, P, Q, INV, p + 1, 1>::run(u);
+      }
+    }
+  }
+};
+
+// E-point DFT in registers, natural order in and out, compile-time twiddles.
+// E = P Q with the factors of fft_plane.cu's Split (4 first, then 2, 3, 5):
+//   X_{k2 + Q k1} = sum_p W_P^{p k1} W_E^{p k2} sum_q x_{p + P q} W_Q^{q k2}.
+template <int E> struct CtSplit {
+  static constexpr bool base = (E == 2 || E == 3 || E == 4 || E == 5);
+  static constexpr int P = base ? E : (E % 4 == 0) ? 4 : (E % 2 == 0) ? 2 : (E % 3 == 0) ? 3 : 5;
+  static constexpr int Q = E / P;
+};
+
+template <typename C, int E, bool INV> struct CtFft {
+  __device__ __forceinline__ static void run(C* v) {
+    constexpr int P = CtSplit<E>::P, Q = CtSplit<E>::Q;
+    if constexpr (Q == 1) {
+      Dft<C, E, INV>::run(v);
+    } else {
+      C u[P][Q];
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int q = 0; q < Q; ++q) u[p][q] = v[p + P * q];
+#pragma unroll
+      for (int p = 0; p < P; ++p) CtFft<C, Q, INV>::run(u[p]);
+      TwiddlePass<C, E, P, Q, INV, 1, 1>::run(u);
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) {
+        C w[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) w[p] = u[p][k2];
+        Dft<C, P, INV>::run(w);
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) v[k2 + Q * k1] = w[k1];
+      }
+    }
+  }
+};
+template <typename C, bool INV> struct CtFft<C, 1, INV> {
+  __device__ __forceinline__ static void run(C*) {}
+};
+
+}  // namespace
+
+template <int NX, int NY> struct RegGeom {
+  static constexpr int PL = NY >= 32 ? 4 : (NY >= 16 ? 8 : 16);   // systems per block
+  static constexpr int ldp = NX | 1;                                // odd row stride
+  static constexpr int ps0 = NY * ldp;
+  static constexpr int PS = ps0 + (((16 / PL) - ps0) % 16 + 16) % 16;   // plane stride = 16/PL mod 16
+  static constexpr int NTH = (PL * NY + 31) / 32 * 32;
+  static constexpr int SH = NX / 2;
+  static constexpr size_t smem(int nxa) {
+    return sizeof(float2) * (size_t)PL * PS + sizeof(float) * (size_t)NY * ldp + sizeof(int) * 3 * (size_t)nxa;
+  }
+};
+
+template <int NX, int NY>
+__global__ void __launch_bounds__(RegGeom<NX, NY>::NTH)
+    k_plane_r(const float2* __restrict__ b1, int nc, int ncp, const int* __restrict__ col_xy,
+              const int* __restrict__ xr, int nxa, unsigned long long xmask, int Nz,
+              const float* __restrict__ pot, const double* __restrict__ pot_scale,
+              const int* __restrict__ active, int nsys, const int* __restrict__ list,
+              float2* __restrict__ b4, const float2* __restrict__ real_in) {
+  using G = RegGeom<NX, NY>;
+  constexpr int PL = G::PL, ldp = G::ldp, PS = G::PS, NTH = G::NTH, SH = G::SH;
+  const int iz = blockIdx.x;
+  __shared__ int live[PL];   // system of slot j, or -1
+  extern __shared__ float4 smem_r[];
+  float2* planes = reinterpret_cast<float2*>(smem_r);
+  float* pot_s = reinterpret_cast<float*>(planes + PL * PS);
+  int* xr_s = reinterpret_cast<int*>(pot_s + NY * ldp);
+  if (threadIdx.x < PL) {
+    const int i = blockIdx.y * PL + threadIdx.x;
+    int s = -1;
+    if (i < nsys) {
+      s = list ? list[i] : i;
+      if (active && !active[s]) s = -1;
+    }
+    live[threadIdx.x] = s;
+  }
+  __syncthreads();
+  int nlive = 0;
+#pragma unroll
+  for (int j = 0; j < PL; ++j) nlive += live[j] >= 0;
+  if (nlive == 0) return;   // uniform over the block
+  const float2 zero = make_float2(0.f, 0.f);
+  for (int e = threadIdx.x; e < NY * NX; e += NTH) {
+    const int iy = e / NX, ix = e - iy * NX;
+    pot_s[iy * ldp + ix] = pot[(size_t)iz * NY * NX + e];
+  }
+  for (int e = threadIdx.x; e < 3 * nxa; e += NTH) xr_s[e] = xr[e];
+  if (real_in) {
+    for (int e = threadIdx.x; e < PL * NY * NX; e += NTH) {
+      const int j = e / (NY * NX), r = e - j * (NY * NX);
+      if (live[j] < 0) continue;
+      const int iy = r / NX, ix = r - iy * NX;
+      const int px = ix + SH >= NX ? ix + SH - NX : ix + SH;
+      planes[j * PS + iy * ldp + px] = real_in[((size_t)live[j] * Nz + iz) * NY * NX + r];
+    }
+  } else {
+    for (int e = threadIdx.x; e < PL * nc; e += NTH) {
+      const int j = e / nc, col = e - j * nc;
+      if (live[j] < 0) continue;
+      const int ix = col_xy[2 * col], iy = col_xy[2 * col + 1];
+      const int px = ix + SH >= NX ? ix + SH - NX : ix + SH;
+      planes[j * PS + iy * ldp + px] = b1[((size_t)live[j] * Nz + iz) * ncp + col];
+    }
+  }
+  __syncthreads();
+  // inverse y-lines of the active x positions: only the column's y-interval is non-zero
+  if (!real_in) {
+    for (int it = threadIdx.x; it < PL * nxa; it += NTH) {
+      const int l = it / PL, j = it - l * PL;
+      if (live[j] < 0) continue;
+      const int px = xr_s[3 * l], ylo = xr_s[3 * l + 1], span = xr_s[3 * l + 2];
+      float2* colp = planes + j * PS + px;
+      float2 v[NY];
+#pragma unroll
+      for (int y = 0; y < NY; ++y) {
+        int d = y - ylo;
+        d += d < 0 ? NY : 0;
+        v[y] = d <= span ? colp[y * ldp] : zero;
+      }
+      CtFft<float2, NY, true>::run(v);
+#pragma unroll
+      for (int y = 0; y < NY; ++y) colp[y * ldp] = v[y];
+    }
+    __syncthreads();
+  }
+  // x-lines: inverse transform (unless real-space input), potential, forward transform
+  {
+    const float sc = pot_scale ? (float)*pot_scale : 1.f;
+    const unsigned long long m = real_in ? ~0ull : xmask;
+    for (int it = threadIdx.x; it < PL * NY; it += NTH) {
+      const int iy = it / PL, j = it - iy * PL;
+      if (live[j] < 0) continue;
+      float2* row = planes + j * PS + iy * ldp;
+      const float* prow = pot_s + iy * ldp;
+      float2 v[NX];
+#pragma unroll
+      for (int x = 0; x < NX; ++x) v[x] = ((m >> x) & 1ull) ? row[(x + SH) % NX] : zero;
+      if (!real_in) CtFft<float2, NX, true>::run(v);
+#pragma unroll
+      for (int x = 0; x < NX; ++x) v[x] = cscale(v[x], prow[x] * sc);
+      CtFft<float2, NX, false>::run(v);
+#pragma unroll
+      for (int x = 0; x < NX; ++x)
+        if ((xmask >> x) & 1ull) row[(x + SH) % NX] = v[x];
+    }
+  }
+  __syncthreads();
+  // forward y-lines of the active x positions; only the sphere interval is kept
+  for (int it = threadIdx.x; it < PL * nxa; it += NTH) {
+    const int l = it / PL, j = it - l * PL;
+    if (live[j] < 0) continue;
+    const int px = xr_s[3 * l], ylo = xr_s[3 * l + 1], span = xr_s[3 * l + 2];
+    float2* colp = planes + j * PS + px;
+    float2 v[NY];
+#pragma unroll
+    for (int y = 0; y < NY; ++y) v[y] = colp[y * ldp];
+    CtFft<float2, NY, false>::run(v);
+#pragma unroll
+    for (int y = 0; y < NY; ++y) {
+      int d = y - ylo;
+      d += d < 0 ? NY : 0;
+      if (d <= span) colp[y * ldp] = v[y];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < PL * nc; e += NTH) {
+    const int j = e / nc, col = e - j * nc;
+    if (live[j] < 0) continue;
+    const int ix = col_xy[2 * col], iy = col_xy[2 * col + 1];
+    const int px = ix + SH >= NX ? ix + SH - NX : ix + SH;
+    b4[((size_t)live[j] * Nz + iz) * ncp + col] = planes[j * PS + iy * ldp + px];
+  }
+}
+
+namespace {
+
+template <int NX, int NY>
+bool try_reg(ikr_ctx* c, int nsys, const float2* b1, const float* pot, const double* pot_scale, const int* active,
+             float2* b4, const float2* real_in, const int* list) {
+  if (c->N[0] != NX || c->N[1] != NY) return false;
+  using G = RegGeom<NX, NY>;
+  const size_t smem = G::smem(c->nxa);
+  if (smem > 200 * 1024) return false;
+  IKR_CUDA(cudaFuncSetAttribute(k_plane_r<NX, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int Nz = c->N[2];
+  dim3 grid(Nz, (nsys + G::PL - 1) / G::PL);
+  k_plane_r<NX, NY><<<grid, G::NTH, smem, c->stream>>>(b1, c->nc, c->ncp, c->d_col_xy.p, c->d_xr.p, c->nxa,
+                                                       c->xmask, Nz, pot, pot_scale, active, nsys, list, b4,
+                                                       real_in);
+  IKR_CUDA(cudaGetLastError());
+  return true;
+}
+
+}  // namespace
+
+bool launch_plane_reg(ikr_ctx* c, int nsys, const float2* b1, const float* pot, const double* pot_scale,
+                      const int* active, float2* b4, const float2* real_in, const int* list, int nlist) {
+  if (!c->reg_plane_ok || nsys == 0) return false;
+  if (list) {
+    if (nlist <= 0) return true;   // nothing active
+    nsys = nlist;
+  }
+  return try_reg<48, 48>(c, nsys, b1, pot, pot_scale, active, b4, real_in, list) ||
+         try_reg<32, 32>(c, nsys, b1, pot, pot_scale, active, b4, real_in, list) ||
+         try_reg<40, 40>(c, nsys, b1, pot, pot_scale, active, b4, real_in, list) ||
+         try_reg<24, 24>(c, nsys, b1, pot, pot_scale, active, b4, real_in, list) ||
+         try_reg<12, 12>(c, nsys, b1, pot, pot_scale, active, b4, real_in, list) ||
+         try_reg<10, 12>(c, nsys, b1, pot, pot_scale, active, b4, real_in, list);
+}
+
+}  // namespace ikr

@@ -441,10 +441,12 @@ __global__ void __launch_bounds__(kEC) k_cg_p(int mode, C_t<R>* __restrict__ Pv,
 //   stage 1 (alpha): alpha = rz / <p, Ap>   (non-positive or non-finite -> numeric stop);
 //                    resets the active counter
 //   stage 2 (check): iters += 1; stop when ||r||^2 <= tol^2 or iters >= maxit;
-//                    counts the systems that stay active
+//                    counts the systems that stay active and, given a list,
+//                    writes their indices to it (compacted, in arrival order)
 //   stage 3 (beta):  beta = rz_new / rz; rz = rz_new
 __global__ void k_cg_scalars(int stage, double* __restrict__ sys, const double* __restrict__ part, int nparts,
-                             int nsys, int maxit, int* __restrict__ active, int* __restrict__ counter) {
+                             int nsys, int maxit, int* __restrict__ active, int* __restrict__ counter,
+                             int* __restrict__ list) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (stage == 1 && s == 0 && counter) *counter = 0;
   if (s >= nsys || !active[s]) return;
@@ -481,7 +483,8 @@ __global__ void k_cg_scalars(int stage, double* __restrict__ sys, const double* 
       f[kSysStatus * nsys + s] = 3;
       active[s] = 0;
     } else if (counter) {
-      atomicAdd(counter, 1);
+      const int slot = atomicAdd(counter, 1);
+      if (list) list[slot] = s;   // any order: each system's work is independent of its slot
     }
   } else {
     const double rz = val;
@@ -870,9 +873,10 @@ void cg_p(ikr_ctx* c, const SysList& L, int mode, CgVecs<R>& v, const double* sy
 }
 
 void cg_scalars(ikr_ctx* c, int stage, double* sys, const double* part, int nparts, int nsys, int maxit,
-                int* active, int* counter) {
+                int* active, int* counter, int* list) {
   ProfScope ps(c, kKidScalar, 1);
-  k_cg_scalars<<<(nsys + 127) / 128, 128, 0, c->stream>>>(stage, sys, part, nparts, nsys, maxit, active, counter);
+  k_cg_scalars<<<(nsys + 127) / 128, 128, 0, c->stream>>>(stage, sys, part, nparts, nsys, maxit, active, counter,
+                                                          list);
   IKR_CUDA(cudaGetLastError());
 }
 

@@ -20,20 +20,28 @@ void launch_z_inverse(ikr_ctx* c, const SysList& L, const C_t<R>* sphere, int ld
                       C_t<R>* b1);
 template <typename R>
 void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, const double* pot_scale,
-                  const int* active, C_t<R>* b4, const C_t<R>* real_in = nullptr);
+                  const int* active, C_t<R>* b4, const C_t<R>* real_in = nullptr, const int* list = nullptr,
+                  int nlist = 0);
 template <typename R> void launch_synth_planes(ikr_ctx* c, int nsys, const C_t<R>* b1, C_t<R>* out);
 template <typename R>
 bool launch_plane_fast(ikr_ctx* c, int nsys, const typename io<R>::cx* b1, const typename io<R>::real* pot,
                        const double* pot_scale, const int* active, typename io<R>::cx* b4,
                        const typename io<R>::cx* real_in);
+// FP32 plane pass with one thread per line (fft_reg.cu); false: shape not covered
+// list: the nlist systems to process (a compacted active set), else all nsys under `active`
+bool launch_plane_reg(ikr_ctx* c, int nsys, const float2* b1, const float* pot, const double* pot_scale,
+                      const int* active, float2* b4, const float2* real_in, const int* list, int nlist);
 template <typename R>
 void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* out, int ld,
                       const C_t<R>* psi, const double* shift, bool kinetic, const int* active,
                       double* dpart = nullptr);
 int zf_chunks(ikr_ctx* c);    // dot partials per system written by launch_z_forward
+// Density partial planes by the compile-time kernel (fft_plane.cu) into
+// c->ws.dens_part; *ngroups = the number of partial planes.  false: shape not covered.
 template <typename R>
-bool launch_density_fast(ikr_ctx* c, int nsys, int ngroups, const typename io<R>::cx* b1d,
-                         const typename io<R>::cx* psir, const double* ca, const double* cb, double* part);
+bool launch_density_fast(ikr_ctx* c, int nsys, const typename io<R>::cx* b1d, const typename io<R>::cx* psir,
+                         const double* ca, const double* cb, int* ngroups);
+int density_groups(ikr_ctx* c, int nsys, int per_sm);
 template <typename R>
 void launch_density(ikr_ctx* c, int nsys, const C_t<R>* b1phi, const C_t<R>* b1d,
                     const double* coef_a, const double* coef_b, double* out, double scale,
@@ -63,7 +71,7 @@ void cg_xr(ikr_ctx* c, const SysList& L, int mode, CgVecs<R>& v, const double* s
 template <typename R>
 void cg_p(ikr_ctx* c, const SysList& L, int mode, CgVecs<R>& v, const double* sys, const int* active);
 void cg_scalars(ikr_ctx* c, int stage, double* sys, const double* part, int nparts, int nsys, int maxit,
-                int* active, int* counter);
+                int* active, int* counter, int* list = nullptr);
 void count_active(ikr_ctx* c, const int* active, int n, int* dout);
 void chi0_sys(ikr_ctx* c, const SysList& L, const double2* M, double* deps, double2* coefP);
 void occupation_response(ikr_ctx* c, const double* deps, double* coef_a, double* coef_b, double* deF);

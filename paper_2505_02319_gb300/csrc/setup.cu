@@ -2,6 +2,7 @@
 // pruned FFT geometry, the potential, and the ground state (occupations,
 // Fermi level, density rho and exchange kernel K^xc[rho]).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <map>
 
@@ -62,6 +63,11 @@ double fd_prime(double x) {
 
 void setup_system(ikr_ctx* c, const ikr_system* sys) {
   IKR_REQUIRE(sys, IKR_ERR_ARG, "system is NULL");
+  {
+    int dev = 0;
+    IKR_CUDA(cudaGetDevice(&dev));
+    IKR_CUDA(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
   IKR_REQUIRE(sys->nkpt >= 1 && sys->kpoints && sys->kweights && sys->V, IKR_ERR_ARG,
               "k-points, weights and V are required");
   IKR_REQUIRE(sys->Ecut > 0, IKR_ERR_ARG, "Ecut must be positive");
@@ -167,6 +173,38 @@ void setup_system(ikr_ctx* c, const ikr_system* sys) {
   c->nxa = (int)xs.size();
   upload(c->d_col_xy, colxy, st);
   upload(c->d_xpos, c->xpos, st);
+  {
+    const int N0 = c->N[0], N1 = c->N[1];
+    std::map<int, std::vector<int>> ys;   // active x -> y of its columns
+    for (size_t i = 0; i < c->col_ix.size(); ++i) ys[c->col_ix[i]].push_back(c->col_iy[i]);
+    std::vector<std::array<int, 3>> rows;
+    bool ok = N0 <= 64;
+    unsigned long long mask = 0;
+    for (auto& kv : ys) {
+      std::vector<char> has(N1, 0);
+      for (int y : kv.second) has[y] = 1;
+      const int n = (int)kv.second.size();
+      int ylo = 0, runs = 0;
+      if (n == N1) {
+        runs = 1;
+      } else {
+        for (int y = 0; y < N1; ++y)
+          if (has[y] && !has[(y + N1 - 1) % N1]) {
+            ylo = y;
+            ++runs;
+          }
+      }
+      ok = ok && runs == 1;
+      rows.push_back({(kv.first + N0 / 2) % N0, ylo, n - 1});
+      if (kv.first < 64) mask |= 1ull << kv.first;
+    }
+    std::sort(rows.begin(), rows.end());
+    std::vector<int> xr;
+    for (const auto& r : rows) xr.insert(xr.end(), r.begin(), r.end());
+    c->xmask = mask;
+    c->reg_plane_ok = ok;
+    upload(c->d_xr, xr, st);
+  }
   // per-k column info and kinetic energies
   const int nk = sys->nkpt;
   std::vector<int> colinfo((size_t)nk * c->nc * 3, 0);

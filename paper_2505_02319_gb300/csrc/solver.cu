@@ -56,6 +56,7 @@ void ensure_workspace(ikr_ctx* c, int n) {
   w.sys.reserve((size_t)kSysFields * std::max(n, 1));
   w.val.reserve(std::max(n, 1));
   w.active.reserve(std::max(n, 1));
+  w.alist.reserve(std::max(n, 1));
   w.deps.reserve(std::max(n, 1));
   w.ca.reserve(std::max(n, 1));
   w.cb.reserve(std::max(n, 1));
@@ -128,8 +129,10 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
   }
   const cudaStream_t strm = c->stream;
   IKR_CUDA(cudaMemcpyAsync(w.sys.p, hs.data(), sizeof(double) * hs.size(), cudaMemcpyHostToDevice, strm));
-  std::vector<int> ones(n, 1);
+  std::vector<int> ones(n, 1), all(n);
+  for (int s = 0; s < n; ++s) all[s] = s;
   IKR_CUDA(cudaMemcpyAsync(w.active.p, ones.data(), sizeof(int) * n, cudaMemcpyHostToDevice, strm));
+  IKR_CUDA(cudaMemcpyAsync(w.alist.p, all.data(), sizeof(int) * n, cudaMemcpyHostToDevice, strm));
   double* sys = w.sys.p;
   int* act = w.active.p;
   const int pch = proj_chunks(c, (int)sizeof(R)), cch = cg_chunks(c);
@@ -147,12 +150,13 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
     // Phi^H (H - eps) P = (Lambda - eps) Phi^H P = 0 for the eigenvectors Phi, so
     // Q W = W up to the eigenpair residual: W is not projected again.
     launch_z_inverse<R>(c, L, v.P, c->ld, act, Bufs<R>::b1(c));
-    launch_plane<R>(c, L, Bufs<R>::b1(c), Bufs<R>::pot(c), nullptr, act, Bufs<R>::b4(c));
+    launch_plane<R>(c, L, Bufs<R>::b1(c), Bufs<R>::pot(c), nullptr, act, Bufs<R>::b4(c), nullptr, w.alist.p,
+                    c->active_hint);
     launch_z_forward<R>(c, L, Bufs<R>::b4(c), v.W, c->ld, v.P, sys + kSysShift * n, true, act, w.dpart.p);
     cg_scalars(c, 1, sys, w.dpart.p, zf_chunks(c), n, maxit, act, dcount);
     // x += alpha p, r -= alpha W, z = M^-1 r, ||r||^2, stopping test
     cg_xr<R>(c, L, 1, v, sys, act, w.dpart.p);
-    cg_scalars(c, 2, sys, w.dpart.p, cch, n, maxit, act, dcount);
+    cg_scalars(c, 2, sys, w.dpart.p, cch, n, maxit, act, dcount, w.alist.p);
     // z = Q z, beta, p = z + beta p
     proj_coef<R>(c, L, v.Z, c->ld, act, coef);
     proj_apply<R>(c, L, coef, v.Z, R(1), R(-1), v.Z, c->ld, v.R, w.dpart.p, act);
