@@ -103,7 +103,8 @@ class Clocks:
 # ------------------------------------------------------------ algorithmic work --
 def plane_pass_work(ctx_geom, fp_bytes):
     """Algorithmic bytes and flops of one (system, z-plane-pass) unit of the
-    plane kernel: the 2D transforms of the pruned plane, see the design doc."""
+    plane kernel: the 2D transforms of the pruned plane (y-lines of the nxa
+    active x positions, all x-lines, the potential product, and back)."""
     import math
     Nx, Ny, Nz, nc, nxa = ctx_geom
     c = 2 * fp_bytes                               # complex element size
@@ -298,40 +299,58 @@ def run_ours(args, rank, world, local_rank):
 
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flops x max SM clock
-FP64_PEAK_TFLOPS = 1.20                              # FMA-chain probe on this machine's GB300
+FP32_INSTR_PEAK = FP32_PEAK_TFLOPS / 2              # FP32 instructions (FMA = 1), in T/s
+FP64_PEAK_TFLOPS = 1.20                              # FP64 FMA-chain rate measured on a GB300
+# FP32 instructions per FP64-equivalent flop of the double-float FFT: an add is
+# TwoSum + two low-part adds (8), a product one FMUL + three FFMA (4); the
+# radix-4/3 butterflies and twiddles of the plane pass mix about 2 adds : 1 product
+DF64_INSTR_PER_FLOP = (2 * 8 + 4) / 3.0
+DF64_PEAK_TFLOPS = FP32_INSTR_PEAK / DF64_INSTR_PER_FLOP
 
 
 def roofline(d, geom, peaks):
-    """Roofline of the plane kernel (the H_k pass of the Sternheimer CG), from
-    the library's CUDA events over the timed steps: achieved = algorithmic
+    """Roofline of the plane pass (the H_k application of the Sternheimer CG),
+    from the library's CUDA events over the timed steps: achieved = algorithmic
     flops of the units (system-plane passes) the launches processed / their
-    summed duration, separately for the FP32 (CG) and FP64 (right-hand side,
-    defect-correction residual) launches."""
+    summed duration.  Two kernels do this work in the mixed path: the FP32 pass
+    of the CG (k_plane_r) and the FP64-accurate pass of the right-hand sides and
+    defect-correction residuals (double-float on the FP32 pipe, k_plane_t<dfloat>).
+    The one with the larger total time is reported, the other is attached."""
     b32, f32 = plane_pass_work(geom, 4)
     b64, f64 = plane_pass_work(geom, 8)
-    out = None
+    entries = []
     if d["ms_fp32"] > 0 and d["units_fp32"]:
         t = d["ms_fp32"] * 1e-3
         calls = max(d["calls_fp32"], 1)
         tfl = d["units_fp32"] * f32 / t / 1e12
         gbs = d["units_fp32"] * b32 / t / 1e9
-        out = {"kernel": "k_plane_t<float,48,48> (H_k plane pass, FP32 CG)", "bound": "alu",
-               "achieved": tfl, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tfl / FP32_PEAK_TFLOPS,
-               "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-               "avg_launch_ms": d["ms_fp32"] / calls, "units_per_launch": d["units_fp32"] / calls,
-               "algorithmic_flops_per_unit": f32, "algorithmic_bytes_per_unit": b32,
-               "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / peaks["hbm_gbs"]}
+        entries.append((d["ms_fp32"], {
+            "kernel": "k_plane_r<48,48> (H_k plane pass of the FP32 CG)", "bound": "alu",
+            "achieved": tfl, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tfl / FP32_PEAK_TFLOPS,
+            "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+            "total_ms": d["ms_fp32"], "avg_launch_ms": d["ms_fp32"] / calls,
+            "units_per_launch": d["units_fp32"] / calls, "algorithmic_flops_per_unit": f32,
+            "algorithmic_bytes_per_unit": b32, "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / peaks["hbm_gbs"]}))
     if d["ms_fp64"] > 0 and d["units_fp64"]:
         t = d["ms_fp64"] * 1e-3
+        calls = max(d["calls_fp64"], 1)
         tfl = d["units_fp64"] * f64 / t / 1e12
-        r64 = {"kernel": "k_plane<double> (H_k plane pass, FP64)", "bound": "alu", "achieved": tfl,
-               "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tfl / FP64_PEAK_TFLOPS,
-               "avg_launch_ms": d["ms_fp64"] / max(d["calls_fp64"], 1),
-               "units_per_launch": d["units_fp64"] / max(d["calls_fp64"], 1)}
-        if out is None:
-            out = r64
-        else:
-            out["fp64_launches"] = r64
+        entries.append((d["ms_fp64"], {
+            "kernel": "k_plane_t<dfloat,48,48> (FP64-accurate plane pass, double-float on the FP32 pipe)",
+            "bound": "alu", "achieved": tfl, "peak": DF64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64-equivalent)",
+            "frac": tfl / DF64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": f"derived: FP32 instruction peak / {DF64_INSTR_PER_FLOP:.2f} FP32 instructions "
+                           f"per double-float flop",
+            "vs_native_fp64_peak": tfl / FP64_PEAK_TFLOPS,
+            "total_ms": d["ms_fp64"], "avg_launch_ms": d["ms_fp64"] / calls,
+            "units_per_launch": d["units_fp64"] / calls, "algorithmic_flops_per_unit": f64,
+            "algorithmic_bytes_per_unit": b64}))
+    if not entries:
+        return None
+    entries.sort(key=lambda e: -e[0])
+    out = entries[0][1]
+    if len(entries) > 1:
+        out["other_plane_kernel"] = entries[1][1]
     return out
 
 

@@ -450,7 +450,10 @@ bool try_launch(ikr_ctx* c, int nsys, const typename io<R>::cx* b1, const typena
   IKR_CUDA(cudaFuncSetAttribute(k_plane_t<R, NX, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int Nz = c->N[2];
   dim3 grid((Nz + G::PL - 1) / G::PL, nsys);
-  k_plane_t<R, NX, NY><<<grid, 256, smem, c->stream>>>(b1, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa, Nz,
+  // double-float: 48 line groups of 4 lanes, so the x-lines of a 48-row plane
+  // take one round and three blocks fit an SM
+  const int nth = std::is_same<R, dfloat>::value ? 192 : 256;
+  k_plane_t<R, NX, NY><<<grid, nth, smem, c->stream>>>(b1, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa, Nz,
                                                         twp<R>(c, 0), twp<R>(c, 1), pot, pot_scale, active, b4,
                                                         real_in);
   IKR_CUDA(cudaGetLastError());

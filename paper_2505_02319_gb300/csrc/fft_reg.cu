@@ -101,6 +101,18 @@ template <typename C, bool INV> struct CtFft<C, 1, INV> {
   __device__ __forceinline__ static void run(C*) {}
 };
 
+// Asynchronous global -> shared copies (cp.async, cached in L1): a thread issues
+// all of its copies of a staging phase back to back and waits once.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 }  // namespace
 
 template <int NX, int NY> struct RegGeom {
@@ -145,28 +157,33 @@ __global__ void __launch_bounds__(RegGeom<NX, NY>::NTH)
   for (int j = 0; j < PL; ++j) nlive += live[j] >= 0;
   if (nlive == 0) return;   // uniform over the block
   const float2 zero = make_float2(0.f, 0.f);
+  const int2* cxy = reinterpret_cast<const int2*>(col_xy);
+#pragma unroll 4
   for (int e = threadIdx.x; e < NY * NX; e += NTH) {
     const int iy = e / NX, ix = e - iy * NX;
-    pot_s[iy * ldp + ix] = pot[(size_t)iz * NY * NX + e];
+    cp_async4(pot_s + iy * ldp + ix, pot + (size_t)iz * NY * NX + e);
   }
-  for (int e = threadIdx.x; e < 3 * nxa; e += NTH) xr_s[e] = xr[e];
+  for (int e = threadIdx.x; e < 3 * nxa; e += NTH) cp_async4(xr_s + e, xr + e);
   if (real_in) {
+#pragma unroll 4
     for (int e = threadIdx.x; e < PL * NY * NX; e += NTH) {
       const int j = e / (NY * NX), r = e - j * (NY * NX);
       if (live[j] < 0) continue;
       const int iy = r / NX, ix = r - iy * NX;
       const int px = ix + SH >= NX ? ix + SH - NX : ix + SH;
-      planes[j * PS + iy * ldp + px] = real_in[((size_t)live[j] * Nz + iz) * NY * NX + r];
+      cp_async8(planes + j * PS + iy * ldp + px, real_in + ((size_t)live[j] * Nz + iz) * NY * NX + r);
     }
   } else {
+#pragma unroll 4
     for (int e = threadIdx.x; e < PL * nc; e += NTH) {
       const int j = e / nc, col = e - j * nc;
       if (live[j] < 0) continue;
-      const int ix = col_xy[2 * col], iy = col_xy[2 * col + 1];
-      const int px = ix + SH >= NX ? ix + SH - NX : ix + SH;
-      planes[j * PS + iy * ldp + px] = b1[((size_t)live[j] * Nz + iz) * ncp + col];
+      const int2 xy = cxy[col];
+      const int px = xy.x + SH >= NX ? xy.x + SH - NX : xy.x + SH;
+      cp_async8(planes + j * PS + xy.y * ldp + px, b1 + ((size_t)live[j] * Nz + iz) * ncp + col);
     }
   }
+  cp_async_wait_all();
   __syncthreads();
   // inverse y-lines of the active x positions: only the column's y-interval is non-zero
   if (!real_in) {
@@ -228,12 +245,13 @@ __global__ void __launch_bounds__(RegGeom<NX, NY>::NTH)
     }
   }
   __syncthreads();
+#pragma unroll 4
   for (int e = threadIdx.x; e < PL * nc; e += NTH) {
     const int j = e / nc, col = e - j * nc;
     if (live[j] < 0) continue;
-    const int ix = col_xy[2 * col], iy = col_xy[2 * col + 1];
-    const int px = ix + SH >= NX ? ix + SH - NX : ix + SH;
-    b4[((size_t)live[j] * Nz + iz) * ncp + col] = planes[j * PS + iy * ldp + px];
+    const int2 xy = cxy[col];
+    const int px = xy.x + SH >= NX ? xy.x + SH - NX : xy.x + SH;
+    b4[((size_t)live[j] * Nz + iz) * ncp + col] = planes[j * PS + xy.y * ldp + px];
   }
 }
 

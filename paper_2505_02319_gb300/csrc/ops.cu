@@ -49,7 +49,13 @@ __global__ void __launch_bounds__(256) k_proj_partial(const C_t<R>* __restrict__
   const int tm = threadIdx.x & 15, ts = threadIdx.x >> 4;   // 16 x 16 threads, 2 x 2 outputs each
   for (int mt = 0; mt < nocc; mt += kTile) {
     for (int st = 0; st < ns; st += kTile) {
-      __syncthreads();
+      // a tile of converged systems is skipped (their partials are never read)
+      int any = 0;
+      if (threadIdx.x < kTile) {
+        const int sl = st + threadIdx.x;
+        any = sl < ns && (!active || active[s0 + sl]);
+      }
+      if (!__syncthreads_or(any)) continue;
       for (int idx = threadIdx.x; idx < kKC * kTile; idx += blockDim.x) {
         const int r = idx / kKC, g = idx - r * kKC;      // r: m (or s) within the tile, g fastest
         const bool gin = g0 + g < nb;
@@ -290,7 +296,13 @@ __global__ void __launch_bounds__(256) k_proj_apply(const C_t<R>* __restrict__ p
 #pragma unroll
     for (int j = 0; j < kSG; ++j) ax[j] = ay[j] = R(0);
     const C* cg = cf + grp * kSG * nocc;
-    for (int m0 = 0; m0 < nocc; m0 += 16) {
+    bool glive = false;   // uniform over the group's warps: groups of converged systems skip the sums
+#pragma unroll
+    for (int j = 0; j < kSG; ++j) {
+      const int sl = sb + grp * kSG + j;
+      glive |= sl < ns && (!active || active[s0 + sl]);
+    }
+    for (int m0 = 0; glive && m0 < nocc; m0 += 16) {
       // the next 16 orbitals at this G are loaded together before use
       C p[16];
 #pragma unroll
@@ -435,8 +447,10 @@ __global__ void __launch_bounds__(kEC) k_cg_p(int mode, C_t<R>* __restrict__ Pv,
   }
 }
 
-// Scalar steps of the CG recurrences, one thread per system.  Each thread first
-// sums its system's nparts partial dot products in fixed order.
+// Scalar steps of the CG recurrences, one warp per system.  The warp first
+// sums its system's nparts partial dot products (lane c takes c, c + 32, ...,
+// then a fixed shuffle tree: the same order on every run); lane 0 then runs
+// the stage.
 //   stage 0 (init):  rz = <r, z>;  iters = 0;  status = 0
 //   stage 1 (alpha): alpha = rz / <p, Ap>   (non-positive or non-finite -> numeric stop);
 //                    resets the active counter
@@ -447,11 +461,13 @@ __global__ void __launch_bounds__(kEC) k_cg_p(int mode, C_t<R>* __restrict__ Pv,
 __global__ void k_cg_scalars(int stage, double* __restrict__ sys, const double* __restrict__ part, int nparts,
                              int nsys, int maxit, int* __restrict__ active, int* __restrict__ counter,
                              int* __restrict__ list) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (stage == 1 && s == 0 && counter) *counter = 0;
-  if (s >= nsys || !active[s]) return;
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (stage == 1 && s == 0 && lane == 0 && counter) *counter = 0;
+  if (s >= nsys || !active[s]) return;   // uniform over the warp
   double val = 0.0;
-  for (int c = 0; c < nparts; ++c) val += part[(size_t)s * nparts + c];
+  for (int c = lane; c < nparts; c += 32) val += part[(size_t)s * nparts + c];
+  val = warp_sum(val);
+  if (lane != 0) return;
   double* f = sys;
   if (stage == 0) {
     f[kSysRz * nsys + s] = val;
@@ -875,8 +891,7 @@ void cg_p(ikr_ctx* c, const SysList& L, int mode, CgVecs<R>& v, const double* sy
 void cg_scalars(ikr_ctx* c, int stage, double* sys, const double* part, int nparts, int nsys, int maxit,
                 int* active, int* counter, int* list) {
   ProfScope ps(c, kKidScalar, 1);
-  k_cg_scalars<<<(nsys + 127) / 128, 128, 0, c->stream>>>(stage, sys, part, nparts, nsys, maxit, active, counter,
-                                                          list);
+  k_cg_scalars<<<(nsys + 3) / 4, 128, 0, c->stream>>>(stage, sys, part, nparts, nsys, maxit, active, counter, list);
   IKR_CUDA(cudaGetLastError());
 }
 
