@@ -170,6 +170,12 @@ struct ikr_ctx {
   ikr::DBuf<int> d_xr;
   unsigned long long xmask = 0;
   bool reg_plane_ok = false;    // every active column's y-set is one cyclic interval
+  // one-thread-per-column z-pass: per k, nc + 1 prefix sums of the column
+  // counts (= the sphere offsets of the columns); zspan = the largest sphere
+  // slice of kZC consecutive columns
+  ikr::DBuf<int> d_colpre;
+  int zspan = 0;
+  bool zreg_ok = false;
   ikr::FftPlan plan[3];
   ikr::DBuf<double2> d_tw[3];
   ikr::DBuf<float2> d_tw32[3];

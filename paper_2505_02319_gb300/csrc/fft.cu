@@ -444,9 +444,13 @@ __global__ void __launch_bounds__(256) k_fft_axis(double2* __restrict__ data, Ff
 
 template <typename R>
 void launch_z_inverse(ikr_ctx* c, const SysList& L, const C_t<R>* sphere, int ld, const int* active,
-                      C_t<R>* b1) {
+                      C_t<R>* b1, const int* list, int nlist) {
   if (L.n == 0) return;
   ProfScope ps(c, kKidZInv, 1, active ? c->active_hint : L.n, (int)sizeof(R));
+  if constexpr (sizeof(R) == 4) {
+    if (list && nlist <= 0 && z_reg_ok(c)) return;   // no active system
+    if (launch_z_inverse_reg(c, list ? nlist : L.n, L.d_k.p, sphere, ld, active, list, b1)) return;
+  }
   const int Nz = c->N[2];
   const int LZ = lines_per_cta(Nz);
   const size_t smem = sizeof(C_t<R>) * (Nz + 2 * LZ * (Nz + 1));
@@ -483,17 +487,25 @@ void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, 
   IKR_CUDA(cudaGetLastError());
 }
 
-int zf_chunks(ikr_ctx* c) {
+int zf_chunks(ikr_ctx* c, int fp_bytes) {
+  if (fp_bytes == 4 && z_reg_ok(c)) return z_reg_chunks(c);
   const int LZ = lines_per_cta(c->N[2]);
   return (c->nc + LZ - 1) / LZ;
 }
+int zf_chunks(ikr_ctx* c) { return std::max(zf_chunks(c, 4), zf_chunks(c, 8)); }
 
 template <typename R>
 void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* out, int ld,
                       const C_t<R>* psi, const double* shift, bool kinetic, const int* active,
-                      double* dpart) {
+                      double* dpart, const int* list, int nlist) {
   if (L.n == 0) return;
   ProfScope ps(c, kKidZFwd, 1, active ? c->active_hint : L.n, (int)sizeof(R));
+  if constexpr (sizeof(R) == 4) {
+    if (list && nlist <= 0 && z_reg_ok(c)) return;   // no active system
+    if (launch_z_forward_reg(c, list ? nlist : L.n, L.d_k.p, b4, out, ld, psi, shift,
+                             kinetic ? kin_all_ptr<R>(c) : nullptr, active, list, dpart))
+      return;
+  }
   const int Nz = c->N[2];
   const int LZ = lines_per_cta(Nz);
   const size_t smem = sizeof(C_t<R>) * (Nz + 2 * LZ * (Nz + 1));
@@ -618,12 +630,13 @@ void full_fft(ikr_ctx* c, double2* data, bool inverse) {
 
 #define IKR_INST(R)                                                                                 \
   template void launch_z_inverse<R>(ikr_ctx*, const SysList&, const C_t<R>*, int, const int*,     \
-                                    C_t<R>*);                                                       \
+                                    C_t<R>*, const int*, int);                                      \
   template void launch_plane<R>(ikr_ctx*, const SysList&, const C_t<R>*, const R*, const double*,  \
                                 const int*, C_t<R>*, const C_t<R>*, const int*, int);               \
   template void launch_synth_planes<R>(ikr_ctx*, int, const C_t<R>*, C_t<R>*);                      \
   template void launch_z_forward<R>(ikr_ctx*, const SysList&, const C_t<R>*, C_t<R>*, int,         \
-                                    const C_t<R>*, const double*, bool, const int*, double*);       \
+                                    const C_t<R>*, const double*, bool, const int*, double*,        \
+                                    const int*, int);                                               \
   template void launch_density<R>(ikr_ctx*, int, const C_t<R>*, const C_t<R>*,                     \
                                   const double*, const double*, double*, double, const C_t<R>*);    \
   template void to_plane_layout<R>(ikr_ctx*, const double*, R*, double, const double*);

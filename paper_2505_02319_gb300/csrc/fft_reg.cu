@@ -291,4 +291,182 @@ bool launch_plane_reg(ikr_ctx* c, int nsys, const float2* b1, const float* pot, 
          try_reg<10, 12>(c, nsys, b1, pot, pot_scale, active, b4, real_in, list);
 }
 
+
+// ------------------------------------------------------------------ z-pass --
+// FP32 z-transforms of the sphere columns with one thread per column: the
+// column's run of plane waves (consecutive z from its z start, cyclic) becomes
+// a z-line in registers, transformed with compile-time twiddles, and written as
+// row iz of b1[s][iz][column] (coalesced over the block's columns); the forward
+// pass reads the rows back, transforms, and keeps the run.  The columns of a
+// block are consecutive, and so are their runs in the sphere order (both are
+// lexicographic in (j1, j2)): the block's slice [pre[c0], pre[c1]) of the
+// orbital-sized vectors moves through shared memory with coalesced copies.
+
+template <int NZ>
+__global__ void __launch_bounds__(kZC)
+    k_zi_r(const float2* __restrict__ sphere, int ld, const int* __restrict__ sys_k,
+           const int* __restrict__ colinfo, const int* __restrict__ colpre, int nc, int ncp,
+           const int* __restrict__ active, const int* __restrict__ list, int nsys, float2* __restrict__ b1) {
+  extern __shared__ float4 smem_z[];
+  float2* sv = reinterpret_cast<float2*>(smem_z);
+  const int i = blockIdx.y;
+  if (i >= nsys) return;
+  const int s = list ? list[i] : i;
+  if (active && !active[s]) return;
+  const int k = sys_k[s];
+  const int c0 = blockIdx.x * kZC, c1 = min(c0 + kZC, nc);
+  const int* pre = colpre + (size_t)k * (nc + 1);
+  const int base = pre[c0], span = pre[c1] - base;
+  const float2* src = sphere + (size_t)s * ld + base;
+  for (int e = threadIdx.x; e < span; e += kZC) cp_async8(sv + e, src + e);
+  cp_async_wait_all();
+  __syncthreads();
+  const int col = c0 + threadIdx.x;
+  if (col >= nc) return;
+  const int* inf = colinfo + ((size_t)k * nc + col) * 3;
+  const int rel = inf[0] - base, cnt = inf[1], zs = inf[2];
+  const float2 zero = make_float2(0.f, 0.f);
+  float2 v[NZ];
+#pragma unroll
+  for (int z = 0; z < NZ; ++z) {
+    int t = z - zs;
+    t += t < 0 ? NZ : 0;
+    v[z] = t < cnt ? sv[rel + t] : zero;
+  }
+  CtFft<float2, NZ, true>::run(v);
+  float2* dst = b1 + (size_t)s * NZ * ncp + col;
+#pragma unroll
+  for (int iz = 0; iz < NZ; ++iz) dst[(size_t)iz * ncp] = v[iz];
+}
+
+// out = F_z(b4) on the sphere; with psi: out += (|k+G|^2/2 - shift_s) psi and
+// dpart[s][block] = Re <psi, out> over the block's plane waves (one warp: a
+// fixed shuffle tree).
+template <int NZ>
+__global__ void __launch_bounds__(kZC)
+    k_zf_r(const float2* __restrict__ b4, int nc, int ncp, const int* __restrict__ sys_k,
+           const int* __restrict__ colinfo, const int* __restrict__ colpre, int zspan, float2* __restrict__ out,
+           int ld, int ldk, const float2* __restrict__ psi, const double* __restrict__ shift,
+           const float* __restrict__ kin_all, const int* __restrict__ active, const int* __restrict__ list,
+           int nsys, double* __restrict__ dpart) {
+  extern __shared__ float4 smem_z[];
+  float2* so = reinterpret_cast<float2*>(smem_z);
+  float2* sp = so + zspan;
+  float* sk = reinterpret_cast<float*>(sp + zspan);
+  const int i = blockIdx.y;
+  if (i >= nsys) return;
+  const int s = list ? list[i] : i;
+  if (active && !active[s]) return;
+  const int k = sys_k[s];
+  const int c0 = blockIdx.x * kZC, c1 = min(c0 + kZC, nc);
+  const int* pre = colpre + (size_t)k * (nc + 1);
+  const int base = pre[c0], span = pre[c1] - base;
+  const float* kin = kin_all ? kin_all + (size_t)k * ldk + base : nullptr;
+  if (psi) {
+    const float2* ps = psi + (size_t)s * ld + base;
+    for (int e = threadIdx.x; e < span; e += kZC) {
+      cp_async8(sp + e, ps + e);
+      if (kin) cp_async4(sk + e, kin + e);
+    }
+  }
+  const int col = c0 + threadIdx.x;
+  float2 v[NZ];
+  if (col < nc) {
+    const float2* srcc = b4 + (size_t)s * NZ * ncp + col;
+#pragma unroll
+    for (int iz = 0; iz < NZ; ++iz) v[iz] = srcc[(size_t)iz * ncp];
+    CtFft<float2, NZ, false>::run(v);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  double dot = 0.0;
+  if (col < nc) {
+    const int* inf = colinfo + ((size_t)k * nc + col) * 3;
+    const int rel = inf[0] - base, cnt = inf[1], zs = inf[2];
+    const float sh = shift ? (float)shift[s] : 0.f;
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) {
+      int t = z - zs;
+      t += t < 0 ? NZ : 0;
+      if (t < cnt) {
+        float2 val = v[z];
+        if (psi) {
+          const float d = (kin ? sk[rel + t] : 0.f) - sh;
+          const float2 p = sp[rel + t];
+          val.x += d * p.x;
+          val.y += d * p.y;
+          dot += (double)p.x * val.x + (double)p.y * val.y;
+        }
+        so[rel + t] = val;
+      }
+    }
+  }
+  __syncthreads();
+  float2* dst = out + (size_t)s * ld + base;
+  for (int e = threadIdx.x; e < span; e += kZC) dst[e] = so[e];
+  if (dpart) {
+    dot = warp_sum(dot);
+    if (threadIdx.x == 0) dpart[(size_t)s * gridDim.x + blockIdx.x] = dot;
+  }
+}
+
+namespace {
+
+template <int NZ>
+bool try_zi(ikr_ctx* c, int nsys, const int* d_k, const float2* sphere, int ld, const int* active, const int* list,
+            float2* b1) {
+  if (c->N[2] != NZ) return false;
+  const size_t smem = sizeof(float2) * (size_t)c->zspan;
+  if (smem > 48 * 1024) return false;
+  dim3 grid((c->nc + kZC - 1) / kZC, nsys);
+  k_zi_r<NZ><<<grid, kZC, smem, c->stream>>>(sphere, ld, d_k, c->k_colinfo.p, c->d_colpre.p, c->nc, c->ncp,
+                                              active, list, nsys, b1);
+  IKR_CUDA(cudaGetLastError());
+  return true;
+}
+
+template <int NZ>
+bool try_zf(ikr_ctx* c, int nsys, const int* d_k, const float2* b4, float2* out, int ld, const float2* psi,
+            const double* shift, const float* kin, const int* active, const int* list, double* dpart) {
+  if (c->N[2] != NZ) return false;
+  const size_t smem = (2 * sizeof(float2) + sizeof(float)) * (size_t)c->zspan;
+  if (smem > 48 * 1024) return false;
+  dim3 grid((c->nc + kZC - 1) / kZC, nsys);
+  k_zf_r<NZ><<<grid, kZC, smem, c->stream>>>(b4, c->nc, c->ncp, d_k, c->k_colinfo.p, c->d_colpre.p, c->zspan,
+                                              out, ld, c->ld, psi, shift, kin, active, list, nsys, dpart);
+  IKR_CUDA(cudaGetLastError());
+  return true;
+}
+
+}  // namespace
+
+bool z_reg_ok(ikr_ctx* c) {
+  const int nz = c->N[2];
+  return c->zreg_ok && (nz == 48 || nz == 32 || nz == 40 || nz == 24 || nz == 16 || nz == 12);
+}
+int z_reg_chunks(ikr_ctx* c) { return (c->nc + kZC - 1) / kZC; }
+
+bool launch_z_inverse_reg(ikr_ctx* c, int nsys, const int* d_k, const float2* sphere, int ld, const int* active,
+                          const int* list, float2* b1) {
+  if (!z_reg_ok(c) || nsys == 0) return false;
+  return try_zi<48>(c, nsys, d_k, sphere, ld, active, list, b1) ||
+         try_zi<32>(c, nsys, d_k, sphere, ld, active, list, b1) ||
+         try_zi<40>(c, nsys, d_k, sphere, ld, active, list, b1) ||
+         try_zi<24>(c, nsys, d_k, sphere, ld, active, list, b1) ||
+         try_zi<16>(c, nsys, d_k, sphere, ld, active, list, b1) ||
+         try_zi<12>(c, nsys, d_k, sphere, ld, active, list, b1);
+}
+
+bool launch_z_forward_reg(ikr_ctx* c, int nsys, const int* d_k, const float2* b4, float2* out, int ld,
+                          const float2* psi, const double* shift, const float* kin, const int* active,
+                          const int* list, double* dpart) {
+  if (!z_reg_ok(c) || nsys == 0) return false;
+  return try_zf<48>(c, nsys, d_k, b4, out, ld, psi, shift, kin, active, list, dpart) ||
+         try_zf<32>(c, nsys, d_k, b4, out, ld, psi, shift, kin, active, list, dpart) ||
+         try_zf<40>(c, nsys, d_k, b4, out, ld, psi, shift, kin, active, list, dpart) ||
+         try_zf<24>(c, nsys, d_k, b4, out, ld, psi, shift, kin, active, list, dpart) ||
+         try_zf<16>(c, nsys, d_k, b4, out, ld, psi, shift, kin, active, list, dpart) ||
+         try_zf<12>(c, nsys, d_k, b4, out, ld, psi, shift, kin, active, list, dpart);
+}
+
 }  // namespace ikr

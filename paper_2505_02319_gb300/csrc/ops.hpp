@@ -17,7 +17,7 @@ template <typename T> struct CgVecs {
 // fft.cu
 template <typename R>
 void launch_z_inverse(ikr_ctx* c, const SysList& L, const C_t<R>* sphere, int ld, const int* active,
-                      C_t<R>* b1);
+                      C_t<R>* b1, const int* list = nullptr, int nlist = 0);
 template <typename R>
 void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, const double* pot_scale,
                   const int* active, C_t<R>* b4, const C_t<R>* real_in = nullptr, const int* list = nullptr,
@@ -27,6 +27,15 @@ template <typename R>
 bool launch_plane_fast(ikr_ctx* c, int nsys, const typename io<R>::cx* b1, const typename io<R>::real* pot,
                        const double* pot_scale, const int* active, typename io<R>::cx* b4,
                        const typename io<R>::cx* real_in);
+constexpr int kZC = 32;        // columns per block of the one-thread-per-column z-pass
+// FP32 z-pass with one thread per column (fft_reg.cu); false: not covered
+bool z_reg_ok(ikr_ctx* c);
+int z_reg_chunks(ikr_ctx* c);
+bool launch_z_inverse_reg(ikr_ctx* c, int nsys, const int* d_k, const float2* sphere, int ld, const int* active,
+                          const int* list, float2* b1);
+bool launch_z_forward_reg(ikr_ctx* c, int nsys, const int* d_k, const float2* b4, float2* out, int ld,
+                          const float2* psi, const double* shift, const float* kin, const int* active,
+                          const int* list, double* dpart);
 // FP32 plane pass with one thread per line (fft_reg.cu); false: shape not covered
 // list: the nlist systems to process (a compacted active set), else all nsys under `active`
 bool launch_plane_reg(ikr_ctx* c, int nsys, const float2* b1, const float* pot, const double* pot_scale,
@@ -34,8 +43,9 @@ bool launch_plane_reg(ikr_ctx* c, int nsys, const float2* b1, const float* pot, 
 template <typename R>
 void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* out, int ld,
                       const C_t<R>* psi, const double* shift, bool kinetic, const int* active,
-                      double* dpart = nullptr);
-int zf_chunks(ikr_ctx* c);    // dot partials per system written by launch_z_forward
+                      double* dpart = nullptr, const int* list = nullptr, int nlist = 0);
+int zf_chunks(ikr_ctx* c);    // dot partials per system written by launch_z_forward (largest)
+int zf_chunks(ikr_ctx* c, int fp_bytes);   // ... by the launch of that precision
 // Density partial planes by the compile-time kernel (fft_plane.cu) into
 // c->ws.dens_part; *ngroups = the number of partial planes.  false: shape not covered.
 template <typename R>

@@ -237,6 +237,25 @@ void setup_system(ikr_ctx* c, const ikr_system* sys) {
     K.colinfo.assign(colinfo.begin() + (size_t)ik * c->nc * 3, colinfo.begin() + (size_t)(ik + 1) * c->nc * 3);
   }
   upload(c->k_colinfo, colinfo, st);
+  {
+    // column prefix sums for the one-thread-per-column z-pass; it relies on the
+    // runs of consecutive columns being consecutive in the sphere order
+    std::vector<int> pre((size_t)nk * (c->nc + 1), 0);
+    bool ok = true;
+    int span = 0;
+    for (int ik = 0; ik < nk; ++ik) {
+      int* pk = &pre[(size_t)ik * (c->nc + 1)];
+      for (int col = 0; col < c->nc; ++col) {
+        const int* inf = &colinfo[((size_t)ik * c->nc + col) * 3];
+        if (inf[1] > 0 && inf[0] != pk[col]) ok = false;
+        pk[col + 1] = pk[col] + inf[1];
+      }
+      for (int c0 = 0; c0 < c->nc; c0 += kZC) span = std::max(span, pk[std::min(c0 + kZC, c->nc)] - pk[c0]);
+    }
+    c->zreg_ok = ok;
+    c->zspan = std::max(span, 1);
+    upload(c->d_colpre, pre, st);
+  }
   upload(c->d_kin_all, kin, st);
   upload(c->d_kin_all32, kin32, st);
   upload(c->d_nb, nbs, st);

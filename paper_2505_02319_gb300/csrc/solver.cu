@@ -149,11 +149,12 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
     // W = (H - eps) P and <P, W>.  P is in range(Q) (z is projected below), and
     // Phi^H (H - eps) P = (Lambda - eps) Phi^H P = 0 for the eigenvectors Phi, so
     // Q W = W up to the eigenpair residual: W is not projected again.
-    launch_z_inverse<R>(c, L, v.P, c->ld, act, Bufs<R>::b1(c));
+    launch_z_inverse<R>(c, L, v.P, c->ld, act, Bufs<R>::b1(c), w.alist.p, c->active_hint);
     launch_plane<R>(c, L, Bufs<R>::b1(c), Bufs<R>::pot(c), nullptr, act, Bufs<R>::b4(c), nullptr, w.alist.p,
                     c->active_hint);
-    launch_z_forward<R>(c, L, Bufs<R>::b4(c), v.W, c->ld, v.P, sys + kSysShift * n, true, act, w.dpart.p);
-    cg_scalars(c, 1, sys, w.dpart.p, zf_chunks(c), n, maxit, act, dcount);
+    launch_z_forward<R>(c, L, Bufs<R>::b4(c), v.W, c->ld, v.P, sys + kSysShift * n, true, act, w.dpart.p,
+                        w.alist.p, c->active_hint);
+    cg_scalars(c, 1, sys, w.dpart.p, zf_chunks(c, (int)sizeof(R)), n, maxit, act, dcount);
     // x += alpha p, r -= alpha W, z = M^-1 r, ||r||^2, stopping test
     cg_xr<R>(c, L, 1, v, sys, act, w.dpart.p);
     cg_scalars(c, 2, sys, w.dpart.p, cch, n, maxit, act, dcount, w.alist.p);
