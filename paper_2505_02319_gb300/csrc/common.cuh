@@ -273,6 +273,24 @@ __device__ C* fft_lines(C* a, C* b, const FftPlan& p, int nlines, int lstride, c
   return in;
 }
 
+// Asynchronous global -> shared copies (cp.async, cached in L1): a thread issues
+// all of its copies of a staging phase back to back and waits once.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// 8 bytes, or zeros when !valid (the source is not read then)
+__device__ __forceinline__ void cp_async8_zfill(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const unsigned n = valid ? 8u : 0u;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+
 // ---- block reductions (deterministic: fixed tree, fixed order) --------------
 
 __device__ __forceinline__ double warp_sum(double v) {

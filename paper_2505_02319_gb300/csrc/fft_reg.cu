@@ -101,18 +101,6 @@ template <typename C, bool INV> struct CtFft<C, 1, INV> {
   __device__ __forceinline__ static void run(C*) {}
 };
 
-// Asynchronous global -> shared copies (cp.async, cached in L1): a thread issues
-// all of its copies of a staging phase back to back and waits once.
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
 }  // namespace
 
 template <int NX, int NY> struct RegGeom {

@@ -12,82 +12,6 @@ namespace ikr {
 // k-point and all (m, s) pairs, with the chunk of Phi and Y staged in shared
 // memory and a 2 x 2 register tile of outputs per thread; the per-chunk
 // partial sums are then added in fixed order (deterministic).
-// G chunk of the Phi^H Y kernel: 64 (FP32) or 32 (FP64) keeps the two staged
-// tiles within 48 KB of static shared memory
-template <typename R> struct KC;
-template <> struct KC<float> { static constexpr int v = 64; };
-template <> struct KC<double> { static constexpr int v = 32; };
-// G chunk and systems per thread of the Y - Phi C kernel: FP32 128 x 16,
-// FP64 32 x 4 (more, shorter CTAs: the FP64 rate of the part makes each
-// CTA long, and the last wave must stay short)
-template <typename R> struct AC;
-template <> struct AC<float> { static constexpr int g = 64, sg = 8; };
-template <> struct AC<double> { static constexpr int g = 32, sg = 4; };
-constexpr int kTile = 32;    // output tile (m and s) of the Phi^H Y kernel
-
-template <typename R>
-__global__ void __launch_bounds__(256) k_proj_partial(const C_t<R>* __restrict__ phi_all, int ld,
-                                                      const int* __restrict__ phi_off,
-                                                      const int* __restrict__ nocc_k,
-                                                      const int* __restrict__ nb_k,
-                                                      const int* __restrict__ kstart,
-                                                      const int* __restrict__ kcount,
-                                                      const C_t<R>* __restrict__ Y, int ldy,
-                                                      const int* __restrict__ active, int nsys,
-                                                      int noccmax, double2* __restrict__ part) {
-  using C = C_t<R>;
-  const int k = blockIdx.y, chunk = blockIdx.x;
-  const int ns = kcount[k];
-  if (ns == 0) return;
-  const int nocc = nocc_k[k], nb = nb_k[k];
-  constexpr int kKC = KC<R>::v;
-  const int g0 = chunk * kKC;
-  __shared__ C ph[kKC][kTile + 1];
-  __shared__ C ys[kKC][kTile + 1];
-  const C* phi = phi_all + (size_t)phi_off[k] * ld;
-  const int s0 = kstart[k];
-  const int tm = threadIdx.x & 15, ts = threadIdx.x >> 4;   // 16 x 16 threads, 2 x 2 outputs each
-  for (int mt = 0; mt < nocc; mt += kTile) {
-    for (int st = 0; st < ns; st += kTile) {
-      // a tile of converged systems is skipped (their partials are never read)
-      int any = 0;
-      if (threadIdx.x < kTile) {
-        const int sl = st + threadIdx.x;
-        any = sl < ns && (!active || active[s0 + sl]);
-      }
-      if (!__syncthreads_or(any)) continue;
-      for (int idx = threadIdx.x; idx < kKC * kTile; idx += blockDim.x) {
-        const int r = idx / kKC, g = idx - r * kKC;      // r: m (or s) within the tile, g fastest
-        const bool gin = g0 + g < nb;
-        const int m = mt + r, sl = st + r;
-        ph[g][r] = (gin && m < nocc) ? phi[(size_t)m * ld + g0 + g] : mk<C>(0, 0);
-        bool act = sl < ns;
-        if (act && active) act = active[s0 + sl] != 0;
-        ys[g][r] = (gin && act) ? Y[(size_t)(s0 + sl) * ldy + g0 + g] : mk<C>(0, 0);
-      }
-      __syncthreads();
-      R a[2][2][2] = {};
-#pragma unroll 8
-      for (int g = 0; g < kKC; ++g) {
-        const C p0 = ph[g][2 * tm], p1 = ph[g][2 * tm + 1];
-        const C y0 = ys[g][2 * ts], y1 = ys[g][2 * ts + 1];
-        // conj(p) * y
-        a[0][0][0] += p0.x * y0.x + p0.y * y0.y;  a[0][0][1] += p0.x * y0.y - p0.y * y0.x;
-        a[0][1][0] += p0.x * y1.x + p0.y * y1.y;  a[0][1][1] += p0.x * y1.y - p0.y * y1.x;
-        a[1][0][0] += p1.x * y0.x + p1.y * y0.y;  a[1][0][1] += p1.x * y0.y - p1.y * y0.x;
-        a[1][1][0] += p1.x * y1.x + p1.y * y1.y;  a[1][1][1] += p1.x * y1.y - p1.y * y1.x;
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int m = mt + 2 * tm + i, sl = st + 2 * ts + j;
-          if (m < nocc && sl < ns)
-            part[((size_t)chunk * nsys + s0 + sl) * noccmax + m] = make_double2(a[i][j][0], a[i][j][1]);
-        }
-    }
-  }
-}
 
 // coef[s][m] = sum over the chunk partials, one warp per (s, m): lanes take
 // chunks lane, lane + 32, ... and a fixed shuffle tree adds them.
@@ -242,119 +166,6 @@ __global__ void __launch_bounds__(256) k_proj_apply_w(const typename io<R>::cx* 
     if (dpart) {
       d = warp_sum(d);
       if (lane == 0) dpart[(size_t)s * nparts + chunk] = d;
-    }
-  }
-}
-
-// FP32: // out[s][G] = alpha * in[s][G] + beta * sum_m Phi_k[m][G] coef[s][m]
-// optionally dpart[s][chunk] = sum_{G in chunk} Re(conj(dv[s][G]) out[s][G]).
-// CTA: kAC plane waves of one k-point; thread (g, group) keeps the sums of
-// kSG systems in registers while m runs, coef of the k-point in shared memory.
-template <typename R>
-__global__ void __launch_bounds__(256) k_proj_apply(const C_t<R>* __restrict__ phi_all, int ld,
-                                                    const int* __restrict__ phi_off,
-                                                    const int* __restrict__ nocc_k,
-                                                    const int* __restrict__ nb_k,
-                                                    const int* __restrict__ kstart,
-                                                    const int* __restrict__ kcount,
-                                                    const double2* __restrict__ coef, int noccmax,
-                                                    const C_t<R>* in, R alpha, R beta,
-                                                    C_t<R>* out, int ldy,
-                                                    const C_t<R>* __restrict__ dv,
-                                                    double* __restrict__ dpart, int nparts,
-                                                    const int* __restrict__ active) {
-  using C = C_t<R>;
-  constexpr int kAC = AC<R>::g, kSG = AC<R>::sg, kGR = 256 / kAC;
-  const int k = blockIdx.y, chunk = blockIdx.x;
-  const int ns = kcount[k];
-  if (ns == 0) return;
-  const int nocc = nocc_k[k], nb = nb_k[k];
-  const int s0 = kstart[k];
-  const int g0 = chunk * kAC;
-  extern __shared__ unsigned char smem_raw[];
-  C* cf = reinterpret_cast<C*>(smem_raw);                 // [kGR * kSG][nocc] coefficients of a system block
-  __shared__ double red[kGR][kSG][kAC / 32];
-  const int gl = threadIdx.x % kAC, grp = threadIdx.x / kAC;   // kGR groups of kSG systems
-  const int g = g0 + gl;
-  const bool gin = g < nb;
-  const C* phi = phi_all + (size_t)phi_off[k] * ld;
-  const int lane = threadIdx.x & 31, wig = gl >> 5;
-  for (int sb = 0; sb < ns; sb += kGR * kSG) {
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < kGR * kSG * nocc; idx += blockDim.x) {
-      const int sl = idx / nocc, m = idx - sl * nocc;
-      const int s = sb + sl;
-      C v = mk<C>(0, 0);
-      if (s < ns) {
-        const double2 d = coef[(size_t)(s0 + s) * noccmax + m];
-        v = mk<C>((R)d.x, (R)d.y);
-      }
-      cf[sl * nocc + m] = v;
-    }
-    __syncthreads();
-    R ax[kSG], ay[kSG];
-#pragma unroll
-    for (int j = 0; j < kSG; ++j) ax[j] = ay[j] = R(0);
-    const C* cg = cf + grp * kSG * nocc;
-    bool glive = false;   // uniform over the group's warps: groups of converged systems skip the sums
-#pragma unroll
-    for (int j = 0; j < kSG; ++j) {
-      const int sl = sb + grp * kSG + j;
-      glive |= sl < ns && (!active || active[s0 + sl]);
-    }
-    for (int m0 = 0; glive && m0 < nocc; m0 += 16) {
-      // the next 16 orbitals at this G are loaded together before use
-      C p[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) p[i] = (gin && m0 + i < nocc) ? phi[(size_t)(m0 + i) * ld + g] : mk<C>(0, 0);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        if (m0 + i < nocc) {
-#pragma unroll
-          for (int j = 0; j < kSG; ++j) {
-            const C c = cg[j * nocc + m0 + i];
-            ax[j] += p[i].x * c.x - p[i].y * c.y;
-            ay[j] += p[i].x * c.y + p[i].y * c.x;
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < kSG; ++j) {
-      const int sl = sb + grp * kSG + j;
-      const int s = s0 + sl;
-      const bool live = sl < ns && (!active || active[s]);
-      double d = 0.0;
-      if (live && gin) {
-        const size_t o = (size_t)s * ldy + g;
-        C v = mk<C>(beta * ax[j], beta * ay[j]);
-        if (alpha != R(0)) {
-          const C x = in[o];
-          v.x += alpha * x.x;
-          v.y += alpha * x.y;
-        }
-        out[o] = v;
-        if (dv) {
-          const C w = dv[o];
-          d = (double)w.x * v.x + (double)w.y * v.y;
-        }
-      }
-      if (dpart) {
-        d = warp_sum(d);
-        if (lane == 0) red[grp][j][wig] = d;
-      }
-    }
-    if (dpart) {
-      __syncthreads();
-      if (threadIdx.x < kGR * kSG) {
-        const int gg = threadIdx.x / kSG, j = threadIdx.x % kSG;
-        const int sl = sb + gg * kSG + j;
-        if (sl < ns && (!active || active[s0 + sl])) {
-          double t = 0.0;
-          for (int w = 0; w < kAC / 32; ++w) t += red[gg][j][w];
-          dpart[(size_t)(s0 + sl) * nparts + chunk] = t;
-        }
-      }
     }
   }
 }
@@ -770,7 +581,7 @@ static void set_smem_attr(const void* f, size_t bytes) {
 }
 
 int proj_chunks(ikr_ctx* c, int fp_bytes) {
-  const int g = fp_bytes == 4 ? AC<float>::g : kPC;
+  const int g = fp_bytes == 4 ? proj_chunks32() : kPC;
   return (c->ld + g - 1) / g;
 }
 int proj_chunks(ikr_ctx* c) { return std::max(proj_chunks(c, 4), proj_chunks(c, 8)); }
@@ -805,20 +616,7 @@ void proj_coef(ikr_ctx* c, const SysList& L, const C_t<R>* Y, int ldy, const int
     IKR_CUDA(cudaGetLastError());
     return;
   }
-  const int kc = KC<R>::v;
-  const int nch = (c->ld + kc - 1) / kc;
-  const int nm = c->noccmax;
-  c->ws.cpart.reserve((size_t)nch * L.n * nm * 2);
-  double2* part = reinterpret_cast<double2*>(c->ws.cpart.p);
-  dim3 grid(nch, (unsigned)c->k.size());
-  k_proj_partial<R><<<grid, 256, 0, c->stream>>>(phi_ptr<R>(c), c->ld, c->d_phi_off.p, c->d_nocc.p,
-                                                  c->d_nb.p, L.d_kstart.p, L.d_kcount.p, Y, ldy,
-                                                  active, L.n, nm, part);
-  IKR_CUDA(cudaGetLastError());
-  const long long threads = 32LL * L.n * nm;
-  k_proj_reduce<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(part, nch, kc, L.n, nm, L.d_k.p,
-                                                                          c->d_nocc.p, c->d_nb.p, active, coef);
-  IKR_CUDA(cudaGetLastError());
+  if constexpr (sizeof(R) == 4) proj_coef32(c, L, Y, ldy, active, coef);
 }
 
 template <typename R>
@@ -848,15 +646,7 @@ void proj_apply(ikr_ctx* c, const SysList& L, const double2* coef, const C_t<R>*
     IKR_CUDA(cudaGetLastError());
     return;
   }
-  const int nch = proj_chunks(c, (int)sizeof(R));
-  const size_t smem = sizeof(C_t<R>) * (256 / AC<R>::g * AC<R>::sg * std::max(c->noccmax, 1));
-  set_smem_attr((const void*)k_proj_apply<R>, smem);
-  dim3 grid(nch, (unsigned)c->k.size());
-  k_proj_apply<R><<<grid, 256, smem, c->stream>>>(phi_ptr<R>(c), c->ld, c->d_phi_off.p, c->d_nocc.p,
-                                                   c->d_nb.p, L.d_kstart.p, L.d_kcount.p, coef,
-                                                   c->noccmax, in, alpha, beta, out, ldy, dv, dpart,
-                                                   nch, active);
-  IKR_CUDA(cudaGetLastError());
+  if constexpr (sizeof(R) == 4) proj_apply32(c, L, coef, in, alpha, beta, out, ldy, dv, dpart, active);
 }
 
 void sys_reduce(ikr_ctx* c, const double* part, int nparts, int nsys, const int* active, double* out) {

@@ -66,6 +66,11 @@ template <> inline const double* kin_all_ptr<double>(ikr_ctx* c) { return c->d_k
 template <> inline const float* kin_all_ptr<float>(ikr_ctx* c) { return c->d_kin_all32.p; }
 
 // ops.cu
+// FP32 projections (proj32.cu)
+int proj_chunks32();
+void proj_coef32(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef);
+void proj_apply32(ikr_ctx* c, const SysList& L, const double2* coef, const float2* in, float alpha, float beta,
+                  float2* out, int ldy, const float2* dv, double* dpart, const int* active);
 int proj_chunks(ikr_ctx* c);                  // the largest count (workspace sizing)
 int proj_chunks(ikr_ctx* c, int fp_bytes);    // dot partials per system written by proj_apply
 int cg_chunks(ikr_ctx* c);
