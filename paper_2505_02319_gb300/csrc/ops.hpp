@@ -66,6 +66,10 @@ template <> inline const double* kin_all_ptr<double>(ikr_ctx* c) { return c->d_k
 template <> inline const float* kin_all_ptr<float>(ikr_ctx* c) { return c->d_kin_all32.p; }
 
 // ops.cu
+// Fused FP32 CG update after the H_k application (cg_fused.cu): false when the
+// shape does not fit a thread-block cluster per k-point (then nothing is launched)
+bool launch_cg_fused(ikr_ctx* c, const SysList& L, float2* X, float2* Rv, float2* P, const float2* W, double* sys,
+                     int maxit, int* active, int* counter, int* list, const double* zpart, int nzf);
 // FP32 projections (proj32.cu)
 int proj_chunks32();
 void proj_coef32(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef);

@@ -154,15 +154,25 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
                     c->active_hint);
     launch_z_forward<R>(c, L, Bufs<R>::b4(c), v.W, c->ld, v.P, sys + kSysShift * n, true, act, w.dpart.p,
                         w.alist.p, c->active_hint);
-    cg_scalars(c, 1, sys, w.dpart.p, zf_chunks(c, (int)sizeof(R)), n, maxit, act, dcount);
-    // x += alpha p, r -= alpha W, z = M^-1 r, ||r||^2, stopping test
-    cg_xr<R>(c, L, 1, v, sys, act, w.dpart.p);
-    cg_scalars(c, 2, sys, w.dpart.p, cch, n, maxit, act, dcount, w.alist.p);
-    // z = Q z, beta, p = z + beta p
-    proj_coef<R>(c, L, v.Z, c->ld, act, coef);
-    proj_apply<R>(c, L, coef, v.Z, R(1), R(-1), v.Z, c->ld, v.R, w.dpart.p, act);
-    cg_scalars(c, 3, sys, w.dpart.p, pch, n, maxit, act, nullptr);
-    cg_p<R>(c, L, 1, v, sys, act);
+    bool fused = false;
+    if constexpr (sizeof(R) == 4) {
+      // alpha, x, r, stopping test, z = Q M^-1 r, beta and p in one launch
+      ProfScope ps(c, kKidCgVec, 1);
+      IKR_CUDA(cudaMemsetAsync(dcount, 0, sizeof(int), strm));
+      fused = launch_cg_fused(c, L, v.X, v.R, v.P, v.W, sys, maxit, act, dcount, w.alist.p, w.dpart.p,
+                              zf_chunks(c, 4));
+    }
+    if (!fused) {
+      cg_scalars(c, 1, sys, w.dpart.p, zf_chunks(c, (int)sizeof(R)), n, maxit, act, dcount);
+      // x += alpha p, r -= alpha W, z = M^-1 r, ||r||^2, stopping test
+      cg_xr<R>(c, L, 1, v, sys, act, w.dpart.p);
+      cg_scalars(c, 2, sys, w.dpart.p, cch, n, maxit, act, dcount, w.alist.p);
+      // z = Q z, beta, p = z + beta p
+      proj_coef<R>(c, L, v.Z, c->ld, act, coef);
+      proj_apply<R>(c, L, coef, v.Z, R(1), R(-1), v.Z, c->ld, v.R, w.dpart.p, act);
+      cg_scalars(c, 3, sys, w.dpart.p, pch, n, maxit, act, nullptr);
+      cg_p<R>(c, L, 1, v, sys, act);
+    }
     IKR_CUDA(cudaMemcpyAsync(c->h_pinned, dcount, sizeof(int), cudaMemcpyDeviceToHost, strm));
     IKR_CUDA(cudaStreamSynchronize(strm));
     c->active_hint = c->h_pinned[0];
