@@ -34,6 +34,11 @@
  *  - Errors: every call returns an ikr_status; no exception crosses the ABI.
  *    ikr_last_error() gives a per-context message for the last failure.
  *    A failed call leaves the context usable unless it returns IKR_ERR_CUDA.
+ *  - Environment: IKR_CG_FUSED=0 (read when a context first runs an FP32 CG
+ *    for a given number of systems per k-point) replaces the fused CG update
+ *    (one thread-block cluster per k-point, one launch per iteration) by the
+ *    equivalent sequence of separate kernels; results agree to FP32 rounding.
+ *    The sequence is also what runs when the fused update does not fit.
  */
 #ifndef IKR_H
 #define IKR_H

@@ -17,6 +17,8 @@
 // and the compacted list of the systems that continue.
 #include <cooperative_groups.h>
 
+#include <cstdlib>
+
 #include "ops.hpp"
 
 namespace cg = cooperative_groups;
@@ -361,6 +363,9 @@ FusedPlan plan_fused(ikr_ctx* c, const SysList& L) {
   c->cgf_nsmax = p.nsmax;
   c->cgf_ok = false;
   if (p.nsmax == 0 || p.nsmax > 64 || c->noccmax > 64) return p;
+  // IKR_CG_FUSED=0 selects the unfused sequence of kernels (read when a context plans)
+  if (const char* e = std::getenv("IKR_CG_FUSED"))
+    if (e[0] == '0') return p;
   int max_optin = 0, dev = 0;
   IKR_CUDA(cudaGetDevice(&dev));
   IKR_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
