@@ -157,6 +157,29 @@ ikr_status ikr_setup_groundstate(const ikr_system* sys, const ikr_eigenpairs* ei
 /* Sets or replaces the ground state of an existing context (see above). */
 ikr_status ikr_set_eigenpairs(ikr_ctx* ctx, const ikr_eigenpairs* eig, cudaStream_t stream);
 
+/* Computes the lowest nbands eigenpairs of every H_k on the GPU and sets them
+ * as by ikr_set_eigenpairs.  The ground state is the input of the method
+ * (eq. discretised_KS); the paper obtains it from an SCF, which this library
+ * does not run.  No counterpart in the paper's algorithms: setup only.
+ * Method: Chebyshev-filtered subspace iteration with the library's own H_k
+ * applications (no dense H_k), SVQB orthonormalisation and Rayleigh-Ritz; a
+ * block of nbands + max(4, nbands/4) vectors, filter polynomial of the given
+ * degree (>= 2), stopping when every wanted band has ||H x - theta x|| <= tol
+ * (Ha, absolute) or after maxit cycles.
+ * Outputs (optional, host): the eigenvalues (nkpt x nbands, ascending per k),
+ * and per k-point the cycles and the final largest residual (nkpt entries).
+ * Returns IKR_ERR_NOCONV (eigenpairs still set) when a k-point stopped at
+ * maxit above tol; IKR_ERR_NOGAP / IKR_ERR_ARG as ikr_set_eigenpairs. */
+ikr_status ikr_compute_eigenpairs(ikr_ctx* ctx, int nbands, double tol, int maxit, int degree, double* eigenvalues,
+                                  int* iters, double* max_residual, cudaStream_t stream);
+
+/* Host utility (no GPU): eigenvalues w (ascending, n) and eigenvectors v
+ * (column j = eigenvector of w[j]; row-major n x n complex, interleaved) of the
+ * Hermitian matrix a (row-major n x n complex, interleaved), by the cyclic
+ * Jacobi rotations the eigensolver uses for its Rayleigh-Ritz steps.
+ * IKR_ERR_ARG for n < 1 or NULL pointers. */
+ikr_status ikr_hermitian_eigh(int n, const double* a, double* w, double* v);
+
 /* Basis queries: number of k-points, Nb_k, and the Miller triples of G_k
  * (host output, Nb_k x 3 ints). */
 int ikr_num_kpoints(const ikr_ctx* ctx);

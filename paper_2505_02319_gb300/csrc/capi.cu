@@ -132,6 +132,55 @@ ikr_status ikr_set_eigenpairs(ikr_ctx* c, const ikr_eigenpairs* eig, cudaStream_
   return guarded(c, [&] { set_eigenpairs(c, eig); });
 }
 
+ikr_status ikr_compute_eigenpairs(ikr_ctx* c, int nbands, double tol, int maxit, int degree, double* eigenvalues,
+                                  int* iters, double* max_residual, cudaStream_t stream) {
+  if (!c) return IKR_ERR_ARG;
+  c->stream = stream;
+  bool conv = true;
+  ikr_status s = guarded(c, [&] {
+    std::vector<DBuf<double2>> vecs;
+    std::vector<double> eps;
+    const std::vector<EigenStats> st = compute_eigenpairs(c, nbands, tol, maxit, degree, vecs, eps);
+    std::vector<const double*> ptrs(vecs.size());
+    for (size_t k = 0; k < vecs.size(); ++k) {
+      ptrs[k] = reinterpret_cast<const double*>(vecs[k].p);
+      if (iters) iters[k] = st[k].iters;
+      if (max_residual) max_residual[k] = st[k].max_residual;
+      conv = conv && st[k].max_residual <= tol;
+    }
+    if (eigenvalues) std::copy(eps.begin(), eps.end(), eigenvalues);
+    ikr_eigenpairs e;
+    e.nbands = nbands;
+    e.eigenvalues = eps.data();
+    e.eigenvectors = ptrs.data();
+    set_eigenpairs(c, &e);
+    IKR_CUDA(cudaStreamSynchronize(stream));
+  });
+  if (s == IKR_OK && !conv) {
+    c->err = "eigensolver stopped at maxit above tol";
+    return IKR_ERR_NOCONV;
+  }
+  return s;
+}
+
+ikr_status ikr_hermitian_eigh(int n, const double* a, double* w, double* v) {
+  if (n < 1 || !a || !w || !v) return IKR_ERR_ARG;
+  try {
+    std::vector<std::complex<double>> A((size_t)n * n), V;
+    for (size_t i = 0; i < (size_t)n * n; ++i) A[i] = {a[2 * i], a[2 * i + 1]};
+    std::vector<double> ww;
+    herm_jacobi(n, A, ww, V);
+    for (int i = 0; i < n; ++i) w[i] = ww[i];
+    for (size_t i = 0; i < (size_t)n * n; ++i) {
+      v[2 * i] = V[i].real();
+      v[2 * i + 1] = V[i].imag();
+    }
+  } catch (...) {
+    return IKR_ERR_ARG;
+  }
+  return IKR_OK;
+}
+
 int ikr_num_kpoints(const ikr_ctx* c) { return c ? (int)c->k.size() : 0; }
 
 ikr_status ikr_basis_size(const ikr_ctx* c, int k, int* nb) {

@@ -40,6 +40,20 @@ template <typename T> struct DBuf {
   DBuf() = default;
   DBuf(const DBuf&) = delete;
   DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) {
+    o.p = nullptr;
+    o.n = 0;
+  }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p;
+      n = o.n;
+      o.p = nullptr;
+      o.n = 0;
+    }
+    return *this;
+  }
   ~DBuf() { release(); }
   void release() {
     if (p) cudaFree(p);
@@ -148,6 +162,7 @@ struct ikr_ctx {
   std::string err;
   int N[3] = {0, 0, 0};
   int nsm = 152;                // streaming multiprocessors of the device
+  double vmax = 0.0;            // largest value of the local potential V(r)
   size_t Ng = 0;
   double lattice[9];            // columns are cell vectors
   double recip[9];              // columns are b_i

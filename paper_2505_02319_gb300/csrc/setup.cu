@@ -263,6 +263,7 @@ void setup_system(ikr_ctx* c, const ikr_system* sys) {
   // potential: C order, and plane layout [i3][i2][i1] divided by Ng
   const int N1 = c->N[0], N2 = c->N[1], N3 = c->N[2];
   std::vector<double> V(sys->V, sys->V + c->Ng);
+  c->vmax = *std::max_element(V.begin(), V.end());
   std::vector<double> Vt(c->Ng);
   std::vector<float> Vt32(c->Ng);
   for (int i1 = 0; i1 < N1; ++i1)

@@ -1,12 +1,23 @@
 // Internal interfaces of the solver layer (solver.cu, mixed.cu).
 #pragma once
 
+#include <complex>
 #include <functional>
 #include <vector>
 
 #include "ops.hpp"
 
 namespace ikr {
+
+// ground-state eigensolver (eigen.cu)
+struct EigenStats {
+  int iters = 0;              // filter + Rayleigh-Ritz cycles
+  double max_residual = 0.0;  // largest ||H x - theta x|| of the wanted bands
+};
+std::vector<EigenStats> compute_eigenpairs(ikr_ctx* c, int nbands, double tol, int maxit, int degree,
+                                           std::vector<DBuf<double2>>& vecs, std::vector<double>& eps);
+void herm_jacobi(int n, std::vector<std::complex<double>>& A, std::vector<double>& w,
+                 std::vector<std::complex<double>>& V);
 
 struct CgStats {
   std::vector<int> iters, status;   // status: 1 converged, 2 numeric, 3 iteration cap

@@ -2,9 +2,11 @@
 
 The response method takes the ground state (eq. discretised_KS) as its input;
 the paper obtains it from an SCF, which is out of scope here.  For the fixed
-synthetic potentials this helper assembles every H_k column by column from
-the library's H_k applications (ikr_apply_hamiltonian) and diagonalises it
-densely on the GPU (torch.linalg.eigh).  This is setup, outside the solver.
+synthetic potentials the ground state comes either from the library's GPU
+eigensolver (ikr_compute_eigenpairs: Chebyshev-filtered subspace iteration on
+its own H_k applications, any basis size) or, for small bases, from every
+H_k assembled column by column from ikr_apply_hamiltonian and diagonalised
+densely (torch.linalg.eigh).  This is setup, outside the solver.
 """
 from __future__ import annotations
 
@@ -35,14 +37,21 @@ def dense_eigenpairs(ctx: ikr.Context, nbands: int, batch: int = 512):
     return np.array(evals), evecs
 
 
-def context_for(system, nbands=None) -> ikr.Context:
-    """Context with ground state for a workloads.System."""
+def context_for(system, nbands=None, eigensolver="dense", eig_tol=1e-10) -> ikr.Context:
+    """Context with ground state for a workloads.System.  ``eigensolver``:
+    "dense" (H_k assembled and diagonalised, small bases) or "chfsi" (the
+    library's GPU Chebyshev-filtered subspace iteration, any basis size)."""
     ctx = ikr.Context.setup_groundstate(system.lattice, system.dims, system.Ecut, system.kpoints,
                                         system.kweights, system.V, system.temperature,
                                         system.n_electrons)
     nb = nbands or system.nbands
-    ev, vecs = dense_eigenpairs(ctx, nb)
-    ctx.set_eigenpairs(ev, vecs)
+    if eigensolver == "chfsi":
+        ctx.compute_eigenpairs(nb, tol=eig_tol)
+    elif eigensolver == "dense":
+        ev, vecs = dense_eigenpairs(ctx, nb)
+        ctx.set_eigenpairs(ev, vecs)
+    else:
+        raise ValueError(f"unknown eigensolver {eigensolver!r}")
     ctx.nbands = nb
     ctx.ngrid = int(np.prod(system.dims))
     ctx.groundstate_nsys = int(ctx.groundstate_info(nb, ctx.ngrid)["nocc"].sum())

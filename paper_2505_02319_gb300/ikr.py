@@ -80,6 +80,8 @@ def _load():
         "ikr_default_opts": (None, [ct.POINTER(SolveOpts)]),
         "ikr_setup_groundstate": (I, [ct.POINTER(System), ct.POINTER(Eigenpairs), S, ct.POINTER(P)]),
         "ikr_set_eigenpairs": (I, [P, ct.POINTER(Eigenpairs), S]),
+        "ikr_compute_eigenpairs": (I, [P, I, D, I, I, ct.POINTER(D), ct.POINTER(I), ct.POINTER(D), S]),
+        "ikr_hermitian_eigh": (I, [I, ct.POINTER(D), ct.POINTER(D), ct.POINTER(D)]),
         "ikr_num_kpoints": (I, [P]),
         "ikr_basis_size": (I, [P, I, ct.POINTER(I)]),
         "ikr_basis_millers": (I, [P, I, ct.POINTER(I)]),
@@ -187,6 +189,21 @@ class Context:
     def set_eigenpairs(self, eigenvalues, eigenvectors):
         eig, keep = _eigenpairs(eigenvalues, eigenvectors)
         self._check(_LIB.ikr_set_eigenpairs(self._h, ct.byref(eig), _stream()))
+
+    def compute_eigenpairs(self, nbands, tol=1e-10, maxit=200, degree=12):
+        """Lowest ``nbands`` eigenpairs of every H_k on the GPU (Chebyshev-filtered
+        subspace iteration on the library's H_k), set as the ground state.
+        Returns (eigenvalues (nk, nbands), cycles per k-point, largest residual
+        per k-point)."""
+        nk = self.nkpt
+        ev = np.zeros((nk, int(nbands)))
+        iters = (ct.c_int * nk)()
+        res = (ct.c_double * nk)()
+        st = _LIB.ikr_compute_eigenpairs(self._h, int(nbands), float(tol), int(maxit), int(degree),
+                                         ev.ctypes.data_as(ct.POINTER(ct.c_double)), iters, res, _stream())
+        self._check(st)
+        self.eigenvalues, self.eig_iters, self.eig_residuals = ev, list(iters), list(res)
+        return ev, list(iters), list(res)
 
     def _check(self, st, allow=()):
         if st != IKR_OK and st not in allow:
@@ -383,3 +400,18 @@ def apply_dielectric_adjoint(ctx, v, tol=None, precision=FP64):
 
 def solve_response_adjoint(ctx, g, **kw):
     return ctx.solve_response_adjoint(g, **kw)
+
+
+def hermitian_eigh(a):
+    """Eigenvalues (ascending) and eigenvectors (columns) of a Hermitian matrix
+    by the library's host Jacobi solver (the Rayleigh-Ritz step of the GPU
+    eigensolver); no GPU needed."""
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    n = a.shape[0]
+    w = np.empty(n)
+    v = np.empty((n, n), dtype=np.complex128)
+    st = _LIB.ikr_hermitian_eigh(n, a.ctypes.data_as(ct.POINTER(ct.c_double)), w.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                 v.ctypes.data_as(ct.POINTER(ct.c_double)))
+    if st != IKR_OK:
+        raise IkrError(st, "ikr_hermitian_eigh failed")
+    return w, v
