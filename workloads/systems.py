@@ -199,10 +199,13 @@ _SPECS = {
     "cfg2": dict(seed=2, cell=(10.26, 10.26, 10.26), dims=(48, 48, 48), Ecut=15.0,
                  layout="diamond", jitter=0.02, depth=4.0, width=0.8,
                  n_electrons=32, nbands=36, T=0.01, kgrid=(2, 2, 2)),
-    # Metallic slab: 10x10x60, 12 Gaussians in 3 layers, 4x4x1 k, 40 bands, FD T=0.01.
+    # Metallic slab: 10x10x60, 12 Gaussians in 3 layers, 4x4x1 k, FD T=0.01.  With
+    # the occupation threshold 1e-10, bands up to T ln(2e10) ~ 0.24 Ha above the
+    # Fermi level count as occupied: N_occ,k = 60-72 here, so 80 bands (the
+    # solver needs one band with f below the threshold at every k).
     "cfg3": dict(seed=3, cell=(10.0, 10.0, 60.0), dims=(40, 40, 216), Ecut=20.0,
                  layout="slab", layers=(25.0, 30.0, 35.0), jitter=0.02, depth=3.0,
-                 width=1.0, n_electrons=48, nbands=40, T=0.01, kgrid=(4, 4, 1)),
+                 width=1.0, n_electrons=48, nbands=80, T=0.01, kgrid=(4, 4, 1)),
     # Large Gamma-point cell: 20.5 bohr, 64 Gaussians, 128 bands, 96^3 grid.
     "cfg4": dict(seed=4, cell=(20.5, 20.5, 20.5), dims=(96, 96, 96), Ecut=20.0,
                  layout="cubic_lattice", per_side=4, jitter=0.05, depth=3.0,
