@@ -35,13 +35,16 @@ inline int lines_per_cta(int n) { return n <= 64 ? 16 : (n <= 128 ? 8 : 4); }
 
 // ------------------------------------------------------------------ z-pass --
 
+// R is the arithmetic type; global arrays hold its storage type io<R>
+// (double2 for the double-float passes of the mixed path), converted on load
+// and store.
 template <typename R>
-__global__ void __launch_bounds__(256) k_z_inverse(const C_t<R>* __restrict__ sphere, int ld,
+__global__ void __launch_bounds__(256) k_z_inverse(const typename io<R>::cx* __restrict__ sphere, int ld,
                                                    const int* __restrict__ sys_k,
                                                    const int* __restrict__ colinfo, int nc, int ncp,
-                                                   FftPlan pz, const C_t<R>* __restrict__ twz,
+                                                   FftPlan pz, const typename io<R>::cx* __restrict__ twz,
                                                    const int* __restrict__ active, int LZ,
-                                                   C_t<R>* __restrict__ b1) {
+                                                   typename io<R>::cx* __restrict__ b1) {
   using C = C_t<R>;
   const int s = blockIdx.y;
   if (active && !active[s]) return;
@@ -52,39 +55,39 @@ __global__ void __launch_bounds__(256) k_z_inverse(const C_t<R>* __restrict__ sp
   C* B = A + LZ * lds;
   const int k = sys_k[s];
   const int c0 = blockIdx.x * LZ;
-  for (int i = threadIdx.x; i < Nz; i += blockDim.x) tw[i] = twz[i];
-  const C* src = sphere + (size_t)s * ld;
+  for (int i = threadIdx.x; i < Nz; i += blockDim.x) tw[i] = to_c<C>(twz[i]);
+  const typename io<R>::cx* src = sphere + (size_t)s * ld;
   for (int idx = threadIdx.x; idx < LZ * Nz; idx += blockDim.x) {
     const int l = idx / Nz, z = idx - l * Nz;
     const int col = c0 + l;
-    C v = mk<C>(0, 0);
+    C v = mk<C>(R(0), R(0));
     if (col < nc) {
       const int* inf = colinfo + ((size_t)k * nc + col) * 3;
       int t = z - inf[2];
       if (t < 0) t += Nz;
-      if (t < inf[1]) v = src[inf[0] + t];
+      if (t < inf[1]) v = to_c<C>(src[inf[0] + t]);
     }
     A[l * lds + z] = v;
   }
   __syncthreads();
   C* res = fft_lines<C, true>(A, B, pz, LZ, lds, nullptr, 1, tw);
-  C* dst = b1 + (size_t)s * Nz * ncp;
+  typename io<R>::cx* dst = b1 + (size_t)s * Nz * ncp;
   for (int idx = threadIdx.x; idx < LZ * Nz; idx += blockDim.x) {
     const int iz = idx / LZ, l = idx - iz * LZ;
     const int col = c0 + l;
-    if (col < nc) dst[(size_t)iz * ncp + col] = res[l * lds + iz];
+    if (col < nc) dst[(size_t)iz * ncp + col] = from_c(res[l * lds + iz]);
   }
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_z_forward(const C_t<R>* __restrict__ b4, int nc, int ncp,
+__global__ void __launch_bounds__(256) k_z_forward(const typename io<R>::cx* __restrict__ b4, int nc, int ncp,
                                                    const int* __restrict__ sys_k,
                                                    const int* __restrict__ colinfo, FftPlan pz,
-                                                   const C_t<R>* __restrict__ twz, int LZ,
-                                                   C_t<R>* __restrict__ out, int ld, int ldk,
-                                                   const C_t<R>* __restrict__ psi,
+                                                   const typename io<R>::cx* __restrict__ twz, int LZ,
+                                                   typename io<R>::cx* __restrict__ out, int ld, int ldk,
+                                                   const typename io<R>::cx* __restrict__ psi,
                                                    const double* __restrict__ shift,
-                                                   const R* __restrict__ kin_all,
+                                                   const typename io<R>::real* __restrict__ kin_all,
                                                    const int* __restrict__ active,
                                                    double* __restrict__ dpart) {
   using C = C_t<R>;
@@ -98,19 +101,19 @@ __global__ void __launch_bounds__(256) k_z_forward(const C_t<R>* __restrict__ b4
   C* B = A + LZ * lds;
   const int k = sys_k[s];
   const int c0 = blockIdx.x * LZ;
-  for (int i = threadIdx.x; i < Nz; i += blockDim.x) tw[i] = twz[i];
-  const C* src = b4 + (size_t)s * Nz * ncp;
+  for (int i = threadIdx.x; i < Nz; i += blockDim.x) tw[i] = to_c<C>(twz[i]);
+  const typename io<R>::cx* src = b4 + (size_t)s * Nz * ncp;
   for (int idx = threadIdx.x; idx < LZ * Nz; idx += blockDim.x) {
     const int iz = idx / LZ, l = idx - iz * LZ;
     const int col = c0 + l;
-    A[l * lds + iz] = (col < nc) ? src[(size_t)iz * ncp + col] : mk<C>(0, 0);
+    A[l * lds + iz] = (col < nc) ? to_c<C>(src[(size_t)iz * ncp + col]) : mk<C>(R(0), R(0));
   }
   __syncthreads();
   C* res = fft_lines<C, false>(A, B, pz, LZ, lds, nullptr, 1, tw);
-  C* dst = out + (size_t)s * ld;
-  const C* ps = psi ? psi + (size_t)s * ld : nullptr;
-  const R sh = shift ? (R)shift[s] : R(0);
-  const R* kin = kin_all ? kin_all + (size_t)k * ldk : nullptr;
+  typename io<R>::cx* dst = out + (size_t)s * ld;
+  const typename io<R>::cx* ps = psi ? psi + (size_t)s * ld : nullptr;
+  const R sh = shift ? to_r<R>(shift[s]) : R(0);
+  const typename io<R>::real* kin = kin_all ? kin_all + (size_t)k * ldk : nullptr;
   double dot = 0.0;
   for (int idx = threadIdx.x; idx < LZ * Nz; idx += blockDim.x) {
     const int l = idx / Nz, z = idx - l * Nz;
@@ -123,13 +126,13 @@ __global__ void __launch_bounds__(256) k_z_forward(const C_t<R>* __restrict__ b4
     const int i = inf[0] + t;
     C v = res[l * lds + z];
     if (ps) {
-      const R d = (kin ? kin[i] : R(0)) - sh;
-      const C p = ps[i];
+      const R d = (kin ? to_r<R>(kin[i]) : R(0)) - sh;
+      const C p = to_c<C>(ps[i]);
       v.x += d * p.x;
       v.y += d * p.y;
-      dot += (double)p.x * v.x + (double)p.y * v.y;
+      dot += to_d(p.x) * to_d(v.x) + to_d(p.y) * to_d(v.y);
     }
-    dst[i] = v;
+    dst[i] = from_c(v);
   }
   if (dpart) {
     // Re <psi, out> over this CTA's plane waves (fixed-order block reduction)
@@ -454,8 +457,18 @@ void launch_z_inverse(ikr_ctx* c, const SysList& L, const C_t<R>* sphere, int ld
   const int Nz = c->N[2];
   const int LZ = lines_per_cta(Nz);
   const size_t smem = sizeof(C_t<R>) * (Nz + 2 * LZ * (Nz + 1));
-  set_smem(k_z_inverse<R>, smem);
   dim3 grid((c->nc + LZ - 1) / LZ, L.n);
+  if (sizeof(R) == 8 && c->emulate_fp64) {
+    // FP64-accurate pass of the mixed path on the FP32 pipe (double-float:
+    // 3.7 -> 3.0 ms per cfg2 solve against the FP64 pipe)
+    set_smem(k_z_inverse<dfloat>, smem);
+    k_z_inverse<dfloat><<<grid, 256, smem, c->stream>>>(
+        reinterpret_cast<const double2*>(sphere), ld, L.d_k.p, c->k_colinfo.p, c->nc, c->ncp, c->plan[2],
+        c->d_tw[2].p, active, LZ, reinterpret_cast<double2*>(b1));
+    IKR_CUDA(cudaGetLastError());
+    return;
+  }
+  set_smem(k_z_inverse<R>, smem);
   k_z_inverse<R><<<grid, 256, smem, c->stream>>>(sphere, ld, L.d_k.p, c->k_colinfo.p, c->nc, c->ncp,
                                                   c->plan[2], tw_ptr<R>(c, 2), active, LZ, b1);
   IKR_CUDA(cudaGetLastError());
@@ -509,8 +522,10 @@ void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* ou
   const int Nz = c->N[2];
   const int LZ = lines_per_cta(Nz);
   const size_t smem = sizeof(C_t<R>) * (Nz + 2 * LZ * (Nz + 1));
-  set_smem(k_z_forward<R>, smem);
   dim3 grid((c->nc + LZ - 1) / LZ, L.n);
+  // (the FP64-accurate forward pass stays on the FP64 pipe: in double-float its
+  // conversions and the normalised kinetic term cost more than they save)
+  set_smem(k_z_forward<R>, smem);
   const R* kin = kinetic ? kin_all_ptr<R>(c) : nullptr;
   k_z_forward<R><<<grid, 256, smem, c->stream>>>(b4, c->nc, c->ncp, L.d_k.p, c->k_colinfo.p,
                                                   c->plan[2], tw_ptr<R>(c, 2), LZ, out, ld, c->ld,
