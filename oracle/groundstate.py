@@ -7,6 +7,9 @@ k-form of Sec. 4.1.1)
 
     H_k = diag(|k+G|^2 / 2) + Z^T W diag(V) W^{-1} Z      on the sphere G_k,
 
+(plus the nonlocal B diag(D) B^H of oracle/kb.py for systems with
+Kleinman-Bylander projectors),
+
 obtained by dense diagonalisation.  Because W is the unitary DFT, the local
 part has the plain closed form (W diag(V) W^{-1})_{G,G'} = Vhat(G - G') / Ng
 with Vhat(q) = sum_r V(r) e^{-i q.r}, the difference G - G' taken modulo the
@@ -23,7 +26,7 @@ import dataclasses
 import numpy as np
 from scipy.special import expit
 
-from . import basis, dft
+from . import basis, dft, kb as kbproj
 
 EPS_OCC = 1e-10
 
@@ -70,10 +73,13 @@ def local_potential_matrix(V: np.ndarray, miller: np.ndarray, dims) -> np.ndarra
     return Vhat[pos[..., 0], pos[..., 1], pos[..., 2]]
 
 
-def hamiltonian(lattice, dims, Ecut, kfrac, V):
+def hamiltonian(lattice, dims, Ecut, kfrac, V, kb=None):
+    """Dense H_k; kb = (centres, sigma, D) adds the nonlocal B diag(D) B^H."""
     miller, flat, kin = basis.sphere(lattice, dims, Ecut, kfrac)
     H = local_potential_matrix(V, miller, dims)
     H[np.diag_indices_from(H)] += kin
+    if kb is not None:
+        H = H + kbproj.nonlocal_matrix(lattice, miller, kfrac, *kb)
     return miller, flat, kin, H
 
 
@@ -134,8 +140,11 @@ def solve(system, V=None) -> GroundState:
     lattice, dims = system.lattice, tuple(system.dims)
     volume = float(abs(np.linalg.det(lattice)))
     blocks = []
+    kb = None
+    if getattr(system, "kb_centers", None) is not None:
+        kb = (system.kb_centers, system.kb_sigma, system.kb_D)
     for kf, w in zip(system.kpoints, system.kweights):
-        miller, flat, kin, H = hamiltonian(lattice, dims, system.Ecut, kf, V)
+        miller, flat, kin, H = hamiltonian(lattice, dims, system.Ecut, kf, V, kb)
         eps, vecs = np.linalg.eigh(H)
         blocks.append(KBlock(kfrac=np.array(kf), weight=float(w), miller=miller, flat=flat,
                              kinetic=kin, H=H, eps=eps, vecs=vecs))

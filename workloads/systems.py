@@ -39,6 +39,13 @@ class System:
     depth: float
     width: float
     seed: int
+    # Kleinman-Bylander nonlocal projectors (or None): a Gaussian s and p channel
+    # on every centre, kb_sigma[l] their widths [bohr] and kb_D[l] their coupling
+    # energies [Ha] (the projector functions themselves are defined where they
+    # are used: the oracle and the GPU setup)
+    kb_centers: np.ndarray = None   # (Nkb, 3) Cartesian [bohr]
+    kb_sigma: tuple = None          # (sigma_s, sigma_p)
+    kb_D: tuple = None              # (D_s, D_p)
 
     @property
     def volume(self) -> float:
@@ -134,11 +141,15 @@ def make_system(name: str) -> System:
     dims = tuple(spec["dims"])
     V = gaussian_sum_on_grid(lattice, dims, positions, -spec["depth"], spec["width"])
     kpts, kw = monkhorst_pack(spec.get("kgrid", (1, 1, 1)))
+    kb = spec.get("kb")
     return System(name=name, lattice=lattice, dims=dims, Ecut=float(spec["Ecut"]),
                   kpoints=kpts, kweights=kw, V=V, n_electrons=int(spec["n_electrons"]),
                   temperature=float(spec.get("T", 0.0)), nbands=int(spec["nbands"]),
                   positions=positions, depth=float(spec["depth"]),
-                  width=float(spec["width"]), seed=seed)
+                  width=float(spec["width"]), seed=seed,
+                  kb_centers=positions.copy() if kb else None,
+                  kb_sigma=tuple(kb["sigma"]) if kb else None,
+                  kb_D=tuple(kb["D"]) if kb else None)
 
 
 def perturbation(system: System, kind: str = "bump", seed: int = 0,
@@ -206,10 +217,11 @@ _SPECS = {
     "cfg3": dict(seed=3, cell=(10.0, 10.0, 60.0), dims=(40, 40, 216), Ecut=20.0,
                  layout="slab", layers=(25.0, 30.0, 35.0), jitter=0.02, depth=3.0,
                  width=1.0, n_electrons=48, nbands=80, T=0.01, kgrid=(4, 4, 1)),
-    # Large Gamma-point cell: 20.5 bohr, 64 Gaussians, 128 bands, 96^3 grid.
+    # Large Gamma-point cell: 20.5 bohr, 64 Gaussians with 4 Kleinman-Bylander
+    # projectors each (s + p), 128 bands, 96^3 grid.
     "cfg4": dict(seed=4, cell=(20.5, 20.5, 20.5), dims=(96, 96, 96), Ecut=20.0,
                  layout="cubic_lattice", per_side=4, jitter=0.05, depth=3.0,
-                 width=1.0, n_electrons=256, nbands=130),
+                 width=1.0, n_electrons=256, nbands=136, kb=dict(sigma=(0.8, 0.8), D=(1.0, 0.5))),
     # Tiny cases for dense checks.
     "tiny_insulator": dict(seed=11, cell=(6.0, 6.0, 6.0), dims=(12, 12, 12), Ecut=3.0,
                            layout="random", natoms=2, min_sep=2.5, depth=3.0, width=1.0,
@@ -217,10 +229,13 @@ _SPECS = {
     "tiny_ortho_k": dict(seed=12, cell=(5.0, 6.0, 7.0), dims=(10, 12, 16), Ecut=3.0,
                          layout="random", natoms=2, min_sep=2.5, depth=3.0, width=1.0,
                          n_electrons=4, nbands=4, kgrid=(2, 1, 1)),
+    "tiny_kb": dict(seed=14, cell=(6.0, 6.5, 7.0), dims=(12, 12, 12), Ecut=3.0,
+                    layout="random", natoms=2, min_sep=2.5, depth=3.0, width=1.0,
+                    n_electrons=4, nbands=6, kgrid=(2, 1, 1), kb=dict(sigma=(0.8, 0.9), D=(1.0, 0.5))),
     "tiny_metal": dict(seed=13, cell=(6.0, 6.0, 6.0), dims=(12, 12, 12), Ecut=3.0,
                        layout="random", natoms=2, min_sep=2.5, depth=2.0, width=1.0,
                        n_electrons=6, nbands=24, T=0.05, kgrid=(2, 1, 1)),
 }
 
 CONFIGS = ("cfg1", "cfg2", "cfg3", "cfg4")
-TEST_SYSTEMS = ("tiny_insulator", "tiny_ortho_k", "tiny_metal")
+TEST_SYSTEMS = ("tiny_insulator", "tiny_ortho_k", "tiny_metal", "tiny_kb")
