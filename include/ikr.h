@@ -157,6 +157,21 @@ ikr_status ikr_setup_groundstate(const ikr_system* sys, const ikr_eigenpairs* ei
 /* Sets or replaces the ground state of an existing context (see above). */
 ikr_status ikr_set_eigenpairs(ikr_ctx* ctx, const ikr_eigenpairs* eig, cudaStream_t stream);
 
+/* Kleinman-Bylander nonlocal part of H_k (the nonlocal term of the
+ * pseudopotentials of Sec. 4, here with Gaussian projectors):
+ * V_nl = sum_j D_j |beta_j><beta_j|, on each centre R_a one s and three p
+ * projectors (order s, p_x, p_y, p_z) of unit norm,
+ *   beta_s(r)   = (pi s^2)^-3/4 exp(-|r|^2/(2 s^2)),            s = sigma[0]
+ *   beta_p,a(r) = sqrt(2)/s (pi s^2)^-3/4 r_a exp(-|r|^2/(2 s^2)), s = sigma[1]
+ * (Bloch sums over the lattice), D[0] for s and D[1] for p, in Ha.
+ * centres: host, ncentres x 3 Cartesian bohr; sigma, D: host, 2 each.
+ * Must be called before the eigenpairs are set (IKR_ERR_STATE otherwise);
+ * ncentres = 0 removes the term.  Every later H_k application (the
+ * eigensolver, the CG, ikr_apply_hamiltonian) includes it; the no-allocation
+ * ikr_apply_hamiltonian_noalloc then returns IKR_ERR_ARG. */
+ikr_status ikr_set_nonlocal(ikr_ctx* ctx, int ncentres, const double* centres, const double* sigma, const double* D,
+                            cudaStream_t stream);
+
 /* Computes the lowest nbands eigenpairs of every H_k on the GPU and sets them
  * as by ikr_set_eigenpairs.  The ground state is the input of the method
  * (eq. discretised_KS); the paper obtains it from an SCF, which this library

@@ -132,6 +132,16 @@ ikr_status ikr_set_eigenpairs(ikr_ctx* c, const ikr_eigenpairs* eig, cudaStream_
   return guarded(c, [&] { set_eigenpairs(c, eig); });
 }
 
+ikr_status ikr_set_nonlocal(ikr_ctx* c, int ncentres, const double* centres, const double* sigma, const double* D,
+                            cudaStream_t stream) {
+  if (!c) return IKR_ERR_ARG;
+  c->stream = stream;
+  return guarded(c, [&] {
+    IKR_REQUIRE(!c->have_gs, IKR_ERR_STATE, "set the nonlocal part before the eigenpairs");
+    set_nonlocal(c, ncentres, centres, sigma, D);
+  });
+}
+
 ikr_status ikr_compute_eigenpairs(ikr_ctx* c, int nbands, double tol, int maxit, int degree, double* eigenvalues,
                                   int* iters, double* max_residual, cudaStream_t stream) {
   if (!c) return IKR_ERR_ARG;
@@ -241,6 +251,7 @@ ikr_status ikr_apply_hamiltonian_noalloc(ikr_ctx* c, int k, const void* psi, voi
     IKR_REQUIRE(nvec >= 0, IKR_ERR_ARG, "nvec must be >= 0");
     if (nvec == 0) return;
     IKR_REQUIRE(psi && hpsi && psi != hpsi, IKR_ERR_ARG, "psi and hpsi must be distinct device pointers");
+    IKR_REQUIRE(c->nproj == 0, IKR_ERR_ARG, "the no-allocation H_k has no nonlocal part");
     hamiltonian_noalloc(c, k, static_cast<const double2*>(psi), static_cast<double2*>(hpsi), nvec);
   });
 }

@@ -107,6 +107,7 @@ struct Workspace {
   DBuf<double> val;             // per-system reduced dot products
   DBuf<int> active;
   DBuf<int> alist;              // compacted indices of the active CG systems
+  DBuf<double2> kbc;            // B^H x of the nonlocal products
   DBuf<double> deps, ca, cb;    // deps_s and the density coefficients
   DBuf<double> rn;              // per-system residual norms (mixed precision)
   DBuf<double> grid1, grid2, grid3, grid4, grid5, grid6;   // Ng-sized real scratch
@@ -156,6 +157,10 @@ struct Profiler {
   size_t used[2 * kNumKid] = {};
 };
 
+}  // namespace ikr
+
+namespace ikr {
+void release_blas(void* handle);   // kb.cu
 }  // namespace ikr
 
 struct ikr_ctx {
@@ -218,6 +223,15 @@ struct ikr_ctx {
   ikr::DBuf<float2> d_psir32;
   ikr::SysList occ;             // all occupied (k, n) in k-major order
   int noccmax = 0;
+  // Kleinman-Bylander nonlocal part (kb.cu): nproj projectors per k-point,
+  // block k at k * nproj * ld (projector j at j * ld within it), and the couplings
+  int nproj = 0;
+  double kb_upper = 0.0;        // an upper bound of the largest eigenvalue of V_nl
+  ikr::DBuf<double2> d_kb;
+  ikr::DBuf<float2> d_kb32;
+  ikr::DBuf<double> d_kbD;
+  ikr::DBuf<float> d_kbD32;
+  void* cublas = nullptr;       // cublasHandle_t of the nonlocal products (created on first use)
   ikr::DBuf<double2> d_phi_all; // occupied orbitals, vector s of occ at s * ld (complex128)
   ikr::DBuf<float2> d_phi_all32;
   ikr::DBuf<int> d_phi_off;     // nk: index of the first occupied orbital of k
@@ -232,6 +246,7 @@ struct ikr_ctx {
   int active_hint = 0;          // systems active in the next masked launch (for accounting)
   bool emulate_fp64 = false;    // FP64 plane passes in double-float on the FP32 units (mixed path)
   ~ikr_ctx() {
+    if (cublas) ikr::release_blas(cublas);
     if (h_pinned) cudaFreeHost(h_pinned);
     for (auto& v : prof.ev)
       for (auto e : v) cudaEventDestroy(e);

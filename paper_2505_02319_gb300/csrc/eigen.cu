@@ -263,7 +263,7 @@ std::vector<EigenStats> compute_eigenpairs(ikr_ctx* c, int nbands, double tol, i
     k_block_init<<<blocks, 256, 0, c->stream>>>(B0.p, nb, m, didx.p);
     IKR_CUDA(cudaGetLastError());
     // upper bound of the spectrum: max kinetic energy + max V
-    const double bup = (*std::max_element(K.kin.begin(), K.kin.end()) + c->vmax) * 1.01 + 0.1;
+    const double bup = (*std::max_element(K.kin.begin(), K.kin.end()) + c->vmax + c->kb_upper) * 1.01 + 0.1;
     double2 *X = B0.p, *Y = B1.p, *HX = B2.p, *T = B3.p;
     ch.svqb(X, Y);
     ch.svqb(Y, X);

@@ -1,0 +1,211 @@
+// Kleinman-Bylander nonlocal part of H_k (the nonlocal term of the GTH
+// pseudopotentials of Sec. 4, here with Gaussian projectors):
+//   V_nl = sum_j D_j |beta_j><beta_j|,
+// an s and three p projectors of unit norm on every centre R,
+//   beta_s(r)   = (pi s^2)^{-3/4} exp(-|r|^2 / (2 s^2)),
+//   beta_p,a(r) = sqrt(2)/s (pi s^2)^{-3/4} r_a exp(-|r|^2 / (2 s^2)),
+// whose Bloch sums have the plane-wave coefficients
+//   <e_q | beta> = e^{-i q.R} betahat(q) / sqrt(Omega),  q = k + G,
+//   betahat_s(q)   = (4 pi s^2)^{3/4} exp(-s^2 q^2 / 2),
+//   betahat_p,a(q) = -i s^2 q_a sqrt(2)/s (pi s^2)^{-3/4} (2 pi s^2)^{3/2} exp(-s^2 q^2 / 2).
+// The projector blocks B_k (Nb_k x nproj) are built once on the GPU; an
+// application out += B_k diag(D) B_k^H in is two complex GEMMs per k-point
+// (cuBLAS: the only dense contractions of the term) around a scaling kernel,
+// which also folds <in, V_nl in> = sum_j D_j |(B^H in)_j|^2 into the first
+// <p, Ap> partial of a CG iteration.
+#include <cublas_v2.h>
+
+#include <cmath>
+
+#include "solver.hpp"
+
+namespace ikr {
+
+void release_blas(void* handle) { cublasDestroy(static_cast<cublasHandle_t>(handle)); }
+
+namespace {
+
+void blas_check(cublasStatus_t s, const char* what) {
+  if (s != CUBLAS_STATUS_SUCCESS) throw Error(IKR_ERR_CUDA, std::string("cuBLAS failed: ") + what);
+}
+
+cublasHandle_t blas(ikr_ctx* c) {
+  if (!c->cublas) {
+    cublasHandle_t h = nullptr;
+    blas_check(cublasCreate(&h), "create");
+    c->cublas = h;
+  }
+  cublasHandle_t h = static_cast<cublasHandle_t>(c->cublas);
+  blas_check(cublasSetStream(h, c->stream), "stream");
+  return h;
+}
+
+// B_k for one k-point: projector j = 4 a + ch of centre a (ch: s, p_x, p_y, p_z)
+__global__ void k_kb_build(const int* __restrict__ miller, int nb, int ld, double k0, double k1, double k2,
+                           const double* __restrict__ recip, const double* __restrict__ centres, int nproj,
+                           double ss, double sp, double omega, double2* __restrict__ B, float2* __restrict__ B32) {
+  const size_t n = (size_t)nproj * ld;
+  const double PI = 3.14159265358979323846;
+  const double cs = pow(4.0 * PI * ss * ss, 0.75);
+  const double cp = sqrt(2.0) / sp * pow(PI * sp * sp, -0.75) * pow(2.0 * PI * sp * sp, 1.5);
+  const double inv_sqrt_omega = 1.0 / sqrt(omega);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / ld), g = (int)(e - (size_t)j * ld);
+    double2 v = make_double2(0.0, 0.0);
+    if (g < nb) {
+      const double m0 = miller[3 * g] + k0, m1 = miller[3 * g + 1] + k1, m2 = miller[3 * g + 2] + k2;
+      double q[3];
+      for (int i = 0; i < 3; ++i) q[i] = recip[3 * i] * m0 + recip[3 * i + 1] * m1 + recip[3 * i + 2] * m2;
+      const double q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+      const int a = j / 4, ch = j - 4 * a;
+      const double* R = centres + 3 * a;
+      double sn, cn;
+      sincos(-(q[0] * R[0] + q[1] * R[1] + q[2] * R[2]), &sn, &cn);   // e^{-i q.R}
+      if (ch == 0) {
+        const double f = cs * exp(-0.5 * ss * ss * q2) * inv_sqrt_omega;
+        v = make_double2(f * cn, f * sn);
+      } else {
+        // -i f (cn + i sn) = f sn - i f cn
+        const double f = sp * sp * cp * q[ch - 1] * exp(-0.5 * sp * sp * q2) * inv_sqrt_omega;
+        v = make_double2(f * sn, -f * cn);
+      }
+    }
+    B[e] = v;
+    B32[e] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+// C_js <- D_j C_js for the systems of one k-point; with pap, also
+// pap[s * nparts] += sum_j D_j |C_js|^2 (before the scaling; one warp per system)
+template <typename C, typename Rr>
+__global__ void k_kb_scale(C* __restrict__ Cm, int nproj, int count, const Rr* __restrict__ D, int s0,
+                           const int* __restrict__ active, double* __restrict__ pap, int nparts) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= count) return;
+  C* col = Cm + (size_t)w * nproj;
+  double acc = 0.0;
+  for (int j = lane; j < nproj; j += 32) {
+    const C v = col[j];
+    const Rr d = D[j];
+    acc += (double)d * ((double)v.x * v.x + (double)v.y * v.y);
+    col[j] = mk<C>(d * v.x, d * v.y);
+  }
+  acc = warp_sum(acc);
+  const int s = s0 + w;
+  if (pap && lane == 0 && (!active || active[s])) pap[(size_t)s * nparts] += acc;
+}
+
+}  // namespace
+
+void set_nonlocal(ikr_ctx* c, int ncentres, const double* centres, const double* sigma, const double* D) {
+  IKR_REQUIRE(ncentres >= 0, IKR_ERR_ARG, "ncentres must be >= 0");
+  c->nproj = 0;
+  if (ncentres == 0) return;
+  IKR_REQUIRE(centres && sigma && D, IKR_ERR_ARG, "NULL argument");
+  IKR_REQUIRE(sigma[0] > 0.0 && sigma[1] > 0.0, IKR_ERR_ARG, "projector widths must be positive");
+  const int nproj = 4 * ncentres, nk = (int)c->k.size();
+  const size_t per_k = (size_t)nproj * c->ld;
+  c->d_kb.reserve(per_k * nk);
+  c->d_kb32.reserve(per_k * nk);
+  DBuf<double> dcen, drec;
+  dcen.reserve(3 * (size_t)ncentres);
+  drec.reserve(9);
+  IKR_CUDA(cudaMemcpyAsync(dcen.p, centres, sizeof(double) * 3 * ncentres, cudaMemcpyHostToDevice, c->stream));
+  IKR_CUDA(cudaMemcpyAsync(drec.p, c->recip, sizeof(double) * 9, cudaMemcpyHostToDevice, c->stream));
+  for (int k = 0; k < nk; ++k) {
+    const KPoint& K = c->k[k];
+    DBuf<int> dm;
+    dm.reserve(K.miller.size());
+    IKR_CUDA(cudaMemcpyAsync(dm.p, K.miller.data(), sizeof(int) * K.miller.size(), cudaMemcpyHostToDevice,
+                             c->stream));
+    const size_t n = per_k;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+    k_kb_build<<<blocks, 256, 0, c->stream>>>(dm.p, K.nb, c->ld, K.kfrac[0], K.kfrac[1], K.kfrac[2], drec.p, dcen.p,
+                                             nproj, sigma[0], sigma[1], c->volume, c->d_kb.p + k * per_k,
+                                             c->d_kb32.p + k * per_k);
+    IKR_CUDA(cudaGetLastError());
+    IKR_CUDA(cudaStreamSynchronize(c->stream));   // dm is released at the end of the iteration
+  }
+  std::vector<double> dd(nproj);
+  std::vector<float> df(nproj);
+  for (int a = 0; a < ncentres; ++a)
+    for (int ch = 0; ch < 4; ++ch) {
+      dd[4 * a + ch] = ch == 0 ? D[0] : D[1];
+      df[4 * a + ch] = (float)dd[4 * a + ch];
+    }
+  c->d_kbD.reserve(nproj);
+  c->d_kbD32.reserve(nproj);
+  IKR_CUDA(cudaMemcpyAsync(c->d_kbD.p, dd.data(), sizeof(double) * nproj, cudaMemcpyHostToDevice, c->stream));
+  IKR_CUDA(cudaMemcpyAsync(c->d_kbD32.p, df.data(), sizeof(float) * nproj, cudaMemcpyHostToDevice, c->stream));
+  IKR_CUDA(cudaStreamSynchronize(c->stream));
+  c->nproj = nproj;
+  // V_nl <= sum_j max(D_j, 0) ||beta_j||^2 with ||beta_j||^2 = 1 up to image overlaps
+  c->kb_upper = 1.1 * 4.0 * ncentres * std::max(std::max(D[0], D[1]), 0.0);
+}
+
+namespace {
+
+template <typename R> struct Blas;
+template <> struct Blas<double> {
+  using T = cuDoubleComplex;
+  static const double2* B(ikr_ctx* c) { return c->d_kb.p; }
+  static const double* D(ikr_ctx* c) { return c->d_kbD.p; }
+  static cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
+                             double ar, const double2* A, int lda, const double2* Bm, int ldb, double br, double2* Cm,
+                             int ldc) {
+    const T a = make_cuDoubleComplex(ar, 0.0), b = make_cuDoubleComplex(br, 0.0);
+    return cublasZgemm(h, ta, tb, m, n, k, &a, reinterpret_cast<const T*>(A), lda, reinterpret_cast<const T*>(Bm),
+                       ldb, &b, reinterpret_cast<T*>(Cm), ldc);
+  }
+};
+template <> struct Blas<float> {
+  using T = cuComplex;
+  static const float2* B(ikr_ctx* c) { return c->d_kb32.p; }
+  static const float* D(ikr_ctx* c) { return c->d_kbD32.p; }
+  static cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
+                             double ar, const float2* A, int lda, const float2* Bm, int ldb, double br, float2* Cm,
+                             int ldc) {
+    const T a = make_cuComplex((float)ar, 0.f), b = make_cuComplex((float)br, 0.f);
+    return cublasCgemm(h, ta, tb, m, n, k, &a, reinterpret_cast<const T*>(A), lda, reinterpret_cast<const T*>(Bm),
+                       ldb, &b, reinterpret_cast<T*>(Cm), ldc);
+  }
+};
+
+}  // namespace
+
+template <typename R>
+void apply_nonlocal(ikr_ctx* c, const SysList& L, const C_t<R>* in, int ld, C_t<R>* out, const int* active,
+                    double* pap, int nparts) {
+  if (c->nproj == 0 || L.n == 0) return;
+  ProfScope ps(c, kKidProjApply, 2, L.n, (int)sizeof(R));
+  cublasHandle_t h = blas(c);
+  const int np = c->nproj;
+  const int nk_groups = (int)L.kcount.size();
+  const int* kstart = L.kstart.data();
+  const int* kcount = L.kcount.data();
+  int maxc = 0;
+  for (int g = 0; g < nk_groups; ++g) maxc = std::max(maxc, kcount[g]);
+  if (maxc == 0) return;
+  DBuf<double2>& ws = c->ws.kbc;
+  ws.reserve(((size_t)np * maxc * sizeof(C_t<R>) + sizeof(double2) - 1) / sizeof(double2));
+  C_t<R>* Cm = reinterpret_cast<C_t<R>*>(ws.p);
+  const size_t per_k = (size_t)np * c->ld;
+  for (int g = 0; g < nk_groups; ++g) {
+    const int cnt = kcount[g];
+    if (cnt == 0) continue;
+    const int k = g, nb = c->k[k].nb;
+    const C_t<R>* Bk = Blas<R>::B(c) + k * per_k;
+    const C_t<R>* ik = in + (size_t)kstart[g] * ld;
+    C_t<R>* ok = out + (size_t)kstart[g] * ld;
+    blas_check(Blas<R>::gemm(h, CUBLAS_OP_C, CUBLAS_OP_N, np, cnt, nb, 1.0, Bk, c->ld, ik, ld, 0.0, Cm, np), "B^H x");
+    k_kb_scale<C_t<R>, R><<<(cnt * 32 + 255) / 256, 256, 0, c->stream>>>(Cm, np, cnt, Blas<R>::D(c), kstart[g],
+                                                                         active, pap, nparts);
+    IKR_CUDA(cudaGetLastError());
+    blas_check(Blas<R>::gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, nb, cnt, np, 1.0, Bk, c->ld, Cm, np, 1.0, ok, ld), "B C");
+  }
+}
+template void apply_nonlocal<double>(ikr_ctx*, const SysList&, const double2*, int, double2*, const int*, double*,
+                                     int);
+template void apply_nonlocal<float>(ikr_ctx*, const SysList&, const float2*, int, float2*, const int*, double*, int);
+
+}  // namespace ikr

@@ -168,6 +168,7 @@ CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv
     launch_z_inverse<double>(c, L, Xv, ld, act, w.b1.p);
     launch_plane<double>(c, L, w.b1.p, c->d_Vt.p, nullptr, act, w.b4.p);
     launch_z_forward<double>(c, L, w.b4.p, w.W.p, ld, Xv, w.val.p, true, act);   // in range(Q): x is
+    apply_nonlocal<double>(c, L, Xv, ld, w.W.p, act, nullptr, 0);
     {
       ProfScope ps(c, kKidCgVec, 1);
       k_residual<<<egrid, 256, 0, strm>>>(Bv, w.W.p, ld, L.d_k.p, c->d_nb.p, act, w.R.p, w.B32.p);

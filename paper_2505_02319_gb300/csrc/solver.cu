@@ -93,6 +93,7 @@ void hamiltonian(ikr_ctx* c, int k, const C_t<R>* psi, C_t<R>* hpsi, int ld, int
     launch_z_inverse<R>(c, L, in, ld, nullptr, Bufs<R>::b1(c));
     launch_plane<R>(c, L, Bufs<R>::b1(c), Bufs<R>::pot(c), nullptr, nullptr, Bufs<R>::b4(c));
     launch_z_forward<R>(c, L, Bufs<R>::b4(c), out, ld, in, nullptr, true, nullptr);
+    apply_nonlocal<R>(c, L, in, ld, out, nullptr, nullptr, 0);
   }
 }
 template void hamiltonian<double>(ikr_ctx*, int, const double2*, double2*, int, int);
@@ -154,6 +155,8 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
                     c->active_hint);
     launch_z_forward<R>(c, L, Bufs<R>::b4(c), v.W, c->ld, v.P, sys + kSysShift * n, true, act, w.dpart.p,
                         w.alist.p, c->active_hint);
+    // nonlocal part of A p, and <p, V_nl p> folded into the first <p, Ap> partial
+    apply_nonlocal<R>(c, L, v.P, c->ld, v.W, act, w.dpart.p, zf_chunks(c, (int)sizeof(R)));
     bool fused = false;
     if constexpr (sizeof(R) == 4) {
       // alpha, x, r, stopping test, z = Q M^-1 r, beta and p in one launch

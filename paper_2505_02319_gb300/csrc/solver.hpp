@@ -9,6 +9,14 @@
 
 namespace ikr {
 
+// Kleinman-Bylander nonlocal part (kb.cu)
+void set_nonlocal(ikr_ctx* c, int ncentres, const double* centres, const double* sigma, const double* D);
+// out += B diag(D) B^H in for the systems of L (k-grouped); with pap, also
+// pap[s * nparts] += <in_s, V_nl in_s> for the active systems
+template <typename R>
+void apply_nonlocal(ikr_ctx* c, const SysList& L, const C_t<R>* in, int ld, C_t<R>* out, const int* active,
+                    double* pap, int nparts);
+
 // ground-state eigensolver (eigen.cu)
 struct EigenStats {
   int iters = 0;              // filter + Rayleigh-Ritz cycles

@@ -45,6 +45,8 @@ def context_for(system, nbands=None, eigensolver="dense", eig_tol=1e-10) -> ikr.
                                         system.kweights, system.V, system.temperature,
                                         system.n_electrons)
     nb = nbands or system.nbands
+    if getattr(system, "kb_centers", None) is not None:
+        ctx.set_nonlocal(system.kb_centers, system.kb_sigma, system.kb_D)
     if eigensolver == "chfsi":
         ctx.compute_eigenpairs(nb, tol=eig_tol)
     elif eigensolver == "dense":

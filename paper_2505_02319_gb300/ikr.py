@@ -81,6 +81,7 @@ def _load():
         "ikr_setup_groundstate": (I, [ct.POINTER(System), ct.POINTER(Eigenpairs), S, ct.POINTER(P)]),
         "ikr_set_eigenpairs": (I, [P, ct.POINTER(Eigenpairs), S]),
         "ikr_compute_eigenpairs": (I, [P, I, D, I, I, ct.POINTER(D), ct.POINTER(I), ct.POINTER(D), S]),
+        "ikr_set_nonlocal": (I, [P, I, ct.POINTER(D), ct.POINTER(D), ct.POINTER(D), S]),
         "ikr_hermitian_eigh": (I, [I, ct.POINTER(D), ct.POINTER(D), ct.POINTER(D)]),
         "ikr_num_kpoints": (I, [P]),
         "ikr_basis_size": (I, [P, I, ct.POINTER(I)]),
@@ -189,6 +190,13 @@ class Context:
     def set_eigenpairs(self, eigenvalues, eigenvectors):
         eig, keep = _eigenpairs(eigenvalues, eigenvectors)
         self._check(_LIB.ikr_set_eigenpairs(self._h, ct.byref(eig), _stream()))
+
+    def set_nonlocal(self, centres, sigma, D):
+        """Kleinman-Bylander projectors (Gaussian s and p) on the given centres."""
+        cen, cp = _dbl(np.asarray(centres, dtype=np.float64).reshape(-1, 3))
+        sg, sp = _dbl(sigma)
+        dd, dp = _dbl(D)
+        self._check(_LIB.ikr_set_nonlocal(self._h, len(cen), cp, sp, dp, _stream()))
 
     def compute_eigenpairs(self, nbands, tol=1e-10, maxit=200, degree=12):
         """Lowest ``nbands`` eigenpairs of every H_k on the GPU (Chebyshev-filtered

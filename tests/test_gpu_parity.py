@@ -10,7 +10,7 @@ from gpu_common import context, dev, oracle_state, rel, system, torch
 
 pytestmark = pytest.mark.gpu
 
-SMALL = ["tiny_insulator", "tiny_ortho_k", "tiny_metal", "cfg1"]
+SMALL = ["tiny_insulator", "tiny_ortho_k", "tiny_metal", "tiny_kb", "cfg1"]
 
 
 @pytest.mark.parametrize("name", SMALL)
