@@ -226,7 +226,7 @@ struct ikr_ctx {
   // Kleinman-Bylander nonlocal part (kb.cu): nproj projectors per k-point,
   // block k at k * nproj * ld (projector j at j * ld within it), and the couplings
   int nproj = 0;
-  double kb_upper = 0.0;        // an upper bound of the largest eigenvalue of V_nl
+  double kb_dmax = 0.0;         // the largest coupling D_j
   ikr::DBuf<double2> d_kb;
   ikr::DBuf<float2> d_kb32;
   ikr::DBuf<double> d_kbD;

@@ -262,8 +262,30 @@ std::vector<EigenStats> compute_eigenpairs(ikr_ctx* c, int nbands, double tol, i
     elementwise_grid(n, &blocks);
     k_block_init<<<blocks, 256, 0, c->stream>>>(B0.p, nb, m, didx.p);
     IKR_CUDA(cudaGetLastError());
-    // upper bound of the spectrum: max kinetic energy + max V
-    const double bup = (*std::max_element(K.kin.begin(), K.kin.end()) + c->vmax + c->kb_upper) * 1.01 + 0.1;
+    // upper bound of the spectrum: max kinetic energy + max V + ||V_nl||, with
+    // ||B diag(D) B^H|| <= max(D, 0) ||B^H B|| <= max(D, 0) max_i sum_j |(B^H B)_ij|
+    double vnl = 0.0;
+    if (c->nproj > 0) {
+      const int np = c->nproj;
+      DBuf<double2> G;
+      G.reserve((size_t)np * np);
+      const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+      const cuDoubleComplex* Bk = reinterpret_cast<const cuDoubleComplex*>(c->d_kb.p + (size_t)k * np * c->ld);
+      cublas_check(cublasZgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, np, np, nb, &one, Bk, c->ld, Bk, c->ld, &zero,
+                               reinterpret_cast<cuDoubleComplex*>(G.p), np),
+                   "projector gram");
+      std::vector<double2> hg((size_t)np * np);
+      IKR_CUDA(cudaMemcpyAsync(hg.data(), G.p, sizeof(double2) * np * np, cudaMemcpyDeviceToHost, c->stream));
+      IKR_CUDA(cudaStreamSynchronize(c->stream));
+      double rowmax = 0.0;
+      for (int i = 0; i < np; ++i) {
+        double r = 0.0;
+        for (int j = 0; j < np; ++j) r += std::hypot(hg[i + (size_t)j * np].x, hg[i + (size_t)j * np].y);
+        rowmax = std::max(rowmax, r);
+      }
+      vnl = std::max(c->kb_dmax, 0.0) * rowmax;
+    }
+    const double bup = (*std::max_element(K.kin.begin(), K.kin.end()) + c->vmax + vnl) * 1.01 + 0.1;
     double2 *X = B0.p, *Y = B1.p, *HX = B2.p, *T = B3.p;
     ch.svqb(X, Y);
     ch.svqb(Y, X);

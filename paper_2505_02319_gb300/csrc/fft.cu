@@ -595,6 +595,7 @@ template <typename R>
 void launch_synth_planes(ikr_ctx* c, int nsys, const C_t<R>* b1, C_t<R>* out) {
   if (nsys == 0) return;
   ProfScope ps(c, kKidPlane, 1, nsys, (int)sizeof(R));
+  if (launch_synth_fast<R>(c, nsys, b1, out)) return;
   const int Nx = c->N[0], Ny = c->N[1], Nz = c->N[2];
   const size_t smem = sizeof(C_t<R>) * (Nx + Ny + 2 * (size_t)Ny * (Nx + 1)) + sizeof(int) * c->nxa;
   set_smem(k_synth_planes<R>, smem);

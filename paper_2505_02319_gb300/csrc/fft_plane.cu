@@ -333,6 +333,65 @@ __global__ void __launch_bounds__(256) k_plane_t(const typename io<R>::cx* __res
   }
 }
 
+// Real-space planes of the sphere vectors (same result as k_synth_planes in
+// fft.cu, which it replaces for the supported grids): the z-transformed
+// columns b1 scattered into a plane, inverse y-lines of the active x
+// positions, inverse x-lines, written out.  One plane in shared memory, the
+// lines transformed in place (the generic kernel needs two plane buffers).
+template <typename R, int NX, int NY>
+__global__ void __launch_bounds__(256) k_synth_t(const typename io<R>::cx* __restrict__ b1, int nc, int ncp,
+                                                 const int* __restrict__ col_xy, const int* __restrict__ xpos,
+                                                 int nxa, int Nz, const typename io<R>::cx* __restrict__ twx,
+                                                 const typename io<R>::cx* __restrict__ twy,
+                                                 typename io<R>::cx* __restrict__ out) {
+  using C = C_t<R>;
+  using G = PlaneGeom<C, NX, NY>;
+  constexpr int ldp = G::ldp;
+  constexpr int TX = Tpl<NX>::v, TY = Tpl<NY>::v;
+  const int iz = blockIdx.x, s = blockIdx.y;
+  extern __shared__ unsigned char smem_raw[];
+  C* tx = reinterpret_cast<C*>(smem_raw);
+  C* ty = tx + NX;
+  C* plane = ty + NY;
+  int* xp = reinterpret_cast<int*>(plane + G::plane);
+  for (int i = threadIdx.x; i < NX; i += blockDim.x) tx[i] = to_c<C>(twx[i]);
+  for (int i = threadIdx.x; i < NY; i += blockDim.x) ty[i] = to_c<C>(twy[i]);
+  for (int i = threadIdx.x; i < nxa; i += blockDim.x) xp[i] = xpos[i];
+  for (int i = threadIdx.x; i < G::plane; i += blockDim.x) plane[i] = mk<C>(R(0), R(0));
+  __syncthreads();
+  const typename io<R>::cx* src = b1 + ((size_t)s * Nz + iz) * ncp;
+  for (int col = threadIdx.x; col < nc; col += blockDim.x)
+    plane[col_xy[2 * col + 1] * ldp + col_xy[2 * col]] = to_c<C>(src[col]);
+  __syncthreads();
+  {
+    const int slots = blockDim.x / TY, slot = threadIdx.x / TY, t = threadIdx.x % TY;
+    const int rounds = (nxa + slots - 1) / slots;
+    for (int r = 0; r < rounds; ++r) {
+      const int l = r * slots + slot;
+      const bool ok = l < nxa;
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (ok) line_fft<C, NY, true>(plane + xp[l], ldp, ty, t, mask);
+    }
+  }
+  __syncthreads();
+  {
+    const int slots = blockDim.x / TX, slot = threadIdx.x / TX, t = threadIdx.x % TX;
+    const int rounds = (NY + slots - 1) / slots;
+    for (int r = 0; r < rounds; ++r) {
+      const int iy = r * slots + slot;
+      const bool ok = iy < NY;
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (ok) line_fft<C, NX, true>(plane + iy * ldp, 1, tx, t, mask);
+    }
+  }
+  __syncthreads();
+  typename io<R>::cx* dst = out + ((size_t)s * Nz + iz) * NY * NX;
+  for (int e = threadIdx.x; e < NY * NX; e += blockDim.x) {
+    const int iy = e / NX, ix = e - iy * NX;
+    dst[e] = from_c(plane[iy * ldp + ix]);
+  }
+}
+
 // Density accumulation with compile-time line lengths (same result as
 // k_density in fft.cu, which it replaces for the supported grids):
 //   part[g][iz][iy][ix] = sum_{s in group g} a_s Re(conj(psi_s) dpsi_s) + b_s |psi_s|^2,
@@ -482,7 +541,31 @@ bool try_density(ikr_ctx* c, int nsys, const typename io<R>::cx* b1d, const type
   return true;
 }
 
+template <typename R, int NX, int NY>
+bool try_synth(ikr_ctx* c, int nsys, const typename io<R>::cx* b1, typename io<R>::cx* out) {
+  if (c->N[0] != NX || c->N[1] != NY) return false;
+  using G = PlaneGeom<C_t<R>, NX, NY>;
+  const size_t smem = sizeof(C_t<R>) * (NX + NY + (size_t)G::plane) + sizeof(int) * c->nxa;
+  if (smem > 227 * 1024) return false;
+  IKR_CUDA(cudaFuncSetAttribute(k_synth_t<R, NX, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(c->N[2], nsys);
+  k_synth_t<R, NX, NY><<<grid, 256, smem, c->stream>>>(b1, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa,
+                                                        c->N[2], twp<R>(c, 0), twp<R>(c, 1), out);
+  IKR_CUDA(cudaGetLastError());
+  return true;
+}
+
 }  // namespace
+
+template <typename R>
+bool launch_synth_fast(ikr_ctx* c, int nsys, const typename io<R>::cx* b1, typename io<R>::cx* out) {
+  return try_synth<R, 48, 48>(c, nsys, b1, out) || try_synth<R, 32, 32>(c, nsys, b1, out) ||
+         try_synth<R, 40, 40>(c, nsys, b1, out) || try_synth<R, 96, 96>(c, nsys, b1, out) ||
+         try_synth<R, 12, 12>(c, nsys, b1, out) || try_synth<R, 10, 12>(c, nsys, b1, out) ||
+         try_synth<R, 24, 24>(c, nsys, b1, out);
+}
+template bool launch_synth_fast<float>(ikr_ctx*, int, const float2*, float2*);
+template bool launch_synth_fast<double>(ikr_ctx*, int, const double2*, double2*);
 
 template <typename R>
 bool launch_density_fast(ikr_ctx* c, int nsys, const typename io<R>::cx* b1d, const typename io<R>::cx* psir,

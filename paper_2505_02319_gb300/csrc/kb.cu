@@ -139,8 +139,7 @@ void set_nonlocal(ikr_ctx* c, int ncentres, const double* centres, const double*
   IKR_CUDA(cudaMemcpyAsync(c->d_kbD32.p, df.data(), sizeof(float) * nproj, cudaMemcpyHostToDevice, c->stream));
   IKR_CUDA(cudaStreamSynchronize(c->stream));
   c->nproj = nproj;
-  // V_nl <= sum_j max(D_j, 0) ||beta_j||^2 with ||beta_j||^2 = 1 up to image overlaps
-  c->kb_upper = 1.1 * 4.0 * ncentres * std::max(std::max(D[0], D[1]), 0.0);
+  c->kb_dmax = std::max(D[0], D[1]);
 }
 
 namespace {

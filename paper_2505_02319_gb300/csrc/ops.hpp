@@ -46,6 +46,9 @@ void launch_z_forward(ikr_ctx* c, const SysList& L, const C_t<R>* b4, C_t<R>* ou
                       double* dpart = nullptr, const int* list = nullptr, int nlist = 0);
 int zf_chunks(ikr_ctx* c);    // dot partials per system written by launch_z_forward (largest)
 int zf_chunks(ikr_ctx* c, int fp_bytes);   // ... by the launch of that precision
+// Real-space planes of sphere vectors by the compile-time kernel (fft_plane.cu); false: not covered
+template <typename R>
+bool launch_synth_fast(ikr_ctx* c, int nsys, const typename io<R>::cx* b1, typename io<R>::cx* out);
 // Density partial planes by the compile-time kernel (fft_plane.cu) into
 // c->ws.dens_part; *ngroups = the number of partial planes.  false: shape not covered.
 template <typename R>

@@ -316,6 +316,22 @@ void make_syslist(ikr_ctx* c, SysList& L, int nsys, const int* kof, const int* b
   upload(L.d_kcount, L.kcount, c->stream);
 }
 
+// rho[C order] = scale * sum_s wf[s] |psir_s|^2 from the cached real-space
+// planes [s][i3][i2][i1] (systems added in order)
+__global__ void k_rho_from_planes(const double2* __restrict__ psir, int S, int N1, int N2, int N3,
+                                  const double* __restrict__ wf, double scale, double* __restrict__ rho) {
+  const size_t ng = (size_t)N1 * N2 * N3;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ng; e += (size_t)gridDim.x * blockDim.x) {
+    double a = 0.0;
+    for (int s = 0; s < S; ++s) {
+      const double2 v = psir[(size_t)s * ng + e];
+      a += wf[s] * (v.x * v.x + v.y * v.y);
+    }
+    const size_t i1 = e % N1, i2 = (e / N1) % N2, i3 = e / ((size_t)N1 * N2);
+    rho[(i1 * N2 + i2) * N3 + i3] = scale * a;
+  }
+}
+
 void set_eigenpairs(ikr_ctx* c, const ikr_eigenpairs* eig) {
   IKR_REQUIRE(eig && eig->eigenvalues && eig->eigenvectors, IKR_ERR_ARG, "eigenpairs are NULL");
   const int nk = (int)c->k.size();
@@ -456,7 +472,12 @@ void set_eigenpairs(ikr_ctx* c, const ikr_eigenpairs* eig) {
   upload(d_wf, wf, st);
   c->d_rho.reserve(c->Ng);
   c->d_kxc.reserve(c->Ng);
-  launch_density<double>(c, S, c->d_b1phi.p, nullptr, nullptr, d_wf.p, c->d_rho.p, 1.0 / c->volume);
+  {
+    const int blocks = (int)std::min<size_t>((c->Ng + 255) / 256, 152 * 16);
+    k_rho_from_planes<<<blocks, 256, 0, st>>>(c->d_psir.p, S, c->N[0], c->N[1], c->N[2], d_wf.p, 1.0 / c->volume,
+                                              c->d_rho.p);
+    IKR_CUDA(cudaGetLastError());
+  }
   exchange_kernel(c);
   {
     // ||K|| <= max 4 pi/|G|^2 + max |K^xc| (K^H and K^xc symmetric; K^xc <= 0)

@@ -209,8 +209,8 @@ class Context:
         res = (ct.c_double * nk)()
         st = _LIB.ikr_compute_eigenpairs(self._h, int(nbands), float(tol), int(maxit), int(degree),
                                          ev.ctypes.data_as(ct.POINTER(ct.c_double)), iters, res, _stream())
-        self._check(st)
         self.eigenvalues, self.eig_iters, self.eig_residuals = ev, list(iters), list(res)
+        self._check(st)
         return ev, list(iters), list(res)
 
     def _check(self, st, allow=()):
