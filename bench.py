@@ -306,6 +306,12 @@ FP64_PEAK_TFLOPS = 1.20                              # FP64 FMA-chain rate measu
 # radix-4/3 butterflies and twiddles of the plane pass mix about 2 adds : 1 product
 DF64_INSTR_PER_FLOP = (2 * 8 + 4) / 3.0
 DF64_PEAK_TFLOPS = FP32_INSTR_PEAK / DF64_INSTR_PER_FLOP
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per system of one
+# launch of each plane kernel, from one ncu capture of a launch with every
+# system active (k_plane_r: 22.89 MB read + 7 KB written for 252 systems;
+# k_plane_t<dfloat>: 41.83 MB + 4.48 MB for 251), 48^3 grid
+TRAFFIC_PER_UNIT_FP32 = (22.888e6 + 7.2e3) / 252
+TRAFFIC_PER_UNIT_DF64 = (41.832e6 + 4.479e6) / 251
 
 
 def roofline(d, geom, peaks):
@@ -327,7 +333,9 @@ def roofline(d, geom, peaks):
         entries.append((d["ms_fp32"], {
             "kernel": "k_plane_r<48,48> (H_k plane pass of the FP32 CG)", "bound": "alu",
             "achieved": tfl, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tfl / FP32_PEAK_TFLOPS,
-            "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+            "traffic": TRAFFIC_PER_UNIT_FP32 * d["units_fp32"] / calls if geom[:3] == (48, 48, 48) else None,
+            "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled to the average launch)",
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
             "total_ms": d["ms_fp32"], "avg_launch_ms": d["ms_fp32"] / calls,
             "units_per_launch": d["units_fp32"] / calls, "algorithmic_flops_per_unit": f32,
             "algorithmic_bytes_per_unit": b32, "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / peaks["hbm_gbs"]}))
@@ -338,7 +346,9 @@ def roofline(d, geom, peaks):
         entries.append((d["ms_fp64"], {
             "kernel": "k_plane_t<dfloat,48,48> (FP64-accurate plane pass, double-float on the FP32 pipe)",
             "bound": "alu", "achieved": tfl, "peak": DF64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64-equivalent)",
-            "frac": tfl / DF64_PEAK_TFLOPS, "traffic": None,
+            "frac": tfl / DF64_PEAK_TFLOPS,
+            "traffic": TRAFFIC_PER_UNIT_DF64 * d["units_fp64"] / calls if geom[:3] == (48, 48, 48) else None,
+            "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled to the average launch)",
             "peak_source": f"derived: FP32 instruction peak / {DF64_INSTR_PER_FLOP:.2f} FP32 instructions "
                            f"per double-float flop",
             "vs_native_fp64_peak": tfl / FP64_PEAK_TFLOPS,
