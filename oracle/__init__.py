@@ -19,8 +19,8 @@ the oracle is that definition written out:
   * Algorithm 1 (inexact GMRES) with the CG tolerances of Table strategies /
     Table strategies_k, emulated with a plain NumPy CG, for strategy tests.
 
-Readings where the paper is silent or garbled are listed in the design doc and
-in the docstrings of the functions that take them.
+Readings where the paper is silent or garbled are stated in the docstrings
+of the functions that take them.
 
 Parity unpinned: nothing in this package.  Every function is pinned by a
 ``-m "not gpu"`` test in tests/test_oracle_*.py.

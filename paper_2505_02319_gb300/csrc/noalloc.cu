@@ -4,7 +4,7 @@
 // code that records its GPU work into a CUDA graph by stream capture (a
 // cudaMalloc during capture invalidates the capture), applications whose
 // device memory is handed out by their own pool and must not be fragmented
-// or exceeded, and latency-critical loops that must not enter the driver's
+// or exceeded, and latency-critical loops that must not enter the CUDA
 // allocator.  ikr_apply_hamiltonian may grow the context's workspace; this
 // entry point instead keeps its scratch (the z-transformed columns of every
 // vector and the per-vector k index) in one file-scope device array of
