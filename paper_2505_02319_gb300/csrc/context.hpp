@@ -232,6 +232,7 @@ struct ikr_ctx {
   ikr::DBuf<double> d_kbD;
   ikr::DBuf<float> d_kbD32;
   void* cublas = nullptr;       // cublasHandle_t of the nonlocal products (created on first use)
+  ikr::DBuf<float4> d_psir_df; // the real-space orbital planes as double-float (x.hi, x.lo, y.hi, y.lo)
   ikr::DBuf<double2> d_phi_all; // occupied orbitals, vector s of occ at s * ld (complex128)
   ikr::DBuf<float2> d_phi_all32;
   ikr::DBuf<int> d_phi_off;     // nk: index of the first occupied orbital of k

@@ -565,9 +565,11 @@ void launch_density(ikr_ctx* c, int nsys, const C_t<R>* b1phi, const C_t<R>* b1d
   bool fast = false;
   int G = 1;
   if (nsys > 0 && psi_real && b1d) {
-    if (sizeof(R) == 8 && c->emulate_fp64)
+    if (sizeof(R) == 8 && c->emulate_fp64 && c->d_psir_df.p &&
+        reinterpret_cast<const void*>(psi_real) == reinterpret_cast<const void*>(c->d_psir.p))
+      // the double-float kernel reads the (hi, lo) copy of the cached orbitals
       fast = launch_density_fast<dfloat>(c, nsys, reinterpret_cast<const double2*>(b1d),
-                                         reinterpret_cast<const double2*>(psi_real), coef_a, coef_b, &G);
+                                         reinterpret_cast<const double2*>(c->d_psir_df.p), coef_a, coef_b, &G);
     if (!fast) fast = launch_density_fast<R>(c, nsys, b1d, psi_real, coef_a, coef_b, &G);
   }
   if (fast) {

@@ -421,9 +421,12 @@ __global__ void __launch_bounds__(256) k_density_t(const typename io<R>::cx* __r
   for (int i = threadIdx.x; i < NX; i += blockDim.x) tx[i] = to_c<C>(twx[i]);
   for (int i = threadIdx.x; i < NY; i += blockDim.x) ty[i] = to_c<C>(twy[i]);
   for (int i = threadIdx.x; i < nxa; i += blockDim.x) xp[i] = xpos[i];
-  double acc[NE];
+  // double-float: products and sums on the FP32 pipe, the orbitals read from
+  // their (hi, lo) copy; FP64 otherwise
+  using A = typename std::conditional<std::is_same<R, dfloat>::value, dfloat, double>::type;
+  A acc[NE];
 #pragma unroll
-  for (int i = 0; i < NE; ++i) acc[i] = 0.0;
+  for (int i = 0; i < NE; ++i) acc[i] = A(0.0);
   const int s0 = (int)((long long)g * nsys / ngroups), s1 = (int)((long long)(g + 1) * nsys / ngroups);
   for (int sb = s0; sb < s1; sb += PL) {
     const int npl = min(PL, s1 - sb);
@@ -468,17 +471,33 @@ __global__ void __launch_bounds__(256) k_density_t(const typename io<R>::cx* __r
     __syncthreads();
     for (int p = 0; p < npl; ++p) {
       const int s = sb + p;
-      const double a = coef_a[s], b = coef_b[s];
-      const typename io<R>::cx* ps = psir + ((size_t)s * Nz + iz) * NX * NY;
+      if constexpr (std::is_same<R, dfloat>::value) {
+        const dfloat a = to_r<dfloat>(coef_a[s]), b = to_r<dfloat>(coef_b[s]);
+        const float4* ps = reinterpret_cast<const float4*>(psir) + ((size_t)s * Nz + iz) * NX * NY;
 #pragma unroll
-      for (int i = 0; i < NE; ++i) {
-        const int e = threadIdx.x + 256 * i;
-        if (e < NX * NY) {
-          const int iy = e / NX, ix = e - iy * NX;
-          const auto d = from_c(planes[p * G::plane + iy * ldp + ix]);
-          const typename io<R>::cx q = ps[e];
-          const double px = (double)q.x, py = (double)q.y;
-          acc[i] += a * (px * (double)d.x + py * (double)d.y) + b * (px * px + py * py);
+        for (int i = 0; i < NE; ++i) {
+          const int e = threadIdx.x + 256 * i;
+          if (e < NX * NY) {
+            const int iy = e / NX, ix = e - iy * NX;
+            const dfloat2 d = planes[p * G::plane + iy * ldp + ix];
+            const float4 q = ps[e];
+            const dfloat px(q.x, q.y), py(q.z, q.w);
+            acc[i] += a * (px * d.x + py * d.y) + b * (px * px + py * py);
+          }
+        }
+      } else {
+        const double a = coef_a[s], b = coef_b[s];
+        const typename io<R>::cx* ps = psir + ((size_t)s * Nz + iz) * NX * NY;
+#pragma unroll
+        for (int i = 0; i < NE; ++i) {
+          const int e = threadIdx.x + 256 * i;
+          if (e < NX * NY) {
+            const int iy = e / NX, ix = e - iy * NX;
+            const auto d = from_c(planes[p * G::plane + iy * ldp + ix]);
+            const typename io<R>::cx q = ps[e];
+            const double px = (double)q.x, py = (double)q.y;
+            acc[i] += a * (px * (double)d.x + py * (double)d.y) + b * (px * px + py * py);
+          }
         }
       }
     }
@@ -487,7 +506,7 @@ __global__ void __launch_bounds__(256) k_density_t(const typename io<R>::cx* __r
 #pragma unroll
   for (int i = 0; i < NE; ++i) {
     const int e = threadIdx.x + 256 * i;
-    if (e < NX * NY) dst[e] = acc[i];
+    if (e < NX * NY) dst[e] = to_d(acc[i]);
   }
 }
 

@@ -316,6 +316,15 @@ void make_syslist(ikr_ctx* c, SysList& L, int nsys, const int* kof, const int* b
   upload(L.d_kcount, L.kcount, c->stream);
 }
 
+// (hi, lo) float pairs of complex128 values: hi = fl32(x), lo = fl32(x - hi)
+__global__ void k_to_dfloat(const double2* __restrict__ in, size_t n, float4* __restrict__ out) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = in[e];
+    const float xh = __double2float_rn(v.x), yh = __double2float_rn(v.y);
+    out[e] = make_float4(xh, __double2float_rn(v.x - (double)xh), yh, __double2float_rn(v.y - (double)yh));
+  }
+}
+
 // rho[C order] = scale * sum_s wf[s] |psir_s|^2 from the cached real-space
 // planes [s][i3][i2][i1] (systems added in order)
 __global__ void k_rho_from_planes(const double2* __restrict__ psir, int S, int N1, int N2, int N3,
@@ -465,6 +474,13 @@ void set_eigenpairs(ikr_ctx* c, const ikr_eigenpairs* eig) {
   launch_synth_planes<double>(c, S, c->d_b1phi.p, c->d_psir.p);
   c->d_psir32.reserve((size_t)S * c->Ng);
   to_fp32(c, c->d_psir.p, (size_t)S * c->Ng, c->d_psir32.p);
+  {
+    const size_t n = (size_t)S * c->Ng;
+    c->d_psir_df.reserve(n);
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 32);
+    k_to_dfloat<<<blocks, 256, 0, st>>>(c->d_psir.p, n, c->d_psir_df.p);
+    IKR_CUDA(cudaGetLastError());
+  }
   // density rho = sum_k w_k sum_n f_nk |F^-1 phi_nk|^2 and K^xc[rho]
   std::vector<double> wf(S);
   for (int s = 0; s < S; ++s) wf[s] = w_o[s] * f_o[s];

@@ -1,8 +1,10 @@
 """The fused FP32 CG update (one thread-block cluster per k-point: alpha, x, r,
 the stopping test, z = Q M^-1 r and p in one launch) against the sequence of
 kernels it replaces, selected with IKR_CG_FUSED=0 when a context plans: both
-solve the Dyson equation to the true residual tau, their solutions agree to
-the FP32 level, and the fused path really replaces the scalar launches."""
+solve the Dyson equation to the true residual tau with the guaranteed
+tolerances (grt_exact, Theorem inexact_gmres_dyson; bal drops the gap terms
+and carries no such guarantee), their solutions agree to the FP32 level, and
+the fused path really replaces the scalar launches."""
 import os
 
 import numpy as np
@@ -19,7 +21,7 @@ def _run(name, b, fused):
     try:
         ctx = groundstate.context_for(system(name))
         ctx.profile_start()
-        x, rep = ctx.solve_response(dev(b), tau=1e-8, strategy="bal", precision="mixed")
+        x, rep = ctx.solve_response(dev(b), tau=1e-8, strategy="grt_exact", precision="mixed")
         prof = ctx.profile_read()
     finally:
         del os.environ["IKR_CG_FUSED"]
