@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     p.add_argument("--strategies", action="store_true",
                    help="also run every tolerance rule once (N_ham, true residual, eta_rel)")
+    p.add_argument("--supercell", default=None, metavar="L1,L2,...",
+                   help="also run the supercell-size study of Remark rmk:scaling on replicas of the "
+                        "10-bohr Gamma-point cell (cfg1) along a_1, e.g. 1,2,4,8")
     p.add_argument("--profile-run", action="store_true",
                    help="only setup, warm-up and the timed steps (for ncu); prints no bench line")
     return p.parse_args()
@@ -155,6 +158,56 @@ def strategy_sweep(ctx, b, nsys, tau, m, precision):
     for name in out:
         out[name]["eta_rel_vs_D10"] = out[name]["eta"] / out["D10"]["eta"]
     return out
+
+
+SUPERCELL_BASE = "cfg1"
+SUPERCELL_BUMP = (0.3, 0.6, 0.45)       # fractional position of dV0 in the base cell
+
+
+def supercell_study(ells, tau, m, precision):
+    """Remark rmk:scaling on the GPU: the base cell repeated ell times along a_1
+    (Gamma point, N_occ, |Omega| and N_g linear in ell), the same localised
+    Gaussian bump dV0 in every supercell, b = chi0 dV0, and every tolerance
+    rule once per size.  Reports N_ham, the true residual ||b - E x|| (tight FP64
+    E) against tau, and the solve time.  The remark predicts that the
+    residual of agr drifts away from tau as ell grows while bal and grt keep
+    to it; grt_exact carries the guarantee of Theorem inexact_gmres_dyson."""
+    import numpy as np
+    import torch
+    from paper_2505_02319_gb300 import groundstate
+    from workloads import make_system, perturbation, supercell
+    base = make_system(SUPERCELL_BASE)
+    center = base.lattice @ np.array(SUPERCELL_BUMP)
+    rows = []
+    for ell in ells:
+        S = supercell(base, ell, kgrid=(1, 1, 1))
+        t0 = time.time()
+        ctx = groundstate.context_for(S, eigensolver="chfsi")
+        torch.cuda.synchronize()
+        setup_s = time.time() - t0
+        nsys = ctx.groundstate_nsys
+        tight = np.full(nsys, 1e-12)
+        dV = torch.tensor(perturbation(S, center=center).ravel(), device="cuda")
+        b, _ = ctx.apply_chi0(dV, tol=tight)
+        b = b.contiguous()
+        row = {"ell": ell, "dims": list(S.dims), "n_occ": nsys, "b_norm": float(torch.linalg.norm(b)),
+               "setup_s": setup_s, "strategies": {}}
+        for name in ("agr", "bal", "grt", "grt_exact", "D10", "D100", "D10n"):
+            torch.cuda.synchronize()
+            t1 = time.time()
+            x, rep = ctx.solve_response(b, tau=tau, m=m, strategy=name, precision=precision)
+            torch.cuda.synchronize()
+            dt = time.time() - t1
+            Ex, _ = ctx.apply_dielectric(x, tol=tight)
+            tr = float(torch.linalg.norm(b - Ex))
+            row["strategies"][name] = {"n_ham": rep[0]["n_ham"], "true_residual": tr,
+                                       "residual_over_tau": tr / tau, "time_s": dt}
+        rows.append(row)
+        ctx.destroy()
+        del ctx
+        torch.cuda.empty_cache()
+    return {"base": SUPERCELL_BASE, "axis": 0, "kpoints": "Gamma", "tau": tau, "m": m,
+            "precision": "fp64" if precision == 0 else "mixed", "rows": rows}
 
 
 # ------------------------------------------------------------------- ours --
@@ -291,6 +344,9 @@ def run_ours(args, rank, world, local_rank):
     }
     if args.strategies:
         out["strategies"] = strategy_sweep(ctx, b, nsys, TAU, M, ikr.MIXED)
+    if args.supercell:
+        out["supercell_study"] = supercell_study([int(v) for v in args.supercell.split(",")], 1e-9, 10,
+                                                 ikr.FP64)
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(s, rep["e_applies"])
         print(json.dumps(out))

@@ -9,7 +9,7 @@ spheres, Fourier transforms, Hamiltonians, eigenpairs, occupations, densities,
 kernels, responses) is computed separately by each side.
 """
 from .systems import (System, make_system, perturbation, response_batch, loss_weights, CONFIGS,
-                      TEST_SYSTEMS, monkhorst_pack, gaussian_sum_on_grid)
+                      TEST_SYSTEMS, monkhorst_pack, gaussian_sum_on_grid, supercell, with_kgrid)
 
 __all__ = ["System", "make_system", "perturbation", "response_batch", "loss_weights", "CONFIGS",
-           "TEST_SYSTEMS", "monkhorst_pack", "gaussian_sum_on_grid"]
+           "TEST_SYSTEMS", "monkhorst_pack", "gaussian_sum_on_grid", "supercell", "with_kgrid"]

@@ -46,6 +46,7 @@ class System:
     kb_centers: np.ndarray = None   # (Nkb, 3) Cartesian [bohr]
     kb_sigma: tuple = None          # (sigma_s, sigma_p)
     kb_D: tuple = None              # (D_s, D_p)
+    kgrid: tuple = (1, 1, 1)        # Monkhorst-Pack counts (l1, l2, l3) behind kpoints
 
     @property
     def volume(self) -> float:
@@ -149,22 +150,73 @@ def make_system(name: str) -> System:
                   width=float(spec["width"]), seed=seed,
                   kb_centers=positions.copy() if kb else None,
                   kb_sigma=tuple(kb["sigma"]) if kb else None,
-                  kb_D=tuple(kb["D"]) if kb else None)
+                  kb_D=tuple(kb["D"]) if kb else None,
+                  kgrid=tuple(spec.get("kgrid", (1, 1, 1))))
+
+
+def with_kgrid(system: System, kgrid) -> System:
+    """The same cell and potential on another Gamma-centred MP k-grid."""
+    kpts, kw = monkhorst_pack(kgrid)
+    name = f"{system.name}_k{'x'.join(str(int(l)) for l in kgrid)}"
+    return dataclasses.replace(system, name=name, kpoints=kpts, kweights=kw,
+                               kgrid=tuple(int(l) for l in kgrid))
+
+
+def supercell(system: System, ell: int, axis: int = 0, kgrid=None) -> System:
+    """The supercell of `ell` replicas of `system` along cell vector `axis`
+    (the construction of Remark rmk:scaling): a_axis -> ell a_axis, N_axis ->
+    ell N_axis, the external potential tiled (it is periodic in the small
+    cell, so tiling is exact), atoms and projector centres replicated at
+    R + j a_axis, and the electron and band counts multiplied by ell.
+
+    k-grid: by default the k-point density is kept, i.e. l_axis -> l_axis/ell,
+    which needs ell to divide l_axis; otherwise pass `kgrid`.  A supercell on
+    grid (l1, l2, l3) describes the same crystal as the small cell on the grid
+    with l_axis replaced by ell * l_axis (band folding, Bloch's theorem).
+    """
+    ell = int(ell)
+    if ell < 1 or axis not in (0, 1, 2):
+        raise ValueError("ell must be >= 1 and axis one of 0, 1, 2")
+    if kgrid is None:
+        kg = list(system.kgrid)
+        if kg[axis] % ell:
+            raise ValueError(f"k-grid {system.kgrid} cannot be folded by {ell} along axis {axis}; pass kgrid")
+        kg[axis] //= ell
+        kgrid = tuple(kg)
+    lattice = system.lattice.copy()
+    a = system.lattice[:, axis].copy()
+    lattice[:, axis] = ell * a
+    dims = list(system.dims)
+    dims[axis] *= ell
+    reps = [1, 1, 1]
+    reps[axis] = ell
+    V = np.tile(system.V, reps)
+
+    def replicate(p):
+        return None if p is None else np.concatenate([p + j * a for j in range(ell)])
+
+    kpts, kw = monkhorst_pack(kgrid)
+    return dataclasses.replace(
+        system, name=f"{system.name}_x{ell}", lattice=lattice, dims=tuple(dims), V=V,
+        kpoints=kpts, kweights=kw, kgrid=tuple(int(l) for l in kgrid),
+        n_electrons=ell * system.n_electrons, nbands=ell * system.nbands,
+        positions=replicate(system.positions), kb_centers=replicate(system.kb_centers))
 
 
 def perturbation(system: System, kind: str = "bump", seed: int = 0,
-                 amplitude: float = 0.1, width: float = 1.0, atom: int = 0, axis: int = 0) -> np.ndarray:
+                 amplitude: float = 0.1, width: float = 1.0, atom: int = 0, axis: int = 0,
+                 center=None) -> np.ndarray:
     """A seeded local perturbation dV0 on the grid.
 
     kind="bump": a periodic Gaussian bump of the given amplitude [Ha] and width
-    [bohr] at a random centre.  kind="displacement": the change of the external
+    [bohr] at a random centre (or at the Cartesian point `center`).  kind="displacement": the change of the external
     potential per unit displacement of pseudo-atom `atom` along Cartesian
     `axis`, i.e. d/dR_axis of -D exp(-|r - R|^2 / (2 sigma^2)) summed over images,
     = -D exp(...) (r - R)_axis / sigma^2 (the perturbation of Sec. 4.1.2, where
     atoms are displaced)."""
     rng = np.random.default_rng(10_000 + seed)
     if kind == "bump":
-        c = system.lattice @ rng.random(3)
+        c = system.lattice @ rng.random(3) if center is None else np.asarray(center, dtype=np.float64)
         return gaussian_sum_on_grid(system.lattice, system.dims, c[None, :], amplitude, width)
     if kind == "displacement":
         lattice, dims = system.lattice, system.dims
@@ -226,6 +278,11 @@ _SPECS = {
     "tiny_insulator": dict(seed=11, cell=(6.0, 6.0, 6.0), dims=(12, 12, 12), Ecut=3.0,
                            layout="random", natoms=2, min_sep=2.5, depth=3.0, width=1.0,
                            n_electrons=4, nbands=4),
+    # tiny_insulator's atoms on a finer grid (64 points per bohr^3 instead of 8),
+    # for the supercell-size study of Remark rmk:scaling
+    "tiny_insulator_fine": dict(seed=11, cell=(6.0, 6.0, 6.0), dims=(24, 24, 24), Ecut=10.0,
+                                layout="random", natoms=2, min_sep=2.5, depth=3.0, width=1.0,
+                                n_electrons=4, nbands=4),
     "tiny_ortho_k": dict(seed=12, cell=(5.0, 6.0, 7.0), dims=(10, 12, 16), Ecut=3.0,
                          layout="random", natoms=2, min_sep=2.5, depth=3.0, width=1.0,
                          n_electrons=4, nbands=4, kgrid=(2, 1, 1)),
