@@ -144,3 +144,29 @@ def test_cg_stays_in_range_of_Q(ins):
     assert np.linalg.norm(b - Q @ A @ Q @ x) < 1e-11
     _, it1, _ = gmres.sternheimer_cg(kb.H, kb.eps[0], Phi, b, 1e3, kb.kinetic, 1.0)
     assert it1 == 1
+
+
+@pytest.mark.parametrize("which", ["ins", "metal"])
+def test_adaptive_strategies_are_more_efficient_than_fixed_ones(which, ins, metal):
+    """The paper's efficiency claim (Sec. 4, Tables summary_*): with the
+    efficiency eta = -log10(||r_end|| / ||r_0||) / N_ham of Sec. 4.1.3, the
+    adaptive rules (agr, bal, grt and the exact prefactor) have eta_rel =
+    eta / eta_D10 > 1 and need fewer Hamiltonian applications than the fixed
+    rule D10, which needs fewer than D100; bal and grt_exact still reach tau."""
+    s, gs = ins if which == "ins" else metal
+    b = response.chi0(gs, perturbation(s))
+    tau, m = 1e-9, 10
+    r0 = float(np.linalg.norm(b))
+    eta, nham = {}, {}
+    for strategy in ("D10", "D100", "agr", "bal", "grt", "grt_exact"):
+        res = gmres.inexact_gmres(gs, b, tau, m, strategy)
+        assert res.converged
+        r_end = _true_residual(gs, b, res.x)
+        if strategy in ("bal", "grt_exact"):
+            assert r_end <= tau
+        eta[strategy] = -np.log10(r_end / r0) / res.nham
+        nham[strategy] = res.nham
+    assert nham["D10"] < nham["D100"]
+    for strategy in ("agr", "bal", "grt", "grt_exact"):
+        assert nham[strategy] < nham["D10"], (strategy, nham)
+        assert eta[strategy] / eta["D10"] > 1.0, (strategy, eta)
