@@ -170,3 +170,23 @@ def test_adaptive_strategies_are_more_efficient_than_fixed_ones(which, ins, meta
     for strategy in ("agr", "bal", "grt", "grt_exact"):
         assert nham[strategy] < nham["D10"], (strategy, nham)
         assert eta[strategy] / eta["D10"] > 1.0, (strategy, eta)
+
+
+@pytest.mark.parametrize("which", ["ins", "metal"])
+def test_kerker_preconditioned_algorithm(which, ins, metal):
+    """Algorithm 1 on T E x = T b (eq. precond_dyson, Kerker T of eq. kerker):
+    with the exact prefactor the preconditioned residual ||T (b - E x)|| is
+    <= tau (reading A10: the guarantee holds for T r, ||T|| = 1), and x solves
+    E x = b to ||T^-1|| tau, ||T^-1|| = 1 / min_{G != 0} |G|^2 / (|G|^2 + alpha^2)."""
+    from oracle import basis
+    s, gs = ins if which == "ins" else metal
+    b = response.chi0(gs, perturbation(s))
+    b /= np.linalg.norm(b)
+    tau, alpha = 1e-9, 0.8
+    res = gmres.inexact_gmres(gs, b, tau, 10, "grt_exact", kerker_alpha=alpha)
+    assert res.converged
+    r = b - response.dielectric(gs, res.x)
+    assert np.linalg.norm(response.kerker(r, s.lattice, s.dims, alpha)) <= tau
+    g2 = np.sort(np.unique(np.round(np.sum(basis.grid_G(s.lattice, s.dims) ** 2, axis=-1).ravel(), 12)))
+    g2min = g2[g2 > 0][0]
+    assert np.linalg.norm(r) <= tau * (g2min + alpha ** 2) / g2min
