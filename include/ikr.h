@@ -188,6 +188,21 @@ ikr_status ikr_set_nonlocal(ikr_ctx* ctx, int ncentres, const double* centres, c
 ikr_status ikr_compute_eigenpairs(ikr_ctx* ctx, int nbands, double tol, int maxit, int degree, double* eigenvalues,
                                   int* iters, double* max_residual, cudaStream_t stream);
 
+/* Schur-complement Sternheimer solves (Sec. 3.4.2 and Sec. 4.1.2, where the
+ * paper uses them in all experiments).  enable = 1: every chi0 application
+ * (ikr_apply_chi0, ikr_apply_dielectric and its adjoint, ikr_solve_response
+ * and its adjoint) solves Q(H_k - eps_n)Q x = b with the extra computed bands
+ * Psi_k = bands N_occ,k + 1 .. nbands of the eigenpairs split off:
+ *   x = Psi a + y,  a = (lambda - eps_n)^-1 Psi^H b,  CG on R(H_k - eps_n)R y = R b,
+ *   R = 1 - [Phi Psi][Phi Psi]^H,
+ * which has the same solution and a larger smallest eigenvalue
+ * (eps_{nbands+1} - eps_n instead of eps_{Nocc+1} - eps_n).  The terms of the
+ * complement in W = R H Psi are dropped: for Rayleigh-Ritz pairs W is the
+ * size of their residual.  enable = 0 restores the plain projected CG.
+ * ikr_solve_sternheimer is not affected.  IKR_ERR_STATE before the eigenpairs
+ * are set (setting new eigenpairs disables it again). */
+ikr_status ikr_set_schur(ikr_ctx* ctx, int enable);
+
 /* Host utility (no GPU): eigenvalues w (ascending, n) and eigenvectors v
  * (column j = eigenvector of w[j]; row-major n x n complex, interleaved) of the
  * Hermitian matrix a (row-major n x n complex, interleaved), by the cyclic

@@ -142,6 +142,15 @@ ikr_status ikr_set_nonlocal(ikr_ctx* c, int ncentres, const double* centres, con
   });
 }
 
+ikr_status ikr_set_schur(ikr_ctx* c, int enable) {
+  if (!c) return IKR_ERR_ARG;
+  return guarded(c, [&] {
+    IKR_REQUIRE(c->have_gs, IKR_ERR_STATE, "the ground state is not set");
+    IKR_REQUIRE(c->xmax >= 1, IKR_ERR_ARG, "no extra computed bands above N_occ,k");
+    c->schur = enable != 0;
+  });
+}
+
 ikr_status ikr_compute_eigenpairs(ikr_ctx* c, int nbands, double tol, int maxit, int degree, double* eigenvalues,
                                   int* iters, double* max_residual, cudaStream_t stream) {
   if (!c) return IKR_ERR_ARG;

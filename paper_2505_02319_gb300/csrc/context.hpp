@@ -102,6 +102,8 @@ struct Workspace {
   // projection coefficients (n x noccmax complex, stored as 2 doubles)
   DBuf<double> cpart;           // per-chunk partial sums of Phi^H Y
   DBuf<double> coef, coefM, coefP;
+  DBuf<double> coefX;           // Psi^H b of the Schur-complement solves (n x xmax complex)
+  DBuf<double> xshift;          // per-system shifts eps_s of the Schur-complement solves
   DBuf<double> dpart;           // per-system partial dot products
   DBuf<double> sys;             // per-system CG scalars (see SysField)
   DBuf<double> val;             // per-system reduced dot products
@@ -239,6 +241,16 @@ struct ikr_ctx {
   ikr::DBuf<int> d_nocc;        // nk
   ikr::DBuf<int> d_occ_kstart;  // == d_phi_off
   ikr::DBuf<double> d_eps_occ, d_f_occ, d_fp_occ, d_w_occ, d_kappa_occ;  // per occupied system
+  // Schur-complement Sternheimer solves (ikr_set_schur): per k-point the occupied
+  // orbitals followed by the extra computed bands Psi_k (nbands - N_occ,k of them),
+  // vector j of k at (roff[k] + j) * ld; Psi_k starts at xoff[k] = roff[k] + N_occ,k.
+  // reps holds the eigenvalue of every stored vector (same index).
+  bool schur = false;
+  int rmax = 0, xmax = 0;
+  ikr::DBuf<double2> d_rset;
+  ikr::DBuf<float2> d_rset32;
+  ikr::DBuf<int> d_roff, d_rcnt, d_xoff, d_xcnt;
+  ikr::DBuf<double> d_reps;
   std::vector<double> h_kappa_occ;
   int* h_pinned = nullptr;      // pinned host scratch: 64 ints, then doubles
   double* h_pinned_d = nullptr;

@@ -124,7 +124,7 @@ CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv
     if (nneed == 0) break;
     // FP32 CG on the current residual (systems already accepted run one
     // iteration and their update is discarded by the mask below)
-    CgStats st = cg_solve<float>(c, L, w.B32.p, w.X32.p, shift, kappa, t32, maxit);
+    CgStats st = sternheimer_solve<float>(c, L, w.B32.p, w.X32.p, shift, kappa, t32, maxit);
     for (int s = 0; s < n; ++s) {
       if (!need[s]) continue;
       out.iters[s] += st.iters[s];

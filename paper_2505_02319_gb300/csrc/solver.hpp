@@ -59,7 +59,12 @@ template <typename R>
 void hamiltonian(ikr_ctx* c, int k, const C_t<R>* psi, C_t<R>* hpsi, int ld, int nvec);
 template <typename R>
 CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, const std::vector<double>& shift,
-                 const std::vector<double>& kappa, const std::vector<double>& tol, int maxit);
+                 const std::vector<double>& kappa, const std::vector<double>& tol, int maxit,
+                 const OrbSet* zset = nullptr);
+// cg_solve, or its Schur-complement form when the context has it enabled (B is then overwritten)
+template <typename R>
+CgStats sternheimer_solve(ikr_ctx* c, const SysList& L, C_t<R>* Bv, C_t<R>* Xv, const std::vector<double>& shift,
+                          const std::vector<double>& kappa, const std::vector<double>& tol, int maxit);
 CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv, const std::vector<double>& shift,
                     const std::vector<double>& kappa, const std::vector<double>& tol, int maxit);
 void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::vector<double>& tol,

@@ -82,6 +82,7 @@ def _load():
         "ikr_set_eigenpairs": (I, [P, ct.POINTER(Eigenpairs), S]),
         "ikr_compute_eigenpairs": (I, [P, I, D, I, I, ct.POINTER(D), ct.POINTER(I), ct.POINTER(D), S]),
         "ikr_set_nonlocal": (I, [P, I, ct.POINTER(D), ct.POINTER(D), ct.POINTER(D), S]),
+        "ikr_set_schur": (I, [P, I]),
         "ikr_hermitian_eigh": (I, [I, ct.POINTER(D), ct.POINTER(D), ct.POINTER(D)]),
         "ikr_num_kpoints": (I, [P]),
         "ikr_basis_size": (I, [P, I, ct.POINTER(I)]),
@@ -197,6 +198,11 @@ class Context:
         sg, sp = _dbl(sigma)
         dd, dp = _dbl(D)
         self._check(_LIB.ikr_set_nonlocal(self._h, len(cen), cp, sp, dp, _stream()))
+
+    def set_schur(self, enable=True):
+        """Schur-complement Sternheimer solves over the extra computed bands
+        (ikr_set_schur): same chi0, better conditioned CG."""
+        self._check(_LIB.ikr_set_schur(self._h, 1 if enable else 0))
 
     def compute_eigenpairs(self, nbands, tol=1e-10, maxit=200, degree=12):
         """Lowest ``nbands`` eigenpairs of every H_k on the GPU (Chebyshev-filtered
