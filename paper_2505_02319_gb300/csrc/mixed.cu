@@ -75,7 +75,7 @@ __global__ void k_residual(const double2* __restrict__ B, const double2* __restr
 }  // namespace
 
 CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv, const std::vector<double>& shift,
-                    const std::vector<double>& kappa, const std::vector<double>& tol, int maxit) {
+                    const std::vector<double>& kappa, const std::vector<double>& tol, int maxit, bool schur) {
   const int n = L.n;
   CgStats out;
   out.fp32 = true;
@@ -124,7 +124,8 @@ CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv
     if (nneed == 0) break;
     // FP32 CG on the current residual (systems already accepted run one
     // iteration and their update is discarded by the mask below)
-    CgStats st = sternheimer_solve<float>(c, L, w.B32.p, w.X32.p, shift, kappa, t32, maxit);
+    CgStats st = schur ? sternheimer_solve<float>(c, L, w.B32.p, w.X32.p, shift, kappa, t32, maxit)
+                       : cg_solve<float>(c, L, w.B32.p, w.X32.p, shift, kappa, t32, maxit);
     for (int s = 0; s < n; ++s) {
       if (!need[s]) continue;
       out.iters[s] += st.iters[s];

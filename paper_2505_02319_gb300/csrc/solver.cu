@@ -302,7 +302,7 @@ void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::
   proj_apply<double>(c, L, M, w.Y.p, -1.0, 1.0, w.B.p, ld, nullptr, nullptr, nullptr);
   CgStats st;
   if (precision == IKR_MIXED) {
-    st = mixed_solve(c, L, w.B.p, w.X.p, shift, kappa, tol, maxit);
+    st = mixed_solve(c, L, w.B.p, w.X.p, shift, kappa, tol, maxit, true);
   } else {
     st = sternheimer_solve<double>(c, L, w.B.p, w.X.p, shift, kappa, tol, maxit);
   }

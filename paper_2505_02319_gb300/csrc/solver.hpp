@@ -65,8 +65,11 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
 template <typename R>
 CgStats sternheimer_solve(ikr_ctx* c, const SysList& L, C_t<R>* Bv, C_t<R>* Xv, const std::vector<double>& shift,
                           const std::vector<double>& kappa, const std::vector<double>& tol, int maxit);
+// schur: the FP32 solves take the Schur-complement form when the context has it
+// enabled (only for occupied systems, whose shifts lie below the extra bands)
 CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv, const std::vector<double>& shift,
-                    const std::vector<double>& kappa, const std::vector<double>& tol, int maxit);
+                    const std::vector<double>& kappa, const std::vector<double>& tol, int maxit,
+                    bool schur = false);
 void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::vector<double>& tol,
                int maxit, int precision, double* drho, RunStats& rs, bool fp32 = false);
 void dielectric_core(ikr_ctx* c, const double* v, double* Ev, const TolFn& tol_fn, int maxit, int precision,
