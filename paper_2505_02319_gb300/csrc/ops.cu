@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) k_proj_partial_w(const typename io<R>::cx
   if (ns == 0) return;
   const int nocc = nocc_k[k], nb = nb_k[k];
   const int g0 = chunk * kPC;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* ph = reinterpret_cast<C*>(smem_raw);           // [g][m], kPC x nocc
   C* ys = ph + kPC * nocc;                          // per warp kPC entries
   const typename io<R>::cx* phi = phi_all + (size_t)phi_off[k] * ld;
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256) k_proj_apply_w(const typename io<R>::cx* 
       for (int sl = threadIdx.x; sl < ns; sl += blockDim.x) dpart[(size_t)(kstart[k] + sl) * nparts + chunk] = 0.0;
     return;
   }
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* ph = reinterpret_cast<C*>(smem_raw);           // [m][g]
   C* cwall = ph + kPC * nocc;                       // per warp: the coefficients of its system
   const typename io<R>::cx* phi = phi_all + (size_t)phi_off[k] * ld;
