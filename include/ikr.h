@@ -287,8 +287,14 @@ ikr_status ikr_apply_dielectric(ikr_ctx* ctx, const double* v, double* Ev, const
  * to ||b - E x|| <= tau, choosing every CG tolerance by opts->strategy
  * (Theorem inexact_gmres_dyson, Table strategies).  With kerker_alpha > 0 the
  * left-preconditioned system T E x = T b (eq. precond_dyson) is solved.
- * b, x: DEVICE, nrhs x Ng doubles (right-hand sides solved one after another);
- * x holds x0 on input if opts->use_x0.  report: host array of nrhs (may be NULL).
+ * b, x: DEVICE, nrhs x Ng doubles; x holds x0 on input if opts->use_x0.
+ * report: host array of nrhs (may be NULL).
+ * nrhs > 1: the right-hand sides advance in lockstep, each with its own GMRES
+ * state and tolerances; the E applications of one round share one batched CG
+ * over all their Sternheimer systems, and their right-hand-side and density
+ * passes are FP64-accurate (the FP32 E applications of late steps are not
+ * used).  Each solution meets its own tau.  The environment variable
+ * IKR_BATCH=0 solves them one after another instead.
  * Returns IKR_ERR_NOCONV (best iterate in x) if max_restarts is exceeded. */
 ikr_status ikr_solve_response(ikr_ctx* ctx, int nrhs, const double* b, double* x,
                               const ikr_solve_opts* opts, ikr_report* report,

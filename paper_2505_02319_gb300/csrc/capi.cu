@@ -1,5 +1,6 @@
 // extern "C" entry points (include/ikr.h).  Each wraps the C++ implementation,
 // turns exceptions into status codes and records the message in the context.
+#include <cstdlib>
 #include <cstring>
 #include <chrono>
 #include <cmath>
@@ -71,6 +72,17 @@ ikr_status solve_any(ikr_ctx* c, int nrhs, const double* b, double* x, const ikr
     IKR_REQUIRE(o.strategy >= IKR_AGR && o.strategy <= IKR_FIXED, IKR_ERR_ARG, "unknown strategy");
     IKR_REQUIRE(o.precision == IKR_FP64 || o.precision == IKR_MIXED, IKR_ERR_ARG, "unknown precision");
     IKR_REQUIRE(o.cg_maxit >= 1, IKR_ERR_ARG, "cg_maxit must be >= 1");
+    const char* env = std::getenv("IKR_BATCH");
+    if (nrhs > 1 && !(env && env[0] == '0')) {
+      try {
+        gmres_solve_batch(c, nrhs, b, x, o, report, adjoint);
+      } catch (const Error& e) {
+        if (e.status != IKR_ERR_NOCONV && e.status != IKR_ERR_TIMEOUT) throw;
+        c->err = e.what();
+        worst = e.status;
+      }
+      return;
+    }
     for (int r = 0; r < nrhs; ++r) {
       ikr_report* rep = report ? report + r : nullptr;
       try {

@@ -118,6 +118,11 @@ struct Workspace {
   DBuf<double> scal;            // a few device scalars
   DBuf<double> gm_V;            // GMRES basis (m+1) x Ng
   DBuf<double> gm_h;            // Arnoldi coefficients and partials
+  // lockstep right-hand sides (batch.cu): per item the potential, density and
+  // norms, the right-hand sides and solutions of its systems, Phi^H Y, the
+  // dphi^P coefficients and deps; per right-hand side the Krylov basis and three vectors
+  DBuf<double> bu, bdrho, bnrm, bM, bCP, bdeps, bgm;
+  DBuf<double2> bB, bX;
 };
 
 // offsets into the per-system scalar block (nsys doubles each)
@@ -246,6 +251,11 @@ struct ikr_ctx {
   // vector j of k at (roff[k] + j) * ld; Psi_k starts at xoff[k] = roff[k] + N_occ,k.
   // reps holds the eigenvalue of every stored vector (same index).
   bool schur = false;
+  // system list of the batched CG over `batch_items` E applications (batch.cu),
+  // and the position of each of its systems in the per-item blocks
+  int batch_items = -1;
+  ikr::SysList batch_list;
+  ikr::DBuf<int> d_batch_map;
   int rmax = 0, xmax = 0;
   ikr::DBuf<double2> d_rset;
   ikr::DBuf<float2> d_rset32;

@@ -82,6 +82,7 @@ CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv
   out.iters.assign(n, 0);
   out.status.assign(n, 1);
   out.res.assign(n, 0.0);
+  out.checks.assign(n, 0);
   if (n == 0) return out;
   ensure_workspace(c, n);
   ensure_pinned(c, n);
@@ -179,6 +180,7 @@ CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv
       if (check[s]) {
         out.n_ham += 1;
         out.n_ham_fp64 += 1;
+        out.checks[s] += 1;
       }
     sys_norms(w.R.p, act, check.data(), rnorm);
     for (int s = 0; s < n; ++s)

@@ -29,6 +29,7 @@ void herm_jacobi(int n, std::vector<std::complex<double>>& A, std::vector<double
 
 struct CgStats {
   std::vector<int> iters, status;   // status: 1 converged, 2 numeric, 3 iteration cap
+  std::vector<int> checks;          // FP64 residual applications per system (mixed solves)
   std::vector<double> res;          // final recursive residual norms
   long long n_ham = 0, n_ham_fp64 = 0;
   int max_iters = 0, noconv = 0, numeric = 0;
@@ -81,5 +82,9 @@ void dielectric_adjoint_core(ikr_ctx* c, const double* v, double* Ev, const TolF
                              int precision, RunStats& rs, double allowed = 0.0);
 void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o, ikr_report* rep,
                  bool adjoint = false);
+// Algorithm 1 for nrhs right-hand sides in lockstep, the E applications of a
+// round batched into one CG (batch.cu); reps: nrhs reports or NULL
+void gmres_solve_batch(ikr_ctx* c, int nrhs, const double* b, double* x, const ikr_solve_opts& o,
+                       ikr_report* reps, bool adjoint = false);
 
 }  // namespace ikr
