@@ -199,41 +199,6 @@ void dielectric_batch(ikr_ctx* c, std::vector<BatchItem>& items, int maxit, int 
 
 namespace {
 
-// smallest singular value of the m x n column-major matrix a (m >= n), by
-// one-sided Jacobi rotations (Hestenes), as the single right-hand-side solver
-double sigma_min_b(std::vector<double> a, int m, int n) {
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        double al = 0, be = 0, ga = 0;
-        for (int r = 0; r < m; ++r) {
-          al += a[p * m + r] * a[p * m + r];
-          be += a[q * m + r] * a[q * m + r];
-          ga += a[p * m + r] * a[q * m + r];
-        }
-        if (ga == 0.0 || std::fabs(ga) <= 1e-17 * std::sqrt(al * be)) continue;
-        off = std::max(off, std::fabs(ga) / std::sqrt(al * be));
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = cs * t;
-        for (int r = 0; r < m; ++r) {
-          const double up = a[p * m + r], uq = a[q * m + r];
-          a[p * m + r] = cs * up - sn * uq;
-          a[q * m + r] = sn * up + cs * uq;
-        }
-      }
-    if (off < 1e-15) break;
-  }
-  double smin = 1e300;
-  for (int p = 0; p < n; ++p) {
-    double s = 0;
-    for (int r = 0; r < m; ++r) s += a[p * m + r] * a[p * m + r];
-    smin = std::min(smin, std::sqrt(s));
-  }
-  return smin;
-}
-
 enum Phase { kStart, kResidual, kStep, kDone };
 
 struct Rhs {
@@ -369,7 +334,7 @@ void gmres_solve_batch(ikr_ctx* c, int nrhs, const double* b, double* x, const i
     std::vector<double> Hs((size_t)(i + 1) * i);
     for (int a = 0; a < i; ++a)
       for (int r = 0; r <= i; ++r) Hs[(size_t)a * (i + 1) + r] = q.Hraw[(size_t)a * (m + 1) + r];
-    const double sig = sigma_min_b(Hs, i + 1, i);
+    const double sig = sigma_min(Hs, i + 1, i);
     std::vector<double> y(i);
     for (int r = i - 1; r >= 0; --r) {
       double a = q.g[r];

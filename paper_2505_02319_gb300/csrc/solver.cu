@@ -386,8 +386,6 @@ void dielectric_adjoint_core(ikr_ctx* c, const double* v, double* Ev, const TolF
 
 // ---------------------------------------------------------- Algorithm 1 --
 
-namespace {
-
 // smallest singular value of the m x n (m >= n) column-major matrix a by
 // one-sided Jacobi rotations (Hestenes).
 double sigma_min(std::vector<double> a, int m, int n) {
@@ -423,7 +421,6 @@ double sigma_min(std::vector<double> a, int m, int n) {
   return smin;
 }
 
-}  // namespace
 
 std::vector<double> strategy_tolerances(ikr_ctx* c, const ikr_solve_opts& o, int i, double s, double rprev,
                                         double kv_norm, double b_norm) {

@@ -75,6 +75,8 @@ void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::
                int maxit, int precision, double* drho, RunStats& rs, bool fp32 = false);
 void dielectric_core(ikr_ctx* c, const double* v, double* Ev, const TolFn& tol_fn, int maxit, int precision,
                      RunStats& rs, double allowed = 0.0);
+// smallest singular value of the m x n column-major matrix a (m >= n)
+double sigma_min(std::vector<double> a, int m, int n);
 std::vector<double> strategy_tolerances(ikr_ctx* c, const ikr_solve_opts& o, int i, double s, double rprev,
                                         double kv_norm, double b_norm);
 void hamiltonian_noalloc(ikr_ctx* c, int k, const double2* psi, double2* hpsi, int nvec);
