@@ -203,6 +203,26 @@ ikr_status ikr_compute_eigenpairs(ikr_ctx* ctx, int nbands, double tol, int maxi
  * are set (setting new eigenpairs disables it again). */
 ikr_status ikr_set_schur(ikr_ctx* ctx, int enable);
 
+/* The FP32 coefficient products V_k^H Y of the projections (eq.
+ * discretised_sternheimer: M = Phi^H Y, and the Q-projection of every FP32 CG
+ * iteration) on the 5th-generation tensor cores: tcgen05 MMAs of kind::tf32
+ * with each operand split into a TF32 high part and the remainder (three
+ * products, FP32 accumulation in tensor memory), split-K over thread blocks,
+ * fixed-order reduction of the chunk partials.  enable = 0 returns to the
+ * CUDA-core kernels.  IKR_ERR_STATE before the eigenpairs are set.  A
+ * tensor-core launch whose internal wait runs out makes the calling solve
+ * return IKR_ERR_TIMEOUT. */
+ikr_status ikr_set_tensor_cores(ikr_ctx* ctx, int enable);
+
+/* c[s][m] = <phi_m,k, y_s> for the occupied orbitals of k-point k (the
+ * coefficient product of eq. discretised_sternheimer, M = Phi_k^H Y) in FP32
+ * arithmetic: method 0 on the CUDA cores, 1 on the tensor cores (as
+ * ikr_set_tensor_cores).  y: DEVICE, Nb_k x nvec complex64, column-major
+ * (vector s at s * Nb_k); c: HOST, nvec x N_occ,k complex128 (row s).
+ * IKR_ERR_ARG for a bad k, nvec < 1 or NULL pointers; IKR_ERR_TIMEOUT as above. */
+ikr_status ikr_projection_coefficients(ikr_ctx* ctx, int k, int nvec, const void* y, int method, double* c,
+                                       cudaStream_t stream);
+
 /* Host utility (no GPU): eigenvalues w (ascending, n) and eigenvectors v
  * (column j = eigenvector of w[j]; row-major n x n complex, interleaved) of the
  * Hermitian matrix a (row-major n x n complex, interleaved), by the cyclic

@@ -214,6 +214,11 @@ int proj_chunks32() { return kPG; }
 
 void proj_coef32(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef,
                  const OrbSet& set) {
+  if (tc_proj_ok(c, set)) {
+    const int ntot = (set.phi32 == c->d_phi_all32.p) ? c->occ.n : c->rset_total;
+    proj_coef_tc(c, L, Y, ldy, active, coef, set, ntot);
+    return;
+  }
   const int nch = (c->ld + kKG - 1) / kKG;
   const int nm = set.maxcnt;
   c->ws.cpart.reserve((size_t)nch * L.n * nm * 2);

@@ -188,6 +188,7 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
   }
   IKR_CUDA(cudaMemcpyAsync(hs.data(), sys, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, strm));
   IKR_CUDA(cudaStreamSynchronize(strm));
+  if (c->tc_proj) tc_check(c);
   for (int s = 0; s < n; ++s) {
     st.iters[s] = (int)hs[kSysIters * n + s];
     int code = (int)hs[kSysStatus * n + s];

@@ -1,0 +1,349 @@
+// Tensor-core projection coefficients (5th-generation tensor cores: tcgen05.mma
+// kind::tf32, accumulators in tensor memory):
+//   C[s][m] = <v_m, y_s> = sum_G conj(V_k[m][G]) y_s[G]
+// for the systems s of each k-point and the vectors v_m of an orbital set
+// (Phi_k, or [Phi_k Psi_k] for the Schur-complement solves): the M = Phi^H Y of
+// eq. discretised_sternheimer and the Q-projection of the CG, in FP32.
+//
+// Real form.  With y and v stored as interleaved (re, im) floats, a complex
+// inner product is two real ones over 2 Nb_k reals:
+//   Re C = <v_il, y_il>,   Im C = <v'_il, y_il>,   v' = (-Im v, Re v),
+// so D = A B^T with A = [v_0; v'_0; v_1; v'_1; ...] (2 n_k rows, fixed by the
+// ground state, prepared once) and B = the systems' vectors (K-major both):
+// C[s][m] = D[2m][s] + i D[2m+1][s].
+//
+// Precision.  kind::tf32 multiplies the upper 19 bits of each float.  Each
+// operand is split x = hi + lo with hi = x with its low 13 mantissa bits
+// cleared (exact) and lo = x - hi (exact), and D accumulates
+// A_hi B_hi + A_hi B_lo + A_lo B_hi: products to about 2^-20 relative, FP32
+// accumulation, as the CUDA-core kernels.
+//
+// Tiling.  One CTA (one warpgroup) owns 128 rows of A, NT systems and a
+// split-K chunk of kTC reals; stages of kTK = 32 reals are written to shared
+// memory in the canonical no-swizzle K-major layout (8 x 16-byte core
+// matrices, 128 bytes apart along K, 8-row groups 1024 bytes apart), one
+// thread issues 4 x 3 MMAs (M = 128, N = NT, K = 8 each) and commits them to
+// an mbarrier that all threads wait on (bounded) before the next stage.  The
+// 128 x NT FP32 partial tile is read back with tcgen05.ld (warp w: lanes
+// 32w..32w+31), even/odd rows paired into (re, im), and written as per-chunk
+// partials that a second kernel adds in fixed chunk order (deterministic).
+#include <cstdint>
+
+#include "ops.hpp"
+
+namespace ikr {
+
+namespace {
+
+constexpr int kTM = 128;     // A rows per tile (64 vectors: re and im rows)
+constexpr int kTK = 32;      // reals of K per stage (16 plane waves)
+constexpr int kTC = 1024;    // reals of K per split-K chunk (512 plane waves)
+constexpr int kTileBytes = kTM * kTK * 4;   // one A tile (16 KB)
+constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz: bound of every mbarrier wait
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of the 16-byte group c4 (reals 4 c4 .. 4 c4 + 3) of row r in a
+// kTK-wide tile: canonical K-major layout without swizzle
+__device__ __forceinline__ int core_off(int r, int c4) { return (r >> 3) * 1024 + c4 * 128 + (r & 7) * 16; }
+
+// shared-memory matrix descriptor: start address, leading (K) byte offset 128,
+// stride (8-row group) byte offset 1024, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         (1ull << 46);
+}
+
+// instruction descriptor: D F32, A and B TF32, both K-major, N = n, M = 128
+__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// waits for the phase with the given parity; false after ~1 s
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// whole warp: allocate ncols tensor-memory columns, address to *slot
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// 32 consecutive columns of this thread's lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+}  // namespace
+
+// A rows of the orbital set: row 2v = v (interleaved), row 2v + 1 = v' = (-Im v, Re v),
+// split into hi and lo; rows of 2 ld reals
+__global__ void k_tc_rows(const float2* __restrict__ phi, int nvec, int ld, float* __restrict__ ahi,
+                          float* __restrict__ alo) {
+  const size_t n = (size_t)nvec * ld;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t v = e / ld, g = e - v * ld;
+    const float2 p = phi[e];
+    const float a[4] = {p.x, p.y, -p.y, p.x};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const size_t o = (2 * v + (q >> 1)) * (size_t)(2 * ld) + 2 * g + (q & 1);
+      const float h = tf32_hi(a[q]);
+      ahi[o] = h;
+      alo[o] = a[q] - h;
+    }
+  }
+}
+
+// Partial sums of D = A B^T over one split-K chunk: part[(s * maxcnt + m) * nch + chunk] = (Re, Im) C[s][m].
+// grid: (chunks, k-points, A-tiles x system tiles); NT systems per tile.
+template <int NT>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_coef(const float* __restrict__ ahi, const float* __restrict__ alo, const int* __restrict__ set_off,
+              const int* __restrict__ set_cnt, const int* __restrict__ nb_k, const int* __restrict__ kstart,
+              const int* __restrict__ kcount, const float2* __restrict__ Y, int ldy, int ld, int nmt, int nch,
+              int maxcnt, const int* __restrict__ active, double2* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* sAhi = sm;
+  unsigned char* sAlo = sm + kTileBytes;
+  unsigned char* sBhi = sm + 2 * kTileBytes;
+  unsigned char* sBlo = sBhi + NT * kTK * 4;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sBlo + NT * kTK * 4);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int k = blockIdx.y, chunk = blockIdx.x;
+  const int tm = blockIdx.z % nmt, tn = blockIdx.z / nmt;
+  const int cnt = set_cnt[k], nb = nb_k[k], ns = kcount[k];
+  const int i0 = tm * kTM, s0 = tn * NT;
+  const int k0 = chunk * kTC, k1 = min(k0 + kTC, 2 * nb);
+  if (i0 >= 2 * cnt || s0 >= ns || k0 >= k1) return;   // uniform over the block
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr uint32_t kCols = NT < 32 ? 32 : NT;
+  if (warp == 0) tmem_alloc(slot, kCols);
+  if (tid == 0) mbar_init(bar, 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const size_t arow0 = 2 * (size_t)set_off[k] + i0;    // first A row of the tile
+  const size_t lda = 2 * (size_t)ld;                    // reals per A row
+  const int sbase = kstart[k] + s0;
+  bool ok = true;
+  uint32_t phase = 0;
+  uint32_t acc = 0;
+  for (int kb = k0; kb < k1 && ok; kb += kTK) {
+    // A tiles: 128 rows x 8 groups of 4 reals; rows past 2 cnt are zero
+    for (int e = tid; e < kTM * (kTK / 4); e += 128) {
+      const int r = e >> 3, c4 = e & 7;
+      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+      if (i0 + r < 2 * cnt && kb + 4 * c4 < k1) {
+        const size_t o = (arow0 + r) * lda + kb + 4 * c4;
+        h = *reinterpret_cast<const float4*>(ahi + o);
+        l = *reinterpret_cast<const float4*>(alo + o);
+      }
+      *reinterpret_cast<float4*>(sAhi + core_off(r, c4)) = h;
+      *reinterpret_cast<float4*>(sAlo + core_off(r, c4)) = l;
+    }
+    // B tiles: NT systems, split on the fly; reals past 2 Nb_k and inactive systems are zero
+    for (int e = tid; e < NT * (kTK / 4); e += 128) {
+      const int r = e >> 3, c4 = e & 7;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int s = sbase + r;
+      const int re = kb + 4 * c4;                       // first real of the group (two plane waves)
+      if (s0 + r < ns && (!active || active[s]) && re < k1) {
+        x = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Y + (size_t)s * ldy) + re);
+        if (re + 2 >= k1) x.z = x.w = 0.f;              // second plane wave past Nb_k
+      }
+      const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+      *reinterpret_cast<float4*>(sBhi + core_off(r, c4)) = h;
+      *reinterpret_cast<float4*>(sBlo + core_off(r, c4)) =
+          make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      constexpr uint32_t id = idesc_tf32(NT);
+#pragma unroll
+      for (int kk = 0; kk < kTK / 8; ++kk) {
+        const uint32_t off = kk * 256;                  // two 16-byte groups along K per MMA
+        const uint64_t ah = sdesc(saddr(sAhi) + off), al = sdesc(saddr(sAlo) + off);
+        const uint64_t bh = sdesc(saddr(sBhi) + off), bl = sdesc(saddr(sBlo) + off);
+        mma_tf32(tmem, ah, bh, id, acc);
+        mma_tf32(tmem, ah, bl, id, 1);
+        mma_tf32(tmem, al, bh, id, 1);
+        acc = 1;
+      }
+      mma_commit(bar);
+    }
+    // the MMAs read this stage's shared memory: wait before it is rewritten; the
+    // outcome is made uniform so that no thread leaves the loop alone
+    ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
+    phase ^= 1;
+    tc_fence_after();
+  }
+  if (!ok) {
+    if (lane == 0) atomicExch(err, 1);
+  } else {
+    // epilogue: lanes 32 w .. 32 w + 31 of tensor memory are rows i0 + 32 w + lane of D
+    const int r = 32 * warp + lane;
+    const int i = i0 + r, m = i >> 1;
+    float v[32];
+#pragma unroll 1
+    for (int c0 = 0; c0 < NT; c0 += 32) {
+      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float im = __shfl_xor_sync(0xffffffffu, v[j], 1);
+        const int sl = s0 + c0 + j;
+        const int s = kstart[k] + sl;
+        if (!(lane & 1) && i < 2 * cnt && sl < ns && (!active || active[s]))
+          part[((size_t)s * maxcnt + m) * nch + chunk] = make_double2((double)v[j], (double)im);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kCols);
+  }
+}
+
+// coef[s][m] = sum of the chunk partials in chunk order: a warp per coefficient
+__global__ void k_tc_reduce(const double2* __restrict__ part, int nsys, int maxcnt, int nch,
+                            const int* __restrict__ sys_k, const int* __restrict__ set_cnt,
+                            const int* __restrict__ nb_k, const int* __restrict__ active, double2* __restrict__ coef) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (long long)nsys * maxcnt) return;
+  const int s = (int)(w / maxcnt), m = (int)(w - (long long)s * maxcnt);
+  if (active && !active[s]) return;
+  const int k = sys_k[s];
+  if (m >= set_cnt[k]) return;
+  const int nc = (2 * nb_k[k] + kTC - 1) / kTC;
+  const double2* p = part + ((size_t)s * maxcnt + m) * nch;
+  double ax = 0.0, ay = 0.0;
+  for (int cc = lane; cc < nc; cc += 32) {
+    const double2 v = p[cc];
+    ax += v.x;
+    ay += v.y;
+  }
+  ax = warp_sum(ax);
+  ay = warp_sum(ay);
+  if (lane == 0) coef[w] = make_double2(ax, ay);
+}
+
+// ----------------------------------------------------------------- host --
+
+// The A rows of an orbital set (prepared once per set and ground state).
+static void tc_prepare(ikr_ctx* c, const OrbSet& set, int nvec_total) {
+  TcRows& t = (set.phi32 == c->d_phi_all32.p && set.off == c->d_phi_off.p) ? c->tc_occ : c->tc_rset;
+  if (t.ready && t.src == set.phi32) return;
+  const size_t n = (size_t)2 * nvec_total * 2 * c->ld;
+  t.hi.reserve(n);
+  t.lo.reserve(n);
+  const size_t work = (size_t)nvec_total * c->ld;
+  const int blocks = (int)std::min<size_t>((work + 255) / 256, (size_t)c->nsm * 16);
+  k_tc_rows<<<blocks, 256, 0, c->stream>>>(set.phi32, nvec_total, c->ld, t.hi.p, t.lo.p);
+  IKR_CUDA(cudaGetLastError());
+  t.ready = true;
+  t.src = set.phi32;
+}
+
+static const TcRows& tc_rows_of(ikr_ctx* c, const OrbSet& set) {
+  return (set.phi32 == c->d_phi_all32.p && set.off == c->d_phi_off.p) ? c->tc_occ : c->tc_rset;
+}
+
+bool tc_proj_ok(ikr_ctx* c, const OrbSet& set) {
+  return c->tc_proj && set.maxcnt >= 1 && (c->ld % 2) == 0;
+}
+
+void proj_coef_tc(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef,
+                  const OrbSet& set, int nvec_total) {
+  IKR_REQUIRE(ldy % 2 == 0, IKR_ERR_ARG, "tensor-core projections need an even vector stride");
+  tc_prepare(c, set, nvec_total);
+  const TcRows& t = tc_rows_of(c, set);
+  int maxns = 0, maxnb = 0;
+  for (int v : L.kcount) maxns = std::max(maxns, v);
+  for (auto& K : c->k) maxnb = std::max(maxnb, K.nb);
+  const int nch = (2 * maxnb + kTC - 1) / kTC;
+  const int nmt = (2 * set.maxcnt + kTM - 1) / kTM;
+  const int nt = maxns <= 32 ? 32 : (maxns <= 64 ? 64 : 128);
+  const int nnt = (maxns + nt - 1) / nt;
+  c->ws.cpart.reserve((size_t)nch * L.n * set.maxcnt * 2);
+  double2* part = reinterpret_cast<double2*>(c->ws.cpart.p);
+  c->tc_err.reserve(1);
+  IKR_CUDA(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+  dim3 grid(nch, (unsigned)c->k.size(), (unsigned)(nmt * std::max(nnt, 1)));
+  const size_t smem = 2 * kTileBytes + 2 * (size_t)nt * kTK * 4 + 64;
+  auto launch = [&](auto kern) {
+    IKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, 128, smem, c->stream>>>(t.hi.p, t.lo.p, set.off, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p, Y,
+                                         ldy, c->ld, nmt, nch, set.maxcnt, active, part, c->tc_err.p);
+  };
+  if (nt == 32) launch(k_tc_coef<32>);
+  else if (nt == 64) launch(k_tc_coef<64>);
+  else launch(k_tc_coef<128>);
+  IKR_CUDA(cudaGetLastError());
+  const long long threads = 32LL * L.n * set.maxcnt;
+  k_tc_reduce<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(part, L.n, set.maxcnt, nch, L.d_k.p,
+                                                                         set.cnt, c->d_nb.p, active, coef);
+  IKR_CUDA(cudaGetLastError());
+}
+
+void tc_check(ikr_ctx* c) {
+  if (!c->tc_err.p) return;
+  int e = 0;
+  IKR_CUDA(cudaMemcpyAsync(&e, c->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  IKR_CUDA(cudaStreamSynchronize(c->stream));
+  IKR_REQUIRE(e == 0, IKR_ERR_TIMEOUT, "tensor-core projection: an mbarrier wait ran out");
+}
+
+}  // namespace ikr
