@@ -251,12 +251,20 @@ class InexactResult:
 
 
 def inexact_gmres(gs, b, tau, m, strategy, x0=None, s=1.0, kxc=None,
-                  max_restarts=20, track_errors=False):
-    """Algorithm 1 with CG-solved Sternheimer equations (emulation on the CPU)."""
+                  max_restarts=20, track_errors=False, kerker_alpha=0.0):
+    """Algorithm 1 with CG-solved Sternheimer equations (emulation on the CPU).
+
+    kerker_alpha > 0: Algorithm 1 on the left-preconditioned system T E x = T b
+    of eq. precond_dyson with the Kerker T of eq. kerker; the tolerance rules
+    are unchanged (||T|| = 1, Lemma kerker_properties), the stopping rule and
+    the reported residuals are those of T r, and b_norm stays ||b||."""
     if kxc is None:
         kxc = response.exchange_kernel(gs.rho)
     shape = b.shape
     b_norm = float(np.linalg.norm(b))
+
+    def T(v):
+        return response.kerker(v, gs.lattice, gs.dims, kerker_alpha) if kerker_alpha > 0 else v
     x0 = np.zeros_like(b) if x0 is None else x0.copy()
     est, sig = [], []
     nham = 0
@@ -271,10 +279,10 @@ def inexact_gmres(gs, b, tau, m, strategy, x0=None, s=1.0, kxc=None,
             Ex0, nh = dielectric_inexact(gs, x0, tol0, kxc)
             nham += nh
             if track_errors:
-                err0 = float(np.linalg.norm(Ex0 - response.dielectric(gs, x0, kxc)))
-            r0 = b - Ex0
+                err0 = float(np.linalg.norm(T(Ex0 - response.dielectric(gs, x0, kxc))))
+            r0 = T(b - Ex0)
         else:
-            r0 = b.copy()
+            r0 = T(b)
         beta = float(np.linalg.norm(r0))
         V = [r0.ravel() / beta]
         H = np.zeros((m + 1, m))
@@ -290,8 +298,8 @@ def inexact_gmres(gs, b, tau, m, strategy, x0=None, s=1.0, kxc=None,
             steps += 1
             if track_errors:
                 errs.append(float(np.linalg.norm(
-                    w - response.dielectric(gs, V[-1].reshape(shape), kxc))))
-            w = w.ravel()
+                    T(w - response.dielectric(gs, V[-1].reshape(shape), kxc)))))
+            w = T(w).ravel()
             for j in range(i):                       # MGS Arnoldi
                 H[j, i - 1] = V[j] @ w
                 w = w - H[j, i - 1] * V[j]

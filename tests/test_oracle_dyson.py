@@ -144,3 +144,49 @@ def test_cg_stays_in_range_of_Q(ins):
     assert np.linalg.norm(b - Q @ A @ Q @ x) < 1e-11
     _, it1, _ = gmres.sternheimer_cg(kb.H, kb.eps[0], Phi, b, 1e3, kb.kinetic, 1.0)
     assert it1 == 1
+
+
+@pytest.mark.parametrize("which", ["ins", "metal"])
+def test_adaptive_strategies_are_more_efficient_than_fixed_ones(which, ins, metal):
+    """The paper's efficiency claim (Sec. 4, Tables summary_*): with the
+    efficiency eta = -log10(||r_end|| / ||r_0||) / N_ham of Sec. 4.1.3, the
+    adaptive rules (agr, bal, grt and the exact prefactor) have eta_rel =
+    eta / eta_D10 > 1 and need fewer Hamiltonian applications than the fixed
+    rule D10, which needs fewer than D100; bal and grt_exact still reach tau."""
+    s, gs = ins if which == "ins" else metal
+    b = response.chi0(gs, perturbation(s))
+    tau, m = 1e-9, 10
+    r0 = float(np.linalg.norm(b))
+    eta, nham = {}, {}
+    for strategy in ("D10", "D100", "agr", "bal", "grt", "grt_exact"):
+        res = gmres.inexact_gmres(gs, b, tau, m, strategy)
+        assert res.converged
+        r_end = _true_residual(gs, b, res.x)
+        if strategy in ("bal", "grt_exact"):
+            assert r_end <= tau
+        eta[strategy] = -np.log10(r_end / r0) / res.nham
+        nham[strategy] = res.nham
+    assert nham["D10"] < nham["D100"]
+    for strategy in ("agr", "bal", "grt", "grt_exact"):
+        assert nham[strategy] < nham["D10"], (strategy, nham)
+        assert eta[strategy] / eta["D10"] > 1.0, (strategy, eta)
+
+
+@pytest.mark.parametrize("which", ["ins", "metal"])
+def test_kerker_preconditioned_algorithm(which, ins, metal):
+    """Algorithm 1 on T E x = T b (eq. precond_dyson, Kerker T of eq. kerker):
+    with the exact prefactor the preconditioned residual ||T (b - E x)|| is
+    <= tau (reading A10: the guarantee holds for T r, ||T|| = 1), and x solves
+    E x = b to ||T^-1|| tau, ||T^-1|| = 1 / min_{G != 0} |G|^2 / (|G|^2 + alpha^2)."""
+    from oracle import basis
+    s, gs = ins if which == "ins" else metal
+    b = response.chi0(gs, perturbation(s))
+    b /= np.linalg.norm(b)
+    tau, alpha = 1e-9, 0.8
+    res = gmres.inexact_gmres(gs, b, tau, 10, "grt_exact", kerker_alpha=alpha)
+    assert res.converged
+    r = b - response.dielectric(gs, res.x)
+    assert np.linalg.norm(response.kerker(r, s.lattice, s.dims, alpha)) <= tau
+    g2 = np.sort(np.unique(np.round(np.sum(basis.grid_G(s.lattice, s.dims) ** 2, axis=-1).ravel(), 12)))
+    g2min = g2[g2 > 0][0]
+    assert np.linalg.norm(r) <= tau * (g2min + alpha ** 2) / g2min
