@@ -18,7 +18,7 @@ import dataclasses
 
 import numpy as np
 
-from . import dft, response
+from . import dft, response, schur
 
 
 # ------------------------------------------------------------ plain GMRES ---
@@ -106,10 +106,12 @@ def sternheimer_cg(H, eps_n, Phi, b, tol, kinetic, kappa, maxiter=500):
     return Q(x), it, rnorm
 
 
-def chi0_inexact(gs, u, tolerances, kxc=None):
+def chi0_inexact(gs, u, tolerances, kxc=None, schur_nbands=0):
     """chi0 u with dphi^Q from CG at the per-(n,k) tolerances (a dict or array
     indexed like ``systems(gs)``); same formula as response.chi0 otherwise.
-    Returns (chi0 u, number of Hamiltonian applications)."""
+    schur_nbands > 0: the Sternheimer equations in their Schur-complement form
+    (Sec. 3.4.2, oracle/schur.py) with the bands N_occ,k + 1 .. schur_nbands as
+    the extra computed bands.  Returns (chi0 u, number of Hamiltonian applications)."""
     dims, vol = gs.dims, gs.volume
     out = np.zeros(dims)
     nham = 0
@@ -125,10 +127,15 @@ def chi0_inexact(gs, u, tolerances, kxc=None):
         deps = a[np.arange(no), np.arange(no)].real
         kappa = np.einsum("gn,g,gn->n", Phi.conj(), kb.kinetic, Phi).real
         dphi = np.zeros((no, Phi.shape[0]), dtype=np.complex128)
+        Psi = kb.vecs[:, no:schur_nbands] if schur_nbands > no else None
         for n in range(no):
             b = -(y[n] - Phi @ a[n])
-            xq, it, _ = sternheimer_cg(kb.H, kb.eps[n], Phi, b, tolerances[s], kb.kinetic,
-                                       max(1.0, kappa[n]))
+            if Psi is not None:
+                xq, it, _ = schur.schur_cg(kb.H, kb.eps[n], Phi, Psi, b, tolerances[s], kb.kinetic,
+                                           max(1.0, kappa[n]))
+            else:
+                xq, it, _ = sternheimer_cg(kb.H, kb.eps[n], Phi, b, tolerances[s], kb.kinetic,
+                                           max(1.0, kappa[n]))
             nham += it
             s += 1
             coef = np.zeros(no, dtype=np.complex128)
@@ -153,13 +160,13 @@ def chi0_inexact(gs, u, tolerances, kxc=None):
     return out, nham
 
 
-def dielectric_inexact(gs, v, tol_fn, kxc=None):
+def dielectric_inexact(gs, v, tol_fn, kxc=None, schur_nbands=0):
     """E~ v = v - ||Kv|| chi0~(Kv/||Kv||) with CG tolerances tol_fn(||Kv||)."""
     Kv = response.apply_K(v, gs, kxc)
     nrm = float(np.linalg.norm(Kv))
     if nrm == 0.0:
         return v.copy(), 0
-    c, nham = chi0_inexact(gs, Kv / nrm, tol_fn(nrm), kxc)
+    c, nham = chi0_inexact(gs, Kv / nrm, tol_fn(nrm), kxc, schur_nbands)
     return v - nrm * c, nham
 
 
@@ -251,13 +258,14 @@ class InexactResult:
 
 
 def inexact_gmres(gs, b, tau, m, strategy, x0=None, s=1.0, kxc=None,
-                  max_restarts=20, track_errors=False, kerker_alpha=0.0):
+                  max_restarts=20, track_errors=False, kerker_alpha=0.0, schur_nbands=0):
     """Algorithm 1 with CG-solved Sternheimer equations (emulation on the CPU).
 
     kerker_alpha > 0: Algorithm 1 on the left-preconditioned system T E x = T b
     of eq. precond_dyson with the Kerker T of eq. kerker; the tolerance rules
     are unchanged (||T|| = 1, Lemma kerker_properties), the stopping rule and
-    the reported residuals are those of T r, and b_norm stays ||b||."""
+    the reported residuals are those of T r, and b_norm stays ||b||.
+    schur_nbands > 0: Schur-complement Sternheimer solves (see chi0_inexact)."""
     if kxc is None:
         kxc = response.exchange_kernel(gs.rho)
     shape = b.shape
@@ -276,7 +284,7 @@ def inexact_gmres(gs, b, tau, m, strategy, x0=None, s=1.0, kxc=None,
         if np.linalg.norm(x0) > 0:
             def tol0(kvn):
                 return cg_tolerances(gs, strategy, tau, 0, m, s, 1.0, kvn, b_norm)
-            Ex0, nh = dielectric_inexact(gs, x0, tol0, kxc)
+            Ex0, nh = dielectric_inexact(gs, x0, tol0, kxc, schur_nbands)
             nham += nh
             if track_errors:
                 err0 = float(np.linalg.norm(T(Ex0 - response.dielectric(gs, x0, kxc))))
@@ -293,7 +301,7 @@ def inexact_gmres(gs, b, tau, m, strategy, x0=None, s=1.0, kxc=None,
         for i in range(1, m + 1):
             def toli(kvn, i=i, rprev=rprev):
                 return cg_tolerances(gs, strategy, tau, i, m, s, rprev, kvn, b_norm)
-            w, nh = dielectric_inexact(gs, V[-1].reshape(shape), toli, kxc)
+            w, nh = dielectric_inexact(gs, V[-1].reshape(shape), toli, kxc, schur_nbands)
             nham += nh
             steps += 1
             if track_errors:

@@ -190,3 +190,21 @@ def test_kerker_preconditioned_algorithm(which, ins, metal):
     g2 = np.sort(np.unique(np.round(np.sum(basis.grid_G(s.lattice, s.dims) ** 2, axis=-1).ravel(), 12)))
     g2min = g2[g2 > 0][0]
     assert np.linalg.norm(r) <= tau * (g2min + alpha ** 2) / g2min
+
+
+@pytest.mark.parametrize("which", ["ins", "metal"])
+def test_schur_complement_solves_inside_algorithm_1(which, ins, metal):
+    """The Schur-complement Sternheimer solves (Sec. 3.4.2) change the operator
+    CG iterates on, not the solutions: Algorithm 1 with them and the exact
+    prefactor still reaches tau, its solution agrees with the plain one to the
+    accuracy both reach, and no more Hamiltonian applications are needed."""
+    s, gs = ins if which == "ins" else metal
+    b = response.chi0(gs, perturbation(s))
+    b /= np.linalg.norm(b)
+    tau = 1e-9
+    plain = gmres.inexact_gmres(gs, b, tau, 10, "grt_exact")
+    nb = max(kb.nocc for kb in gs.kblocks) + 4
+    sch = gmres.inexact_gmres(gs, b, tau, 10, "grt_exact", schur_nbands=nb)
+    assert sch.converged and _true_residual(gs, b, sch.x) <= tau
+    assert np.linalg.norm(sch.x - plain.x) < 100 * tau
+    assert sch.nham <= plain.nham
