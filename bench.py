@@ -55,6 +55,11 @@ def parse():
     p.add_argument("--batch", action="store_true",
                    help="also time the batched workload: 32 perturbations of the 10-bohr cell (cfg1), "
                         "lockstep against one after another")
+    p.add_argument("--slab-strategies", action="store_true",
+                   help="also run every tolerance rule on the full-size metallic slab (cfg3) with Kerker")
+    p.add_argument("--cfg4-guaranteed", action="store_true",
+                   help="also solve the 64-atom cell with Kleinman-Bylander projectors (cfg4) with the "
+                        "guaranteed rule grt_exact, beside bal")
     p.add_argument("--profile-run", action="store_true",
                    help="only setup, warm-up and the timed steps (for ncu); prints no bench line")
     return p.parse_args()
@@ -229,6 +234,71 @@ def batch_run(tau, m, stream):
             "time_s_lockstep": tb, "time_s_one_by_one": ts, "speedup": ts / tb,
             "n_ham_lockstep": int(sum(r["n_ham"] for r in rb)), "n_ham_one_by_one": int(sum(r["n_ham"] for r in rs)),
             "max_true_residual": max(res), "tau": tau}
+def _rule_run(ctx, b, nsys, rule, tau, m, precision, alpha=0.0):
+    """One solve with one tolerance rule: time, N_ham, the solver's residual
+    estimate (of T r with Kerker) and the true unpreconditioned residual
+    ||b - E x|| from an FP64 E application at tight CG tolerances."""
+    import numpy as np
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.time()
+    x, rep = ctx.solve_response(b, tau=tau, m=m, strategy=rule, precision=precision, kerker_alpha=alpha)
+    torch.cuda.synchronize()
+    dt = time.time() - t0
+    Ex, _ = ctx.apply_dielectric(x, tol=np.full(nsys, 1e-12))
+    tr = float(torch.linalg.norm(b - Ex))
+    r = rep[0]
+    return {"time_s": dt, "status": r["status"], "n_ham": r["n_ham"], "n_ham_fp64": r["n_ham_fp64"],
+            "outer_iters": r["outer_iters"], "restarts": r["restarts"], "est_residual": r["est_residual"],
+            "true_residual": tr, "eta": efficiency(float(torch.linalg.norm(b)), max(tr, 1e-300), r["n_ham"])}
+
+
+def slab_strategies(tau, m):
+    """NEXT row f1 at full size: the metallic slab (cfg3: 40 x 40 x 216 grid,
+    16 k-points, about 1,050 Sternheimer systems per E application), ground
+    state by the GPU eigensolver, b = chi0 dV0 / ||chi0 dV0||, left Kerker
+    alpha = 0.8, every tolerance rule in mixed precision; eta_rel against D10."""
+    import numpy as np
+    import torch
+    from paper_2505_02319_gb300 import groundstate
+    from workloads import make_system, perturbation
+    s = make_system("cfg3")
+    t0 = time.time()
+    ctx = groundstate.context_for(s, eigensolver="chfsi", eig_tol=1e-9)
+    setup = time.time() - t0
+    nsys = ctx.groundstate_nsys
+    b, _ = ctx.apply_chi0(torch.tensor(perturbation(s).ravel(), device="cuda"), tol=np.full(nsys, 1e-12))
+    b = (b / torch.linalg.norm(b)).contiguous()
+    out = {"workload": "cfg3 slab, Kerker alpha 0.8, mixed precision", "tau": tau, "m": m, "setup_s": setup,
+           "systems_per_E": nsys, "rules": {}}
+    for rule in ("D10", "D100", "D10n", "agr", "bal", "grt", "grt_exact"):
+        out["rules"][rule] = _rule_run(ctx, b, nsys, rule, tau, m, "mixed", alpha=0.8)
+    for rule, v in out["rules"].items():
+        v["eta_rel_vs_D10"] = v["eta"] / out["rules"]["D10"]["eta"]
+    ctx.destroy()
+    return out
+
+
+def cfg4_guaranteed(tau, m):
+    """cfg4 (20.5-bohr cell, 64 Gaussian atoms with s and p Kleinman-Bylander
+    projectors, 96^3 grid, 128 occupied bands, eps_129 - eps_128 = 1e-4 Ha):
+    bal, which drops the gap from its tolerances, against grt_exact, which keeps
+    it and carries the guarantee of Theorem inexact_gmres_dyson; mixed precision."""
+    import numpy as np
+    import torch
+    from paper_2505_02319_gb300 import groundstate
+    from workloads import make_system, perturbation
+    s = make_system("cfg4")
+    t0 = time.time()
+    ctx = groundstate.context_for(s, eigensolver="chfsi", eig_tol=1e-9)
+    setup = time.time() - t0
+    nsys = ctx.groundstate_nsys
+    b, _ = ctx.apply_chi0(torch.tensor(perturbation(s).ravel(), device="cuda"), tol=np.full(nsys, 1e-12))
+    b = (b / torch.linalg.norm(b)).contiguous()
+    out = {"workload": "cfg4, 256 KB projectors, mixed precision", "tau": tau, "m": m, "setup_s": setup,
+           "rules": {rule: _rule_run(ctx, b, nsys, rule, tau, m, "mixed") for rule in ("bal", "grt_exact")}}
+    ctx.destroy()
+    return out
 
 
 SUPERCELL_BASE = "cfg1"
@@ -419,6 +489,10 @@ def run_ours(args, rank, world, local_rank):
         out["schur"] = schur_run(ctx, b, nsys, opts, stream)
     if args.batch:
         out["batch"] = batch_run(TAU, M, stream)
+    if args.slab_strategies:
+        out["slab_strategies"] = slab_strategies(TAU, M)
+    if args.cfg4_guaranteed:
+        out["cfg4_guaranteed"] = cfg4_guaranteed(TAU, M)
     if args.supercell:
         out["supercell_study"] = supercell_study([int(v) for v in args.supercell.split(",")], 1e-9, 10,
                                                  ikr.FP64)
