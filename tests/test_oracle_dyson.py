@@ -20,6 +20,13 @@ def metal():
     return s, groundstate.solve(s)
 
 
+@pytest.fixture(scope="module")
+def metal_E(metal):
+    """The dense E of the tiny metal (one column per grid point)."""
+    s, gs = metal
+    return response.dense_operator(lambda v: response.dielectric(gs, v), s.dims)
+
+
 def test_rescaling_is_an_identity(ins):
     """eq. op_discretised: v - ||Kv|| chi0(Kv/||Kv||) = v - chi0 K v (linearity)."""
     s, gs = ins
@@ -38,19 +45,19 @@ def test_adjoint_is_the_dielectric_operator(ins):
     assert abs(lhs - rhs) < 1e-12 * abs(lhs)
 
 
-def test_adjoint_function_is_the_transpose(metal):
+def test_adjoint_function_is_the_transpose(metal, metal_E):
     """dielectric_adjoint is the transpose of the dense E (metal, k-points)."""
     s, gs = metal
-    E = response.dense_operator(lambda v: response.dielectric(gs, v), s.dims)
+    E = metal_E
     rng = np.random.default_rng(4)
     v = rng.normal(size=s.dims)
     np.testing.assert_allclose(response.dielectric_adjoint(gs, v).ravel(), E.T @ v.ravel(), atol=1e-12)
 
 
 @pytest.mark.parametrize("which", ["ins", "metal"])
-def test_gmres_matches_dense_solve(which, ins, metal):
+def test_gmres_matches_dense_solve(which, ins, metal, metal_E):
     s, gs = ins if which == "ins" else metal
-    E = response.dense_operator(lambda v: response.dielectric(gs, v), s.dims)
+    E = response.dense_operator(lambda v: response.dielectric(gs, v), s.dims) if which == "ins" else metal_E
     b = response.chi0(gs, perturbation(s))
     b /= np.linalg.norm(b)
     x_dense = np.linalg.solve(E, b.ravel()).reshape(s.dims)
@@ -208,3 +215,29 @@ def test_schur_complement_solves_inside_algorithm_1(which, ins, metal):
     assert sch.converged and _true_residual(gs, b, sch.x) <= tau
     assert np.linalg.norm(sch.x - plain.x) < 100 * tau
     assert sch.nham <= plain.nham
+
+
+def test_adjoint_gradient_equals_finite_difference(metal, metal_E):
+    """The gradient of L(dV) = ||W drho||^2, drho = E^-1 chi0 dV, is
+    chi0 E^-T (2 W^2 drho) (the adjoint solve of Sec. 2.2 with E^T = 1 - K chi0).
+    L is quadratic in dV, so the central difference is exact up to rounding;
+    dense solves on the tiny grid."""
+    from workloads import loss_weights
+    s, gs = metal
+    E = metal_E
+    W2 = loss_weights(s).ravel() ** 2
+    dV = perturbation(s)
+    d = np.random.default_rng(12).normal(size=s.dims)
+    d *= np.linalg.norm(dV) / np.linalg.norm(d)
+
+    def drho(v):
+        return np.linalg.solve(E, response.chi0(gs, v).ravel())
+
+    def loss(v):
+        return float(np.sum(W2 * drho(v) ** 2))
+
+    lam = np.linalg.solve(E.T, 2.0 * W2 * drho(dV))
+    grad = response.chi0(gs, lam.reshape(s.dims)).ravel()
+    h = 1e-3
+    fd = (loss(dV + h * d) - loss(dV - h * d)) / (2 * h)
+    assert abs(float(grad @ d.ravel()) - fd) <= 1e-9 * abs(fd)
