@@ -88,7 +88,9 @@ struct KPoint {
 // buffer: per vector v the rows 2v = v and 2v + 1 = (-Im v, Re v) as FP32
 // reals, split into TF32 hi and lo parts; rows of 2 ld reals.
 struct TcRows {
-  DBuf<float> hi, lo;
+  DBuf<float> hi, lo;       // A: rows of the set's vectors
+  DBuf<float> thi, tlo;     // AT: per k-point, rows 2g + c of 2 mpad reals (the apply product)
+  int mpad = 0;
   bool ready = false;
   const float2* src = nullptr;
 };
@@ -266,7 +268,7 @@ struct ikr_ctx {
   int rset_total = 0;           // vectors in d_rset (sum of nbands over k)
   // tensor-core projection coefficients (tc_proj.cu; ikr_set_tensor_cores)
   bool tc_proj = false;
-  ikr::TcRows tc_occ, tc_rset;
+  ikr::TcRows tc_occ, tc_rset, tc_xset;   // per orbital set: Phi, [Phi Psi], Psi
   ikr::DBuf<int> tc_err;
   ikr::SysList batch_list;
   ikr::DBuf<int> d_batch_map;

@@ -256,6 +256,181 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
+// Transposed A for the apply product, per k-point: AT[k][2g + c][2m + q], rows of 2 mpad reals
+// (mpad = maxcnt rounded up to even, so that rows are whole 16-byte groups; zero past the set),
+// q = 0: (Re v_m[g], Im v_m[g])[c], q = 1: (-Im v_m[g], Re v_m[g])[c], split into hi and lo
+__global__ void k_tc_cols(const float2* __restrict__ phi, const int* __restrict__ set_off,
+                          const int* __restrict__ set_cnt, int nk, int ld, int mpad, float* __restrict__ thi,
+                          float* __restrict__ tlo) {
+  const size_t n = (size_t)nk * ld * mpad;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e % mpad);
+    const size_t kg = e / mpad;
+    const int g = (int)(kg % ld), k = (int)(kg / ld);
+    float2 p = make_float2(0.f, 0.f);
+    if (m < set_cnt[k]) p = phi[((size_t)set_off[k] + m) * ld + g];
+    const float a[4] = {p.x, -p.y, p.y, p.x};   // (c, q) = (0,0), (0,1), (1,0), (1,1)
+#pragma unroll
+    for (int cq = 0; cq < 4; ++cq) {
+      const int c = cq >> 1, q = cq & 1;
+      const size_t o = (((size_t)k * ld + g) * 2 + c) * (2 * (size_t)mpad) + 2 * m + q;
+      const float h = tf32_hi(a[cq]);
+      thi[o] = h;
+      tlo[o] = a[cq] - h;
+    }
+  }
+}
+
+// out[s][g] = alpha in[s][g] + beta sum_m v_m[g] coef[s][m] for the plane waves of one 128-real
+// tile (64 plane waves) and NT systems; with dv, dpart[s * nparts + tile] = sum Re(conj(dv) out)
+// over the tile (the chunking of the CUDA-core apply: 64 plane waves).
+template <int NT>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_apply(const float* __restrict__ thi, const float* __restrict__ tlo, const int* __restrict__ set_cnt,
+               const int* __restrict__ nb_k, const int* __restrict__ kstart, const int* __restrict__ kcount,
+               const double2* __restrict__ coef, int maxcnt, int mpad, const float2* in, float alpha, float beta,
+               float2* out, int ldy, int ld, const float2* __restrict__ dv, double* __restrict__ dpart, int nparts,
+               const int* __restrict__ active, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* sAhi = sm;
+  unsigned char* sAlo = sm + kTileBytes;
+  unsigned char* sBhi = sm + 2 * kTileBytes;
+  unsigned char* sBlo = sBhi + NT * kTK * 4;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sBlo + NT * kTK * 4);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
+  double* red = reinterpret_cast<double*>(slot + 2);              // [4 warps][NT] dot partials
+  const int k = blockIdx.y, tile = blockIdx.x, tn = blockIdx.z;
+  const int cnt = set_cnt[k], nb = nb_k[k], ns = kcount[k];
+  const int r0 = tile * kTM, s0 = tn * NT;                        // first real row (2 g + c), first system
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (s0 >= ns) return;                                           // uniform
+  if (r0 >= 2 * nb) {                                             // tile past Nb_k: define the dot partials
+    if (dpart)
+      for (int j = tid; j < NT; j += 128) {
+        const int s = kstart[k] + s0 + j;
+        if (s0 + j < ns && (!active || active[s])) dpart[(size_t)s * nparts + tile] = 0.0;
+      }
+    return;
+  }
+  constexpr uint32_t kCols = NT < 32 ? 32 : NT;
+  if (warp == 0) tmem_alloc(slot, kCols);
+  if (tid == 0) mbar_init(bar, 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const size_t ldt = 2 * (size_t)mpad;                            // reals per AT row (multiple of 4)
+  const size_t trow0 = (size_t)k * 2 * ld + r0;
+  const int sbase = kstart[k] + s0;
+  const int kend = 2 * cnt;
+  bool ok = true;
+  uint32_t phase = 0, acc = 0;
+  for (int kb = 0; kb < kend && ok; kb += kTK) {
+    for (int e = tid; e < kTM * (kTK / 4); e += 128) {
+      const int r = e >> 3, c4 = e & 7;
+      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+      if (kb + 4 * c4 < kend) {                                   // AT is zero past 2 cnt (padding)
+        const size_t o = (trow0 + r) * ldt + kb + 4 * c4;
+        h = *reinterpret_cast<const float4*>(thi + o);
+        l = *reinterpret_cast<const float4*>(tlo + o);
+      }
+      *reinterpret_cast<float4*>(sAhi + core_off(r, c4)) = h;
+      *reinterpret_cast<float4*>(sAlo + core_off(r, c4)) = l;
+    }
+    for (int e = tid; e < NT * (kTK / 4); e += 128) {
+      const int r = e >> 3, c4 = e & 7;
+      float x[4] = {0.f, 0.f, 0.f, 0.f};
+      const int s = sbase + r;
+      if (s0 + r < ns && (!active || active[s]))
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int i = kb + 4 * c4 + 2 * q;                      // real index 2 m (+1 below)
+          if (i < kend) {
+            const double2 cc = coef[(size_t)s * maxcnt + (i >> 1)];
+            x[2 * q] = (float)cc.x;
+            x[2 * q + 1] = (float)cc.y;
+          }
+        }
+      const float4 h = make_float4(tf32_hi(x[0]), tf32_hi(x[1]), tf32_hi(x[2]), tf32_hi(x[3]));
+      *reinterpret_cast<float4*>(sBhi + core_off(r, c4)) = h;
+      *reinterpret_cast<float4*>(sBlo + core_off(r, c4)) =
+          make_float4(x[0] - h.x, x[1] - h.y, x[2] - h.z, x[3] - h.w);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      constexpr uint32_t id = idesc_tf32(NT);
+#pragma unroll
+      for (int kk = 0; kk < kTK / 8; ++kk) {
+        const uint32_t off = kk * 256;
+        const uint64_t ah = sdesc(saddr(sAhi) + off), al = sdesc(saddr(sAlo) + off);
+        const uint64_t bh = sdesc(saddr(sBhi) + off), bl = sdesc(saddr(sBlo) + off);
+        mma_tf32(tmem, ah, bh, id, acc);
+        mma_tf32(tmem, ah, bl, id, 1);
+        mma_tf32(tmem, al, bh, id, 1);
+        acc = 1;
+      }
+      mma_commit(bar);
+    }
+    ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
+    phase ^= 1;
+    tc_fence_after();
+  }
+  if (!ok) {
+    if (lane == 0) atomicExch(err, 1);
+  } else {
+    const int row = r0 + 32 * warp + lane;                         // 2 g + c
+    const int g = row >> 1;
+    float v[32];
+#pragma unroll 1
+    for (int c0 = 0; c0 < NT; c0 += 32) {
+      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float im = __shfl_xor_sync(0xffffffffu, v[j], 1);
+        const int sl = s0 + c0 + j;
+        const int s = kstart[k] + sl;
+        const bool on = !(lane & 1) && g < nb && sl < ns && (!active || active[s]);
+        double d = 0.0;
+        if (on) {
+          const size_t o = (size_t)s * ldy + g;
+          float2 y = make_float2(beta * v[j], beta * im);
+          if (alpha != 0.f) {
+            const float2 xi = in[o];
+            y.x += alpha * xi.x;
+            y.y += alpha * xi.y;
+          }
+          out[o] = y;
+          if (dv) {
+            const float2 w = dv[o];
+            d = (double)w.x * y.x + (double)w.y * y.y;
+          }
+        }
+        if (dpart) {
+          d = warp_sum(d);
+          if (lane == 0) red[warp * NT + c0 + j] = d;
+        }
+      }
+    }
+    if (dpart) {
+      __syncthreads();
+      for (int j = tid; j < NT; j += 128) {
+        const int s = kstart[k] + s0 + j;
+        if (s0 + j < ns && (!active || active[s]))
+          dpart[(size_t)s * nparts + tile] = ((red[j] + red[NT + j]) + red[2 * NT + j]) + red[3 * NT + j];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kCols);
+  }
+}
+
 // coef[s][m] = sum of the chunk partials in chunk order: a warp per coefficient
 __global__ void k_tc_reduce(const double2* __restrict__ part, int nsys, int maxcnt, int nch,
                             const int* __restrict__ sys_k, const int* __restrict__ set_cnt,
@@ -282,9 +457,17 @@ __global__ void k_tc_reduce(const double2* __restrict__ part, int nsys, int maxc
 
 // ----------------------------------------------------------------- host --
 
-// The A rows of an orbital set (prepared once per set and ground state).
+// The operands of an orbital set (prepared once per set and ground state); the sets are told
+// apart by their offset arrays (the transposed blocks depend on which vectors a set takes)
+static TcRows& tc_rows_of(ikr_ctx* c, const OrbSet& set) {
+  if (set.off == c->d_phi_off.p) return c->tc_occ;
+  if (set.off == c->d_roff.p) return c->tc_rset;
+  IKR_REQUIRE(set.off == c->d_xoff.p, IKR_ERR_ARG, "tensor-core projections: unknown orbital set");
+  return c->tc_xset;
+}
+
 static void tc_prepare(ikr_ctx* c, const OrbSet& set, int nvec_total) {
-  TcRows& t = (set.phi32 == c->d_phi_all32.p && set.off == c->d_phi_off.p) ? c->tc_occ : c->tc_rset;
+  TcRows& t = tc_rows_of(c, set);
   if (t.ready && t.src == set.phi32) return;
   const size_t n = (size_t)2 * nvec_total * 2 * c->ld;
   t.hi.reserve(n);
@@ -293,12 +476,18 @@ static void tc_prepare(ikr_ctx* c, const OrbSet& set, int nvec_total) {
   const int blocks = (int)std::min<size_t>((work + 255) / 256, (size_t)c->nsm * 16);
   k_tc_rows<<<blocks, 256, 0, c->stream>>>(set.phi32, nvec_total, c->ld, t.hi.p, t.lo.p);
   IKR_CUDA(cudaGetLastError());
+  // AT for the apply product (every set sharing this buffer uses the same maxcnt bound)
+  const int nk = (int)c->k.size();
+  t.mpad = (set.maxcnt + 1) & ~1;
+  const size_t nt = (size_t)nk * 2 * c->ld * 2 * t.mpad;
+  t.thi.reserve(nt);
+  t.tlo.reserve(nt);
+  const size_t wk = (size_t)nk * c->ld * t.mpad;
+  const int bl2 = (int)std::min<size_t>((wk + 255) / 256, (size_t)c->nsm * 16);
+  k_tc_cols<<<bl2, 256, 0, c->stream>>>(set.phi32, set.off, set.cnt, nk, c->ld, t.mpad, t.thi.p, t.tlo.p);
+  IKR_CUDA(cudaGetLastError());
   t.ready = true;
   t.src = set.phi32;
-}
-
-static const TcRows& tc_rows_of(ikr_ctx* c, const OrbSet& set) {
-  return (set.phi32 == c->d_phi_all32.p && set.off == c->d_phi_off.p) ? c->tc_occ : c->tc_rset;
 }
 
 bool tc_proj_ok(ikr_ctx* c, const OrbSet& set) {
@@ -335,6 +524,33 @@ void proj_coef_tc(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const 
   const long long threads = 32LL * L.n * set.maxcnt;
   k_tc_reduce<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(part, L.n, set.maxcnt, nch, L.d_k.p,
                                                                          set.cnt, c->d_nb.p, active, coef);
+  IKR_CUDA(cudaGetLastError());
+}
+
+void proj_apply_tc(ikr_ctx* c, const SysList& L, const double2* coef, const float2* in, float alpha, float beta,
+                   float2* out, int ldy, const float2* dv, double* dpart, const int* active, const OrbSet& set,
+                   int nvec_total) {
+  tc_prepare(c, set, nvec_total);
+  const TcRows& t = tc_rows_of(c, set);
+  IKR_REQUIRE(t.mpad >= set.maxcnt, IKR_ERR_ARG, "tensor-core apply: transposed rows too short for the set");
+  int maxns = 0;
+  for (int v : L.kcount) maxns = std::max(maxns, v);
+  const int nparts = (c->ld + 63) / 64;                           // 64 plane waves per tile and dot partial
+  const int nt = maxns <= 32 ? 32 : (maxns <= 64 ? 64 : 128);
+  const int nnt = std::max(1, (maxns + nt - 1) / nt);
+  c->tc_err.reserve(1);
+  IKR_CUDA(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+  dim3 grid(nparts, (unsigned)c->k.size(), (unsigned)nnt);
+  const size_t smem = 2 * kTileBytes + 2 * (size_t)nt * kTK * 4 + 16 + 32 * (size_t)nt;
+  auto launch = [&](auto kern) {
+    IKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, 128, smem, c->stream>>>(t.thi.p, t.tlo.p, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p, coef,
+                                         set.maxcnt, t.mpad, in, alpha, beta, out, ldy, c->ld, dv, dpart, nparts,
+                                         active, c->tc_err.p);
+  };
+  if (nt == 32) launch(k_tc_apply<32>);
+  else if (nt == 64) launch(k_tc_apply<64>);
+  else launch(k_tc_apply<128>);
   IKR_CUDA(cudaGetLastError());
 }
 
