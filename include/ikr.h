@@ -203,13 +203,13 @@ ikr_status ikr_compute_eigenpairs(ikr_ctx* ctx, int nbands, double tol, int maxi
  * are set (setting new eigenpairs disables it again). */
 ikr_status ikr_set_schur(ikr_ctx* ctx, int enable);
 
-/* The FP32 coefficient products V_k^H Y of the projections (eq.
- * discretised_sternheimer: M = Phi^H Y, and the Q-projection of every FP32 CG
- * iteration) on the 5th-generation tensor cores: tcgen05 MMAs of kind::tf32
- * with each operand split into a TF32 high part and the remainder (three
- * products, FP32 accumulation in tensor memory), split-K over thread blocks,
- * fixed-order reduction of the chunk partials.  enable = 0 returns to the
- * CUDA-core kernels.  IKR_ERR_STATE before the eigenpairs are set.  A
+/* The FP32 projection products (eq. discretised_sternheimer: M = Phi^H Y, and
+ * the Q-projection Y - Phi (Phi^H Y) of every FP32 CG iteration), both V_k^H Y
+ * and Y - V_k C, on the 5th-generation tensor cores: tcgen05 MMAs of
+ * kind::tf32 with each operand split into a TF32 high part and the remainder
+ * (three products, FP32 accumulation in tensor memory); V_k^H Y split-K over
+ * thread blocks with a fixed-order reduction of the chunk partials.
+ * enable = 0 returns to the CUDA-core kernels.  IKR_ERR_STATE before the eigenpairs are set.  A
  * tensor-core launch whose internal wait runs out makes the calling solve
  * return IKR_ERR_TIMEOUT. */
 ikr_status ikr_set_tensor_cores(ikr_ctx* ctx, int enable);
@@ -222,6 +222,12 @@ ikr_status ikr_set_tensor_cores(ikr_ctx* ctx, int enable);
  * IKR_ERR_ARG for a bad k, nvec < 1 or NULL pointers; IKR_ERR_TIMEOUT as above. */
 ikr_status ikr_projection_coefficients(ikr_ctx* ctx, int k, int nvec, const void* y, int method, double* c,
                                        cudaStream_t stream);
+
+/* y <- Q_k y = y - Phi_k (Phi_k^H y), the projector of eq.
+ * discretised_sternheimer, in FP32 arithmetic: method 0 on the CUDA cores, 1
+ * on the tensor cores.  y: DEVICE, Nb_k x nvec complex64, column-major,
+ * overwritten.  Errors as ikr_projection_coefficients. */
+ikr_status ikr_project_out(ikr_ctx* ctx, int k, int nvec, void* y, int method, cudaStream_t stream);
 
 /* Host utility (no GPU): eigenvalues w (ascending, n) and eigenvectors v
  * (column j = eigenvector of w[j]; row-major n x n complex, interleaved) of the

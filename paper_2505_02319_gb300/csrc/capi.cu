@@ -207,6 +207,37 @@ ikr_status ikr_projection_coefficients(ikr_ctx* c, int k, int nvec, const void* 
   return s;
 }
 
+ikr_status ikr_project_out(ikr_ctx* c, int k, int nvec, void* y, int method, cudaStream_t stream) {
+  if (!c) return IKR_ERR_ARG;
+  c->stream = stream;
+  const bool old = c->tc_proj;
+  ikr_status s = guarded(c, [&] {
+    IKR_REQUIRE(c->have_gs, IKR_ERR_STATE, "the ground state is not set");
+    IKR_REQUIRE(k >= 0 && k < (int)c->k.size() && nvec >= 1 && y, IKR_ERR_ARG, "invalid arguments");
+    IKR_REQUIRE(method == 0 || method == 1, IKR_ERR_ARG, "method must be 0 or 1");
+    const KPoint& K = c->k[k];
+    std::vector<int> kof(nvec, k), band(nvec, 0);
+    SysList L;
+    make_syslist(c, L, nvec, kof.data(), band.data());
+    ensure_workspace(c, nvec);
+    Workspace& w = c->ws;
+    const int ld = c->ld;
+    IKR_CUDA(cudaMemsetAsync(w.Z32.p, 0, sizeof(float2) * (size_t)nvec * ld, stream));
+    IKR_CUDA(cudaMemcpy2DAsync(w.Z32.p, sizeof(float2) * ld, y, sizeof(float2) * K.nb, sizeof(float2) * K.nb, nvec,
+                               cudaMemcpyDeviceToDevice, stream));
+    c->tc_proj = method == 1;
+    double2* cf = reinterpret_cast<double2*>(w.coef.p);
+    proj_coef<float>(c, L, w.Z32.p, ld, nullptr, cf);
+    proj_apply<float>(c, L, cf, w.Z32.p, 1.0f, -1.0f, w.Z32.p, ld, nullptr, nullptr, nullptr);
+    if (c->tc_proj) tc_check(c);
+    IKR_CUDA(cudaMemcpy2DAsync(y, sizeof(float2) * K.nb, w.Z32.p, sizeof(float2) * ld, sizeof(float2) * K.nb, nvec,
+                               cudaMemcpyDeviceToDevice, stream));
+    IKR_CUDA(cudaStreamSynchronize(stream));
+  });
+  c->tc_proj = old;
+  return s;
+}
+
 ikr_status ikr_compute_eigenpairs(ikr_ctx* c, int nbands, double tol, int maxit, int degree, double* eigenvalues,
                                   int* iters, double* max_residual, cudaStream_t stream) {
   if (!c) return IKR_ERR_ARG;

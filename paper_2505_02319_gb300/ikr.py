@@ -85,6 +85,7 @@ def _load():
         "ikr_set_schur": (I, [P, I]),
         "ikr_set_tensor_cores": (I, [P, I]),
         "ikr_projection_coefficients": (I, [P, I, I, P, I, ct.POINTER(D), S]),
+        "ikr_project_out": (I, [P, I, I, P, I, S]),
         "ikr_hermitian_eigh": (I, [I, ct.POINTER(D), ct.POINTER(D), ct.POINTER(D)]),
         "ikr_num_kpoints": (I, [P]),
         "ikr_basis_size": (I, [P, I, ct.POINTER(I)]),
@@ -221,6 +222,13 @@ class Context:
         self._check(_LIB.ikr_projection_coefficients(self._h, int(k), nvec, _dptr(yy), int(method),
                                                       out.ctypes.data_as(ct.POINTER(ct.c_double)), _stream()))
         return out
+
+    def project_out(self, k, y, method=0):
+        """Q_k y = y - Phi_k (Phi_k^H y) for a (nvec, Nb_k) complex64 CUDA tensor
+        (in place; returned); method 0 CUDA cores, 1 tensor cores."""
+        self._check(_LIB.ikr_project_out(self._h, int(k), int(y.reshape(-1, y.shape[-1]).shape[0]), _dptr(y),
+                                         int(method), _stream()))
+        return y
 
     def compute_eigenpairs(self, nbands, tol=1e-10, maxit=200, degree=12):
         """Lowest ``nbands`` eigenpairs of every H_k on the GPU (Chebyshev-filtered

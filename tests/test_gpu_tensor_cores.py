@@ -37,6 +37,25 @@ def test_tensor_core_coefficients_match_cuda_cores(name, nvec):
         assert np.abs(c1 - c0).max() < 2e-6 * scale * np.sqrt(nb)
 
 
+@pytest.mark.parametrize("name,nvec", [("tiny_insulator", 3), ("tiny_metal", 24), ("tiny_kb", 40)])
+def test_tensor_core_projection_matches_cuda_cores(name, nvec):
+    ctx = context(name)
+    rng = np.random.default_rng(8)
+    vecs = _orbitals(ctx, name)
+    for k in range(len(vecs)):
+        nb = ctx.basis_size(k)
+        y = (rng.normal(size=(nvec, nb)) + 1j * rng.normal(size=(nvec, nb))).astype(np.complex64)
+        q0 = ctx.project_out(k, torch.tensor(y, device="cuda"), method=0).cpu().numpy()
+        q1 = ctx.project_out(k, torch.tensor(y, device="cuda"), method=1).cpu().numpy()
+        nocc = ctx.projection_coefficients(k, torch.tensor(y, device="cuda"), method=0).shape[1]
+        phi = vecs[k].cpu().numpy()[:nocc].astype(np.complex64).astype(np.complex128)
+        ref = y - (y.astype(np.complex128) @ phi.conj().T) @ phi
+        scale = np.abs(y).max()
+        assert np.abs(q0 - ref).max() < 1e-5 * scale
+        assert np.abs(q1 - ref).max() < 1e-5 * scale
+        assert np.abs(q1.astype(np.complex128) @ phi.conj().T).max() < 1e-5 * scale * np.sqrt(nb)
+
+
 def test_tensor_core_coefficients_of_the_orbitals_are_the_identity():
     ctx = context("tiny_metal")
     vecs = _orbitals(ctx, "tiny_metal")
