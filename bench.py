@@ -52,6 +52,8 @@ def parse():
                         "10-bohr Gamma-point cell (cfg1) along a_1, e.g. 1,2,4,8")
     p.add_argument("--schur", action="store_true",
                    help="also time the bench solve with Schur-complement Sternheimer solves")
+    p.add_argument("--tensor-cores", action="store_true",
+                   help="also time the bench solve with the projections on the tensor cores")
     p.add_argument("--batch", action="store_true",
                    help="also time the batched workload: 32 perturbations of the 10-bohr cell (cfg1), "
                         "lockstep against one after another")
@@ -199,6 +201,24 @@ def schur_run(ctx, b, nsys, opts, stream):
         ctx.set_schur(False)
     return {"time_s": t1, "time_s_plain": t0, "n_ham": r1[0]["n_ham"], "n_ham_plain": r0[0]["n_ham"],
             "true_residual": tr, "rel_diff_vs_plain": float(torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0))}
+
+
+def tensor_core_run(ctx, b, nsys, opts, stream):
+    """The bench solve with the FP32 projection products on the tensor cores
+    (tcgen05), against the same solve on the CUDA cores."""
+    import numpy as np
+    import torch
+    (x0, r0), t0 = timed(lambda: ctx.solve_response(b, opts=opts), stream)
+    ctx.set_tensor_cores(True)
+    try:
+        ctx.solve_response(b, opts=opts)
+        (x1, r1), t1 = timed(lambda: ctx.solve_response(b, opts=opts), stream)
+        Ex, _ = ctx.apply_dielectric(x1, tol=np.full(nsys, 1e-12))
+        tr = float(torch.linalg.norm(b - Ex))
+    finally:
+        ctx.set_tensor_cores(False)
+    return {"time_s": t1, "time_s_cuda_cores": t0, "n_ham": r1[0]["n_ham"], "n_ham_cuda_cores": r0[0]["n_ham"],
+            "true_residual": tr, "rel_diff_vs_cuda_cores": float(torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0))}
 
 
 def batch_run(tau, m, stream):
@@ -487,6 +507,8 @@ def run_ours(args, rank, world, local_rank):
         out["strategies"] = strategy_sweep(ctx, b, nsys, TAU, M, ikr.MIXED)
     if args.schur:
         out["schur"] = schur_run(ctx, b, nsys, opts, stream)
+    if args.tensor_cores:
+        out["tensor_cores"] = tensor_core_run(ctx, b, nsys, opts, stream)
     if args.batch:
         out["batch"] = batch_run(TAU, M, stream)
     if args.slab_strategies:
