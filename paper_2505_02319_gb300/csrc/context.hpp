@@ -84,17 +84,6 @@ struct KPoint {
   double rownorm_re = 0.0;      // ||Re F_k^-1 Phi_k||_{2,inf}
 };
 
-// The A operand of the tensor-core projections (tc_proj.cu) for one orbital
-// buffer: per vector v the rows 2v = v and 2v + 1 = (-Im v, Re v) as FP32
-// reals, split into TF32 hi and lo parts; rows of 2 ld reals.
-struct TcRows {
-  DBuf<float> hi, lo;       // A: rows of the set's vectors
-  DBuf<float> thi, tlo;     // AT: per k-point, rows 2g + c of 2 mpad reals (the apply product)
-  int mpad = 0;
-  bool ready = false;
-  const float2* src = nullptr;
-};
-
 // One batch of Sternheimer-type systems (k-point, band), grouped by k.
 struct SysList {
   int n = 0;
@@ -265,10 +254,8 @@ struct ikr_ctx {
   // system list of the batched CG over `batch_items` E applications (batch.cu),
   // and the position of each of its systems in the per-item blocks
   int batch_items = -1;
-  int rset_total = 0;           // vectors in d_rset (sum of nbands over k)
   // tensor-core projection coefficients (tc_proj.cu; ikr_set_tensor_cores)
   bool tc_proj = false;
-  ikr::TcRows tc_occ, tc_rset, tc_xset;   // per orbital set: Phi, [Phi Psi], Psi
   ikr::DBuf<int> tc_err;
   ikr::SysList batch_list;
   ikr::DBuf<int> d_batch_map;

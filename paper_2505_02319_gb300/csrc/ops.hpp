@@ -92,14 +92,13 @@ void proj_coef32(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const i
                  const OrbSet& set);
 void proj_apply32(ikr_ctx* c, const SysList& L, const double2* coef, const float2* in, float alpha, float beta,
                   float2* out, int ldy, const float2* dv, double* dpart, const int* active, const OrbSet& set);
-// Tensor-core Phi^H Y (tc_proj.cu): the FP32 coefficients of proj_coef32 by
-// tcgen05 MMAs; nvec_total = the vectors of the set's buffer
+// Tensor-core projection products (tc_proj.cu): the FP32 V^H Y of proj_coef32
+// and Y - V C of proj_apply32 by tcgen05 MMAs
 bool tc_proj_ok(ikr_ctx* c, const OrbSet& set);
 void proj_coef_tc(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef,
-                  const OrbSet& set, int nvec_total);
+                  const OrbSet& set);
 void proj_apply_tc(ikr_ctx* c, const SysList& L, const double2* coef, const float2* in, float alpha, float beta,
-                   float2* out, int ldy, const float2* dv, double* dpart, const int* active, const OrbSet& set,
-                   int nvec_total);
+                   float2* out, int ldy, const float2* dv, double* dpart, const int* active, const OrbSet& set);
 void tc_check(ikr_ctx* c);    // IKR_ERR_TIMEOUT if a tensor-core launch gave up on a wait
 int proj_chunks(ikr_ctx* c);                  // the largest count (workspace sizing)
 int proj_chunks(ikr_ctx* c, int fp_bytes);    // dot partials per system written by proj_apply

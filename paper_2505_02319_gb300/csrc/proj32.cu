@@ -215,8 +215,7 @@ int proj_chunks32() { return kPG; }
 void proj_coef32(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef,
                  const OrbSet& set) {
   if (tc_proj_ok(c, set)) {
-    const int ntot = (set.phi32 == c->d_phi_all32.p) ? c->occ.n : c->rset_total;
-    proj_coef_tc(c, L, Y, ldy, active, coef, set, ntot);
+    proj_coef_tc(c, L, Y, ldy, active, coef, set);
     return;
   }
   const int nch = (c->ld + kKG - 1) / kKG;
@@ -239,8 +238,7 @@ void proj_coef32(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const i
 void proj_apply32(ikr_ctx* c, const SysList& L, const double2* coef, const float2* in, float alpha, float beta,
                   float2* out, int ldy, const float2* dv, double* dpart, const int* active, const OrbSet& set) {
   if (tc_proj_ok(c, set)) {
-    const int ntot = (set.phi32 == c->d_phi_all32.p) ? c->occ.n : c->rset_total;
-    proj_apply_tc(c, L, coef, in, alpha, beta, out, ldy, dv, dpart, active, set, ntot);
+    proj_apply_tc(c, L, coef, in, alpha, beta, out, ldy, dv, dpart, active, set);
     return;
   }
   const int nch = (c->ld + kPG - 1) / kPG;

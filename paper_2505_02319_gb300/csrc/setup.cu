@@ -482,8 +482,6 @@ void set_eigenpairs(ikr_ctx* c, const ikr_eigenpairs* eig) {
     upload(c->d_reps, reps, st);
     c->schur = false;
     c->batch_items = -1;
-    c->rset_total = tot;
-    c->tc_occ.ready = c->tc_rset.ready = c->tc_xset.ready = false;
   }
   // preconditioner constants kappa_n = max(1, <phi_n, |k+G|^2/2 phi_n>)
   std::vector<double2> hphi((size_t)S * ld);

@@ -8,15 +8,16 @@
 // Real form.  With y and v stored as interleaved (re, im) floats, a complex
 // inner product is two real ones over 2 Nb_k reals:
 //   Re C = <v_il, y_il>,   Im C = <v'_il, y_il>,   v' = (-Im v, Re v),
-// so D = A B^T with A = [v_0; v'_0; v_1; v'_1; ...] (2 n_k rows, fixed by the
-// ground state, prepared once) and B = the systems' vectors (K-major both):
-// C[s][m] = D[2m][s] + i D[2m+1][s].
+// so D = A B^T with A = [v_0; v'_0; v_1; v'_1; ...] (2 n_k rows) and B = the
+// systems' vectors (K-major both): C[s][m] = D[2m][s] + i D[2m+1][s].  A is
+// never stored: each stage forms its rows from the FP32 orbitals in registers.
 //
 // Precision.  kind::tf32 multiplies the upper 19 bits of each float.  Each
-// operand is split x = hi + lo with hi = x with its low 13 mantissa bits
-// cleared (exact) and lo = x - hi (exact), and D accumulates
+// operand is split on the fly x = hi + lo with hi = x with its low 13
+// mantissa bits cleared (exact) and lo = x - hi (exact), and D accumulates
 // A_hi B_hi + A_hi B_lo + A_lo B_hi: products to about 2^-20 relative, FP32
-// accumulation, as the CUDA-core kernels.
+// accumulation, as the CUDA-core kernels.  Global traffic is that of the
+// FP32 operands themselves.
 //
 // Tiling.  One CTA (one warpgroup) owns 128 rows of A, NT systems and a
 // split-K chunk of kTC reals; stages of kTK = 32 reals are written to shared
@@ -122,30 +123,11 @@ __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__flo
 
 }  // namespace
 
-// A rows of the orbital set: row 2v = v (interleaved), row 2v + 1 = v' = (-Im v, Re v),
-// split into hi and lo; rows of 2 ld reals
-__global__ void k_tc_rows(const float2* __restrict__ phi, int nvec, int ld, float* __restrict__ ahi,
-                          float* __restrict__ alo) {
-  const size_t n = (size_t)nvec * ld;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t v = e / ld, g = e - v * ld;
-    const float2 p = phi[e];
-    const float a[4] = {p.x, p.y, -p.y, p.x};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const size_t o = (2 * v + (q >> 1)) * (size_t)(2 * ld) + 2 * g + (q & 1);
-      const float h = tf32_hi(a[q]);
-      ahi[o] = h;
-      alo[o] = a[q] - h;
-    }
-  }
-}
-
 // Partial sums of D = A B^T over one split-K chunk: part[(s * maxcnt + m) * nch + chunk] = (Re, Im) C[s][m].
 // grid: (chunks, k-points, A-tiles x system tiles); NT systems per tile.
 template <int NT>
 __global__ void __launch_bounds__(128, 1)
-    k_tc_coef(const float* __restrict__ ahi, const float* __restrict__ alo, const int* __restrict__ set_off,
+    k_tc_coef(const float2* __restrict__ phi, const int* __restrict__ set_off,
               const int* __restrict__ set_cnt, const int* __restrict__ nb_k, const int* __restrict__ kstart,
               const int* __restrict__ kcount, const float2* __restrict__ Y, int ldy, int ld, int nmt, int nch,
               int maxcnt, const int* __restrict__ active, double2* __restrict__ part, int* __restrict__ err) {
@@ -170,24 +152,30 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
-  const size_t arow0 = 2 * (size_t)set_off[k] + i0;    // first A row of the tile
-  const size_t lda = 2 * (size_t)ld;                    // reals per A row
+  const float* vbase = reinterpret_cast<const float*>(phi + ((size_t)set_off[k] + i0 / 2) * ld);
+  const size_t lda = 2 * (size_t)ld;                    // reals per orbital
   const int sbase = kstart[k] + s0;
   bool ok = true;
   uint32_t phase = 0;
   uint32_t acc = 0;
   for (int kb = k0; kb < k1 && ok; kb += kTK) {
-    // A tiles: 128 rows x 8 groups of 4 reals; rows past 2 cnt are zero
-    for (int e = tid; e < kTM * (kTK / 4); e += 128) {
-      const int r = e >> 3, c4 = e & 7;
-      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-      if (i0 + r < 2 * cnt && kb + 4 * c4 < k1) {
-        const size_t o = (arow0 + r) * lda + kb + 4 * c4;
-        h = *reinterpret_cast<const float4*>(ahi + o);
-        l = *reinterpret_cast<const float4*>(alo + o);
-      }
-      *reinterpret_cast<float4*>(sAhi + core_off(r, c4)) = h;
-      *reinterpret_cast<float4*>(sAlo + core_off(r, c4)) = l;
+    // A tiles from the orbitals: orbital mo of the tile gives row 2 mo = (Re, Im) and row
+    // 2 mo + 1 = (-Im, Re) of two plane waves per 16-byte group; orbitals past cnt are zero
+    // (the orbitals are zero past Nb_k, so a group across 2 Nb_k needs no mask)
+    for (int e = tid; e < (kTM / 2) * (kTK / 4); e += 128) {
+      const int mo = e >> 3, c4 = e & 7;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i0 / 2 + mo < cnt && kb + 4 * c4 < k1)
+        x = *reinterpret_cast<const float4*>(vbase + mo * lda + kb + 4 * c4);
+      const float4 y = make_float4(-x.y, x.x, -x.w, x.z);
+      const float4 xh = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+      const float4 yh = make_float4(tf32_hi(y.x), tf32_hi(y.y), tf32_hi(y.z), tf32_hi(y.w));
+      *reinterpret_cast<float4*>(sAhi + core_off(2 * mo, c4)) = xh;
+      *reinterpret_cast<float4*>(sAlo + core_off(2 * mo, c4)) =
+          make_float4(x.x - xh.x, x.y - xh.y, x.z - xh.z, x.w - xh.w);
+      *reinterpret_cast<float4*>(sAhi + core_off(2 * mo + 1, c4)) = yh;
+      *reinterpret_cast<float4*>(sAlo + core_off(2 * mo + 1, c4)) =
+          make_float4(y.x - yh.x, y.y - yh.y, y.z - yh.z, y.w - yh.w);
     }
     // B tiles: NT systems, split on the fly; reals past 2 Nb_k and inactive systems are zero
     for (int e = tid; e < NT * (kTK / 4); e += 128) {
@@ -256,39 +244,14 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
-// Transposed A for the apply product, per k-point: AT[k][2g + c][2m + q], rows of 2 mpad reals
-// (mpad = maxcnt rounded up to even, so that rows are whole 16-byte groups; zero past the set),
-// q = 0: (Re v_m[g], Im v_m[g])[c], q = 1: (-Im v_m[g], Re v_m[g])[c], split into hi and lo
-__global__ void k_tc_cols(const float2* __restrict__ phi, const int* __restrict__ set_off,
-                          const int* __restrict__ set_cnt, int nk, int ld, int mpad, float* __restrict__ thi,
-                          float* __restrict__ tlo) {
-  const size_t n = (size_t)nk * ld * mpad;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const int m = (int)(e % mpad);
-    const size_t kg = e / mpad;
-    const int g = (int)(kg % ld), k = (int)(kg / ld);
-    float2 p = make_float2(0.f, 0.f);
-    if (m < set_cnt[k]) p = phi[((size_t)set_off[k] + m) * ld + g];
-    const float a[4] = {p.x, -p.y, p.y, p.x};   // (c, q) = (0,0), (0,1), (1,0), (1,1)
-#pragma unroll
-    for (int cq = 0; cq < 4; ++cq) {
-      const int c = cq >> 1, q = cq & 1;
-      const size_t o = (((size_t)k * ld + g) * 2 + c) * (2 * (size_t)mpad) + 2 * m + q;
-      const float h = tf32_hi(a[cq]);
-      thi[o] = h;
-      tlo[o] = a[cq] - h;
-    }
-  }
-}
-
 // out[s][g] = alpha in[s][g] + beta sum_m v_m[g] coef[s][m] for the plane waves of one 128-real
 // tile (64 plane waves) and NT systems; with dv, dpart[s * nparts + tile] = sum Re(conj(dv) out)
 // over the tile (the chunking of the CUDA-core apply: 64 plane waves).
 template <int NT>
 __global__ void __launch_bounds__(128, 1)
-    k_tc_apply(const float* __restrict__ thi, const float* __restrict__ tlo, const int* __restrict__ set_cnt,
+    k_tc_apply(const float2* __restrict__ phi, const int* __restrict__ set_off, const int* __restrict__ set_cnt,
                const int* __restrict__ nb_k, const int* __restrict__ kstart, const int* __restrict__ kcount,
-               const double2* __restrict__ coef, int maxcnt, int mpad, const float2* in, float alpha, float beta,
+               const double2* __restrict__ coef, int maxcnt, const float2* in, float alpha, float beta,
                float2* out, int ldy, int ld, const float2* __restrict__ dv, double* __restrict__ dpart, int nparts,
                const int* __restrict__ active, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -319,23 +282,30 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
-  const size_t ldt = 2 * (size_t)mpad;                            // reals per AT row (multiple of 4)
-  const size_t trow0 = (size_t)k * 2 * ld + r0;
+  const int g0 = r0 / 2;                                          // first plane wave of the tile
+  const float2* vk = phi + (size_t)set_off[k] * ld;
   const int sbase = kstart[k] + s0;
   const int kend = 2 * cnt;
   bool ok = true;
   uint32_t phase = 0, acc = 0;
   for (int kb = 0; kb < kend && ok; kb += kTK) {
-    for (int e = tid; e < kTM * (kTK / 4); e += 128) {
-      const int r = e >> 3, c4 = e & 7;
-      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-      if (kb + 4 * c4 < kend) {                                   // AT is zero past 2 cnt (padding)
-        const size_t o = (trow0 + r) * ldt + kb + 4 * c4;
-        h = *reinterpret_cast<const float4*>(thi + o);
-        l = *reinterpret_cast<const float4*>(tlo + o);
+    // A tile = AT[2g + c][2m + q] from the orbitals: (c, q) = (0, 0) Re v_m[g], (0, 1) -Im,
+    // (1, 0) Im, (1, 1) Re; 64 plane waves x 16 orbitals, plane waves fastest (coalesced);
+    // orbitals past cnt are zero (g0 + 63 < ld: the orbitals are zero past Nb_k)
+    for (int e = tid; e < (kTM / 2) * (kTK / 2); e += 128) {
+      const int gl = e & 63, ml = e >> 6;
+      const int m = kb / 2 + ml;
+      float2 p = make_float2(0.f, 0.f);
+      if (m < cnt) p = vk[(size_t)m * ld + g0 + gl];
+      const float v4[4] = {p.x, -p.y, p.y, p.x};
+      const int c4 = ml >> 1, wpos = 2 * (ml & 1);
+#pragma unroll
+      for (int cq = 0; cq < 4; ++cq) {
+        const int byte = core_off(2 * gl + (cq >> 1), c4) + 4 * (wpos + (cq & 1));
+        const float h = tf32_hi(v4[cq]);
+        *reinterpret_cast<float*>(sAhi + byte) = h;
+        *reinterpret_cast<float*>(sAlo + byte) = v4[cq] - h;
       }
-      *reinterpret_cast<float4*>(sAhi + core_off(r, c4)) = h;
-      *reinterpret_cast<float4*>(sAlo + core_off(r, c4)) = l;
     }
     for (int e = tid; e < NT * (kTK / 4); e += 128) {
       const int r = e >> 3, c4 = e & 7;
@@ -457,48 +427,13 @@ __global__ void k_tc_reduce(const double2* __restrict__ part, int nsys, int maxc
 
 // ----------------------------------------------------------------- host --
 
-// The operands of an orbital set (prepared once per set and ground state); the sets are told
-// apart by their offset arrays (the transposed blocks depend on which vectors a set takes)
-static TcRows& tc_rows_of(ikr_ctx* c, const OrbSet& set) {
-  if (set.off == c->d_phi_off.p) return c->tc_occ;
-  if (set.off == c->d_roff.p) return c->tc_rset;
-  IKR_REQUIRE(set.off == c->d_xoff.p, IKR_ERR_ARG, "tensor-core projections: unknown orbital set");
-  return c->tc_xset;
-}
-
-static void tc_prepare(ikr_ctx* c, const OrbSet& set, int nvec_total) {
-  TcRows& t = tc_rows_of(c, set);
-  if (t.ready && t.src == set.phi32) return;
-  const size_t n = (size_t)2 * nvec_total * 2 * c->ld;
-  t.hi.reserve(n);
-  t.lo.reserve(n);
-  const size_t work = (size_t)nvec_total * c->ld;
-  const int blocks = (int)std::min<size_t>((work + 255) / 256, (size_t)c->nsm * 16);
-  k_tc_rows<<<blocks, 256, 0, c->stream>>>(set.phi32, nvec_total, c->ld, t.hi.p, t.lo.p);
-  IKR_CUDA(cudaGetLastError());
-  // AT for the apply product (every set sharing this buffer uses the same maxcnt bound)
-  const int nk = (int)c->k.size();
-  t.mpad = (set.maxcnt + 1) & ~1;
-  const size_t nt = (size_t)nk * 2 * c->ld * 2 * t.mpad;
-  t.thi.reserve(nt);
-  t.tlo.reserve(nt);
-  const size_t wk = (size_t)nk * c->ld * t.mpad;
-  const int bl2 = (int)std::min<size_t>((wk + 255) / 256, (size_t)c->nsm * 16);
-  k_tc_cols<<<bl2, 256, 0, c->stream>>>(set.phi32, set.off, set.cnt, nk, c->ld, t.mpad, t.thi.p, t.tlo.p);
-  IKR_CUDA(cudaGetLastError());
-  t.ready = true;
-  t.src = set.phi32;
-}
-
 bool tc_proj_ok(ikr_ctx* c, const OrbSet& set) {
   return c->tc_proj && set.maxcnt >= 1 && (c->ld % 2) == 0;
 }
 
 void proj_coef_tc(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef,
-                  const OrbSet& set, int nvec_total) {
+                  const OrbSet& set) {
   IKR_REQUIRE(ldy % 2 == 0, IKR_ERR_ARG, "tensor-core projections need an even vector stride");
-  tc_prepare(c, set, nvec_total);
-  const TcRows& t = tc_rows_of(c, set);
   int maxns = 0, maxnb = 0;
   for (int v : L.kcount) maxns = std::max(maxns, v);
   for (auto& K : c->k) maxnb = std::max(maxnb, K.nb);
@@ -514,7 +449,7 @@ void proj_coef_tc(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const 
   const size_t smem = 2 * kTileBytes + 2 * (size_t)nt * kTK * 4 + 64;
   auto launch = [&](auto kern) {
     IKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, 128, smem, c->stream>>>(t.hi.p, t.lo.p, set.off, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p, Y,
+    kern<<<grid, 128, smem, c->stream>>>(set.phi32, set.off, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p, Y,
                                          ldy, c->ld, nmt, nch, set.maxcnt, active, part, c->tc_err.p);
   };
   if (nt == 32) launch(k_tc_coef<32>);
@@ -528,11 +463,7 @@ void proj_coef_tc(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const 
 }
 
 void proj_apply_tc(ikr_ctx* c, const SysList& L, const double2* coef, const float2* in, float alpha, float beta,
-                   float2* out, int ldy, const float2* dv, double* dpart, const int* active, const OrbSet& set,
-                   int nvec_total) {
-  tc_prepare(c, set, nvec_total);
-  const TcRows& t = tc_rows_of(c, set);
-  IKR_REQUIRE(t.mpad >= set.maxcnt, IKR_ERR_ARG, "tensor-core apply: transposed rows too short for the set");
+                   float2* out, int ldy, const float2* dv, double* dpart, const int* active, const OrbSet& set) {
   int maxns = 0;
   for (int v : L.kcount) maxns = std::max(maxns, v);
   const int nparts = (c->ld + 63) / 64;                           // 64 plane waves per tile and dot partial
@@ -544,9 +475,9 @@ void proj_apply_tc(ikr_ctx* c, const SysList& L, const double2* coef, const floa
   const size_t smem = 2 * kTileBytes + 2 * (size_t)nt * kTK * 4 + 16 + 32 * (size_t)nt;
   auto launch = [&](auto kern) {
     IKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, 128, smem, c->stream>>>(t.thi.p, t.tlo.p, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p, coef,
-                                         set.maxcnt, t.mpad, in, alpha, beta, out, ldy, c->ld, dv, dpart, nparts,
-                                         active, c->tc_err.p);
+    kern<<<grid, 128, smem, c->stream>>>(set.phi32, set.off, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p, coef,
+                                         set.maxcnt, in, alpha, beta, out, ldy, c->ld, dv, dpart, nparts, active,
+                                         c->tc_err.p);
   };
   if (nt == 32) launch(k_tc_apply<32>);
   else if (nt == 64) launch(k_tc_apply<64>);
