@@ -78,3 +78,21 @@ def test_tensor_core_projections_in_the_mixed_solve():
         ctx.set_tensor_cores(False)
     assert rep[0]["status"] == 0
     assert np.linalg.norm(b - response.dielectric(gs, x.cpu().numpy().reshape(s.dims))) <= 1e-8
+
+
+def test_tensor_cores_with_schur_sets_in_chi0():
+    """The Schur-complement solves project on [Phi Psi] and Psi: with the tensor
+    cores on, the mixed-precision chi0 of the metal still matches the oracle."""
+    from oracle import response
+    from workloads import perturbation
+    s, gs = system("tiny_metal"), oracle_state("tiny_metal")
+    from paper_2505_02319_gb300 import groundstate
+    ctx = groundstate.context_for(s, schur=True)
+    ctx.set_tensor_cores(True)
+    dV = perturbation(s)
+    nsys = ctx.groundstate_nsys
+    from paper_2505_02319_gb300 import ikr
+    d, _ = ctx.apply_chi0(dev(dV), tol=np.full(nsys, 1e-11), precision=ikr.MIXED)
+    ref = response.chi0(gs, dV)
+    assert np.linalg.norm(d.cpu().numpy() - ref.ravel()) < 1e-9 * np.linalg.norm(ref)
+    ctx.destroy()
