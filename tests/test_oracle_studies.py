@@ -14,14 +14,13 @@ same claims are in test_oracle_dyson.py and test_oracle_supercell.py.
    adaptive rules need fewer Hamiltonian applications than D10 and D100
    (eta_rel > 1) and reach tau on the preconditioned residual.
 """
-import dataclasses
 import os
 
 import numpy as np
 import pytest
 
 from oracle import groundstate as ogs, response as oresp, gmres as og
-from workloads import gaussian_sum_on_grid, make_system, perturbation, supercell, with_kgrid
+from workloads import make_system, perturbation, supercell, with_cutoff, with_kgrid
 
 pytestmark = [pytest.mark.slow,
               pytest.mark.skipif(not os.environ.get("IKR_STUDIES"), reason="set IKR_STUDIES=1 to run")]
@@ -29,15 +28,8 @@ pytestmark = [pytest.mark.slow,
 RULES = ("D10", "D100", "D10n", "agr", "bal", "grt", "grt_exact")
 
 
-def _refined(name, Ecut, n):
-    P0 = make_system(name)
-    dims = (n, n, n)
-    return dataclasses.replace(P0, Ecut=Ecut, dims=dims,
-                               V=gaussian_sum_on_grid(P0.lattice, dims, P0.positions, -P0.depth, P0.width))
-
-
 def test_supercell_study():
-    P = _refined("tiny_insulator", 20.0, 32)          # 148 grid points per bohr^3
+    P = with_cutoff(make_system("tiny_insulator"), 20.0, (32, 32, 32))   # 148 grid points per bohr^3
     center = P.lattice @ np.array([0.3, 0.6, 0.45])
     tau, m = 1e-9, 10
     agr = []
@@ -62,10 +54,7 @@ def test_supercell_study():
 
 
 def test_metallic_slab_study():
-    P0 = make_system("cfg3")
-    dims = (12, 12, 64)
-    P = dataclasses.replace(with_kgrid(P0, (2, 2, 1)), Ecut=2.5, dims=dims,
-                            V=gaussian_sum_on_grid(P0.lattice, dims, P0.positions, -P0.depth, P0.width))
+    P = with_cutoff(with_kgrid(make_system("cfg3"), (2, 2, 1)), 2.5, (12, 12, 64))
     gs = ogs.solve(P)
     kxc = oresp.exchange_kernel(gs.rho)
     b = oresp.chi0(gs, perturbation(P))

@@ -9,7 +9,9 @@ spheres, Fourier transforms, Hamiltonians, eigenpairs, occupations, densities,
 kernels, responses) is computed separately by each side.
 """
 from .systems import (System, make_system, perturbation, response_batch, loss_weights, CONFIGS,
-                      TEST_SYSTEMS, monkhorst_pack, gaussian_sum_on_grid, supercell, with_kgrid)
+                      TEST_SYSTEMS, monkhorst_pack, gaussian_sum_on_grid, supercell, with_kgrid,
+                      with_cutoff)
 
 __all__ = ["System", "make_system", "perturbation", "response_batch", "loss_weights", "CONFIGS",
-           "TEST_SYSTEMS", "monkhorst_pack", "gaussian_sum_on_grid", "supercell", "with_kgrid"]
+           "TEST_SYSTEMS", "monkhorst_pack", "gaussian_sum_on_grid", "supercell", "with_kgrid",
+           "with_cutoff"]

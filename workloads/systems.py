@@ -162,6 +162,14 @@ def with_kgrid(system: System, kgrid) -> System:
                                kgrid=tuple(int(l) for l in kgrid))
 
 
+def with_cutoff(system: System, Ecut: float, dims) -> System:
+    """The same atoms, k-points and counts at another cut-off and FFT grid (the
+    potential evaluated on the new grid), for reduced-size versions of a workload."""
+    dims = tuple(int(n) for n in dims)
+    V = gaussian_sum_on_grid(system.lattice, dims, system.positions, -system.depth, system.width)
+    return dataclasses.replace(system, name=f"{system.name}_E{Ecut:g}", Ecut=float(Ecut), dims=dims, V=V)
+
+
 def supercell(system: System, ell: int, axis: int = 0, kgrid=None) -> System:
     """The supercell of `ell` replicas of `system` along cell vector `axis`
     (the construction of Remark rmk:scaling): a_axis -> ell a_axis, N_axis ->
