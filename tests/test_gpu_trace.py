@@ -80,3 +80,32 @@ def test_cfg1_fp64_solve_follows_the_oracle(schur):
     tr = float(torch.linalg.norm(b - Ex))
     assert abs(tr - g["true_residual"]) <= 0.05 * g["true_residual"] + 1e-10
     ctx.destroy()
+
+
+def test_metallic_slab_kerker_solve_follows_the_oracle():
+    """The metallic slab at a reduced cut-off (cfg3's atoms, Ecut 2.5 Ha,
+    12 x 12 x 64, 2 x 2 x 1 k, N_occ,k 68-76), bal with the Kerker
+    preconditioner: the dphi^P and Fermi-level terms of the metal and the left
+    preconditioner T, trace against the oracle's."""
+    from oracle import response
+    from paper_2505_02319_gb300 import groundstate
+    from workloads import make_system, perturbation, with_cutoff, with_kgrid
+    g = _golden(os.path.join(os.path.dirname(GOLDEN), "slab_bal_kerker_fp64.txt"))
+    s = with_cutoff(with_kgrid(make_system("cfg3"), (2, 2, 1)), 2.5, (12, 12, 64))
+    ctx = groundstate.context_for(s)
+    nsys = ctx.groundstate_nsys
+    b, _ = ctx.apply_chi0(dev(perturbation(s)), tol=np.full(nsys, 1e-12))
+    b = (b / torch.linalg.norm(b)).contiguous()
+    alpha = 0.8
+    x, rep = ctx.solve_response(b, tau=1e-8, m=20, strategy="bal", kerker_alpha=alpha)
+    r = rep[0]
+    assert r["outer_iters"] == int(g["steps"]) and r["restarts"] == int(g["restarts"])
+    assert abs(r["n_ham"] - g["n_ham"]) <= 0.005 * g["n_ham"], (r["n_ham"], g["n_ham"])
+    hist, ref = np.array(r["history"]), np.array(g["history"])
+    assert len(hist) == len(ref)
+    assert np.all(np.abs(hist - ref) <= 1e-3 * ref + 1e-9), np.max(np.abs(hist - ref) / ref)
+    Ex, _ = ctx.apply_dielectric(x, tol=np.full(nsys, 1e-12))
+    res = (b - Ex).cpu().numpy().reshape(s.dims)
+    tr = float(np.linalg.norm(response.kerker(res, s.lattice, s.dims, alpha)))
+    assert tr <= 1e-8 and abs(tr - g["true_residual"]) <= 0.05 * g["true_residual"] + 1e-10
+    ctx.destroy()
