@@ -204,7 +204,7 @@ struct ikr_ctx {
   int zspan = 0;
   bool zreg_ok = false;
   // launch plan of the fused FP32 CG update (cg_fused.cu), for cgf_nsmax systems per k-point
-  int cgf_nsmax = -1, cgf_cs = 0, cgf_sl = 0, cgf_lds = 0;
+  int cgf_nsmax = -1, cgf_maxcnt = -1, cgf_cs = 0, cgf_sl = 0, cgf_lds = 0;
   size_t cgf_smem = 0;
   bool cgf_ok = false;
   ikr::FftPlan plan[3];

@@ -68,11 +68,6 @@ template <typename R> const R* kin_all_ptr(ikr_ctx* c);
 template <> inline const double* kin_all_ptr<double>(ikr_ctx* c) { return c->d_kin_all.p; }
 template <> inline const float* kin_all_ptr<float>(ikr_ctx* c) { return c->d_kin_all32.p; }
 
-// ops.cu
-// Fused FP32 CG update after the H_k application (cg_fused.cu): false when the
-// shape does not fit a thread-block cluster per k-point (then nothing is launched)
-bool launch_cg_fused(ikr_ctx* c, const SysList& L, float2* X, float2* Rv, float2* P, const float2* W, double* sys,
-                     int maxit, int* active, int* counter, int* list, const double* zpart, int nzf);
 // A set of orthonormal vectors per k-point for the projections, stored like the
 // occupied orbitals: vector j of k-point k at (off[k] + j) * ld, cnt[k] of them.
 // The projections use the occupied orbitals Phi_k unless another set is given.
@@ -86,6 +81,14 @@ struct OrbSet {
 OrbSet occ_set(ikr_ctx* c);     // Phi_k
 OrbSet schur_set(ikr_ctx* c);   // [Phi_k Psi_k]: the occupied and the extra computed bands
 OrbSet extra_set(ikr_ctx* c);   // Psi_k
+
+// ops.cu
+// Fused FP32 CG update after the H_k application (cg_fused.cu): false when the
+// shape does not fit a thread-block cluster per k-point (then nothing is launched)
+// set: project z on the complement of this orbital set (default: Phi_k)
+bool launch_cg_fused(ikr_ctx* c, const SysList& L, float2* X, float2* Rv, float2* P, const float2* W, double* sys,
+                     int maxit, int* active, int* counter, int* list, const double* zpart, int nzf,
+                     const OrbSet* set = nullptr);
 // FP32 projections (proj32.cu)
 int proj_chunks32();
 void proj_coef32(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef,

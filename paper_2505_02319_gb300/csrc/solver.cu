@@ -162,12 +162,12 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
     apply_nonlocal<R>(c, L, v.P, c->ld, v.W, act, w.dpart.p, zf_chunks(c, (int)sizeof(R)));
     bool fused = false;
     if constexpr (sizeof(R) == 4) {
-      if (!zset) {   // the fused kernel projects on Phi_k only
-        // alpha, x, r, stopping test, z = Q M^-1 r, beta and p in one launch
+      if (!c->tc_proj) {   // the fused kernel projects on the CUDA cores
+        // alpha, x, r, stopping test, z = Q M^-1 r (or R M^-1 r), beta and p in one launch
         ProfScope ps(c, kKidCgVec, 1);
         IKR_CUDA(cudaMemsetAsync(dcount, 0, sizeof(int), strm));
         fused = launch_cg_fused(c, L, v.X, v.R, v.P, v.W, sys, maxit, act, dcount, w.alist.p, w.dpart.p,
-                                zf_chunks(c, 4));
+                                zf_chunks(c, 4), zset);
       }
     }
     if (!fused) {
