@@ -52,6 +52,8 @@ def parse():
                         "10-bohr Gamma-point cell (cfg1) along a_1, e.g. 1,2,4,8")
     p.add_argument("--schur", action="store_true",
                    help="also time the bench solve with Schur-complement Sternheimer solves")
+    p.add_argument("--schur-bands", type=int, default=0,
+                   help="with --schur: also time it on a context with this many computed bands per k-point")
     p.add_argument("--tensor-cores", action="store_true",
                    help="also time the bench solve with the projections on the tensor cores")
     p.add_argument("--batch", action="store_true",
@@ -185,22 +187,35 @@ def timed(fn, stream):
     return out, e0.elapsed_time(e1) / 1e3
 
 
-def schur_run(ctx, b, nsys, opts, stream):
+def schur_run(ctx, b, nsys, opts, stream, nbands=0):
     """The bench solve with Schur-complement Sternheimer solves (the extra
-    computed bands split off), against the same solve without."""
+    computed bands split off), against the same solve without; with nbands,
+    also on a context holding that many computed bands per k-point."""
     import numpy as np
     import torch
     (x0, r0), t0 = timed(lambda: ctx.solve_response(b, opts=opts), stream)
-    ctx.set_schur(True)
-    try:
-        ctx.solve_response(b, opts=opts)                       # warm-up of the new shapes
-        (x1, r1), t1 = timed(lambda: ctx.solve_response(b, opts=opts), stream)
-        Ex, _ = ctx.apply_dielectric(x1, tol=np.full(nsys, 1e-12))
-        tr = float(torch.linalg.norm(b - Ex))
-    finally:
-        ctx.set_schur(False)
-    return {"time_s": t1, "time_s_plain": t0, "n_ham": r1[0]["n_ham"], "n_ham_plain": r0[0]["n_ham"],
-            "true_residual": tr, "rel_diff_vs_plain": float(torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0))}
+
+    def one(cx):
+        cx.set_schur(True)
+        try:
+            cx.solve_response(b, opts=opts)                    # warm-up of the new shapes
+            (x1, r1), t1 = timed(lambda: cx.solve_response(b, opts=opts), stream)
+            Ex, _ = cx.apply_dielectric(x1, tol=np.full(nsys, 1e-12))
+            tr = float(torch.linalg.norm(b - Ex))
+        finally:
+            cx.set_schur(False)
+        return {"time_s": t1, "n_ham": r1[0]["n_ham"], "n_ham_fp64": r1[0]["n_ham_fp64"], "true_residual": tr,
+                "rel_diff_vs_plain": float(torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0))}
+
+    out = {"time_s_plain": t0, "n_ham_plain": r0[0]["n_ham"], "bands": one(ctx)}
+    if nbands:
+        from paper_2505_02319_gb300 import groundstate
+        from workloads import make_system
+        cx = groundstate.context_for(make_system(WORKLOAD), nbands=nbands)
+        assert cx.groundstate_nsys == nsys
+        out[f"bands_{nbands}"] = one(cx)
+        cx.destroy()
+    return out
 
 
 def tensor_core_run(ctx, b, nsys, opts, stream):
@@ -506,7 +521,7 @@ def run_ours(args, rank, world, local_rank):
     if args.strategies:
         out["strategies"] = strategy_sweep(ctx, b, nsys, TAU, M, ikr.MIXED)
     if args.schur:
-        out["schur"] = schur_run(ctx, b, nsys, opts, stream)
+        out["schur"] = schur_run(ctx, b, nsys, opts, stream, args.schur_bands)
     if args.tensor_cores:
         out["tensor_cores"] = tensor_core_run(ctx, b, nsys, opts, stream)
     if args.batch:
