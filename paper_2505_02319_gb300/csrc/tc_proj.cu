@@ -158,15 +158,40 @@ __global__ void __launch_bounds__(128, 1)
   bool ok = true;
   uint32_t phase = 0;
   uint32_t acc = 0;
-  for (int kb = k0; kb < k1 && ok; kb += kTK) {
-    // A tiles from the orbitals: orbital mo of the tile gives row 2 mo = (Re, Im) and row
-    // 2 mo + 1 = (-Im, Re) of two plane waves per 16-byte group; orbitals past cnt are zero
-    // (the orbitals are zero past Nb_k, so a group across 2 Nb_k needs no mask)
-    for (int e = tid; e < (kTM / 2) * (kTK / 4); e += 128) {
-      const int mo = e >> 3, c4 = e & 7;
-      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+  // each thread's share of a stage, fetched into registers one stage ahead so that the
+  // global loads of stage kb + kTK overlap the MMAs of stage kb
+  constexpr int kAE = (kTM / 2) * (kTK / 4) / 128;   // A groups per thread (64 orbitals x 8)
+  constexpr int kBE = NT * (kTK / 4) / 128;          // B groups per thread
+  float4 ra[kAE], rb[kBE];
+  auto fetch = [&](int kb) {
+#pragma unroll
+    for (int j = 0; j < kAE; ++j) {
+      const int e = tid + 128 * j, mo = e >> 3, c4 = e & 7;
+      ra[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      // orbitals past cnt are zero; the orbitals are zero past Nb_k, so a group across
+      // 2 Nb_k needs no mask
       if (i0 / 2 + mo < cnt && kb + 4 * c4 < k1)
-        x = *reinterpret_cast<const float4*>(vbase + mo * lda + kb + 4 * c4);
+        ra[j] = *reinterpret_cast<const float4*>(vbase + mo * lda + kb + 4 * c4);
+    }
+#pragma unroll
+    for (int j = 0; j < kBE; ++j) {
+      const int e = tid + 128 * j, r = e >> 3, c4 = e & 7;
+      const int s = sbase + r, re = kb + 4 * c4;       // first real of the group (two plane waves)
+      rb[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (s0 + r < ns && (!active || active[s]) && re < k1) {
+        rb[j] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Y + (size_t)s * ldy) + re);
+        if (re + 2 >= k1) rb[j].z = rb[j].w = 0.f;      // second plane wave past Nb_k
+      }
+    }
+  };
+  fetch(k0);
+  for (int kb = k0; kb < k1 && ok; kb += kTK) {
+    // A tile: orbital mo gives row 2 mo = (Re, Im) and row 2 mo + 1 = (-Im, Re) of two plane
+    // waves per 16-byte group; B tile: the systems' vectors; both split into hi and lo
+#pragma unroll
+    for (int j = 0; j < kAE; ++j) {
+      const int e = tid + 128 * j, mo = e >> 3, c4 = e & 7;
+      const float4 x = ra[j];
       const float4 y = make_float4(-x.y, x.x, -x.w, x.z);
       const float4 xh = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
       const float4 yh = make_float4(tf32_hi(y.x), tf32_hi(y.y), tf32_hi(y.z), tf32_hi(y.w));
@@ -177,20 +202,13 @@ __global__ void __launch_bounds__(128, 1)
       *reinterpret_cast<float4*>(sAlo + core_off(2 * mo + 1, c4)) =
           make_float4(y.x - yh.x, y.y - yh.y, y.z - yh.z, y.w - yh.w);
     }
-    // B tiles: NT systems, split on the fly; reals past 2 Nb_k and inactive systems are zero
-    for (int e = tid; e < NT * (kTK / 4); e += 128) {
-      const int r = e >> 3, c4 = e & 7;
-      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-      const int s = sbase + r;
-      const int re = kb + 4 * c4;                       // first real of the group (two plane waves)
-      if (s0 + r < ns && (!active || active[s]) && re < k1) {
-        x = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Y + (size_t)s * ldy) + re);
-        if (re + 2 >= k1) x.z = x.w = 0.f;              // second plane wave past Nb_k
-      }
+#pragma unroll
+    for (int j = 0; j < kBE; ++j) {
+      const int e = tid + 128 * j, r = e >> 3, c4 = e & 7;
+      const float4 x = rb[j];
       const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
       *reinterpret_cast<float4*>(sBhi + core_off(r, c4)) = h;
-      *reinterpret_cast<float4*>(sBlo + core_off(r, c4)) =
-          make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      *reinterpret_cast<float4*>(sBlo + core_off(r, c4)) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
     }
     fence_async_smem();
     tc_fence_before();
@@ -210,6 +228,7 @@ __global__ void __launch_bounds__(128, 1)
       }
       mma_commit(bar);
     }
+    if (kb + kTK < k1) fetch(kb + kTK);
     // the MMAs read this stage's shared memory: wait before it is rewritten; the
     // outcome is made uniform so that no thread leaves the loop alone
     ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
