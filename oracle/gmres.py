@@ -18,7 +18,7 @@ import dataclasses
 
 import numpy as np
 
-from . import dft, response, schur
+from . import basis, dft, response, schur
 
 
 # ------------------------------------------------------------ plain GMRES ---
@@ -170,6 +170,24 @@ def dielectric_inexact(gs, v, tol_fn, kxc=None, schur_nbands=0):
     return v - nrm * c, nham
 
 
+def kernel_norm_bound(gs, kxc):
+    """||K|| <= max_{G != 0} 4 pi/|G|^2 + max_r |K^xc(r)| (K^H and K^xc symmetric)."""
+    G = basis.grid_G(gs.lattice, gs.dims)
+    g2 = np.sum(G * G, axis=-1)
+    return float(4.0 * np.pi / g2[g2 > 0].min() + np.abs(kxc).max())
+
+
+def dielectric_adjoint_inexact(gs, v, tol_fn, kxc, knorm, schur_nbands=0):
+    """E~^T v = v - ||v|| K chi0~(v/||v||) (the transpose of eq. op_discretised):
+    the Sternheimer error enters through K after chi0, so the tolerances take
+    ||K|| (its bound) where the forward application takes ||K v||."""
+    nrm = float(np.linalg.norm(v))
+    if nrm == 0.0:
+        return v.copy(), 0
+    c, nham = chi0_inexact(gs, v / nrm, tol_fn(knorm), kxc, schur_nbands)
+    return v - nrm * response.apply_K(c, gs, kxc), nham
+
+
 # ------------------------------------------------------------- strategies ---
 
 def systems(gs):
@@ -258,14 +276,16 @@ class InexactResult:
 
 
 def inexact_gmres(gs, b, tau, m, strategy, x0=None, s=1.0, kxc=None,
-                  max_restarts=20, track_errors=False, kerker_alpha=0.0, schur_nbands=0):
+                  max_restarts=20, track_errors=False, kerker_alpha=0.0, schur_nbands=0, adjoint=False):
     """Algorithm 1 with CG-solved Sternheimer equations (emulation on the CPU).
 
     kerker_alpha > 0: Algorithm 1 on the left-preconditioned system T E x = T b
     of eq. precond_dyson with the Kerker T of eq. kerker; the tolerance rules
     are unchanged (||T|| = 1, Lemma kerker_properties), the stopping rule and
     the reported residuals are those of T r, and b_norm stays ||b||.
-    schur_nbands > 0: Schur-complement Sternheimer solves (see chi0_inexact)."""
+    schur_nbands > 0: Schur-complement Sternheimer solves (see chi0_inexact).
+    adjoint: Algorithm 1 on E^T lambda = b (dielectric_adjoint_inexact, the
+    tolerance rules with ||K|| for ||K v_i||)."""
     if kxc is None:
         kxc = response.exchange_kernel(gs.rho)
     shape = b.shape
@@ -273,6 +293,16 @@ def inexact_gmres(gs, b, tau, m, strategy, x0=None, s=1.0, kxc=None,
 
     def T(v):
         return response.kerker(v, gs.lattice, gs.dims, kerker_alpha) if kerker_alpha > 0 else v
+
+    knorm = kernel_norm_bound(gs, kxc)
+
+    def apply_E(v, tol_fn):
+        if adjoint:
+            return dielectric_adjoint_inexact(gs, v, tol_fn, kxc, knorm, schur_nbands)
+        return dielectric_inexact(gs, v, tol_fn, kxc, schur_nbands)
+
+    def exact_E(v):
+        return response.dielectric_adjoint(gs, v, kxc) if adjoint else response.dielectric(gs, v, kxc)
     x0 = np.zeros_like(b) if x0 is None else x0.copy()
     est, sig = [], []
     nham = 0
@@ -284,10 +314,10 @@ def inexact_gmres(gs, b, tau, m, strategy, x0=None, s=1.0, kxc=None,
         if np.linalg.norm(x0) > 0:
             def tol0(kvn):
                 return cg_tolerances(gs, strategy, tau, 0, m, s, 1.0, kvn, b_norm)
-            Ex0, nh = dielectric_inexact(gs, x0, tol0, kxc, schur_nbands)
+            Ex0, nh = apply_E(x0, tol0)
             nham += nh
             if track_errors:
-                err0 = float(np.linalg.norm(T(Ex0 - response.dielectric(gs, x0, kxc))))
+                err0 = float(np.linalg.norm(T(Ex0 - exact_E(x0))))
             r0 = T(b - Ex0)
         else:
             r0 = T(b)
@@ -301,12 +331,11 @@ def inexact_gmres(gs, b, tau, m, strategy, x0=None, s=1.0, kxc=None,
         for i in range(1, m + 1):
             def toli(kvn, i=i, rprev=rprev):
                 return cg_tolerances(gs, strategy, tau, i, m, s, rprev, kvn, b_norm)
-            w, nh = dielectric_inexact(gs, V[-1].reshape(shape), toli, kxc, schur_nbands)
+            w, nh = apply_E(V[-1].reshape(shape), toli)
             nham += nh
             steps += 1
             if track_errors:
-                errs.append(float(np.linalg.norm(
-                    T(w - response.dielectric(gs, V[-1].reshape(shape), kxc)))))
+                errs.append(float(np.linalg.norm(T(w - exact_E(V[-1].reshape(shape))))))
             w = T(w).ravel()
             for j in range(i):                       # MGS Arnoldi
                 H[j, i - 1] = V[j] @ w

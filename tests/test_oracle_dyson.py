@@ -241,3 +241,24 @@ def test_adjoint_gradient_equals_finite_difference(metal, metal_E):
     h = 1e-3
     fd = (loss(dV + h * d) - loss(dV - h * d)) / (2 * h)
     assert abs(float(grad @ d.ravel()) - fd) <= 1e-9 * abs(fd)
+
+
+@pytest.mark.parametrize("which", ["ins", "metal"])
+def test_adjoint_algorithm_1_reaches_tau_with_the_kernel_bound(which, ins, metal):
+    """Algorithm 1 on E^T lambda = g (the adjoint solve of the differentiated
+    response) with the exact prefactor, ||K v_i|| replaced by the bound
+    ||K|| <= max 4 pi/|G|^2 + max |K^xc|: the true residual ||g - E^T lambda||
+    is <= tau, and lambda is the dense solution to that accuracy."""
+    s, gs = ins if which == "ins" else metal
+    g = response.chi0(gs, perturbation(s))
+    g /= np.linalg.norm(g)
+    tau = 1e-9
+    res = gmres.inexact_gmres(gs, g, tau, 10, "grt_exact", adjoint=True)
+    assert res.converged
+    assert np.linalg.norm(g - response.dielectric_adjoint(gs, res.x)) <= tau
+    # the bound dominates ||K v|| / ||v||, also for the smoothest vectors K^H amplifies most
+    kxc = response.exchange_kernel(gs.rho)
+    bound = gmres.kernel_norm_bound(gs, kxc)
+    rng = np.random.default_rng(5)
+    for v in list(rng.normal(size=(4,) + s.dims)) + [g]:
+        assert np.linalg.norm(response.apply_K(v, gs, kxc)) <= bound * np.linalg.norm(v)
