@@ -537,11 +537,21 @@ void set_eigenpairs(ikr_ctx* c, const ikr_eigenpairs* eig) {
     IKR_CUDA(cudaStreamSynchronize(st));
     double kmax = 0.0, g2min = 1e300;
     for (double v : kx) kmax = std::max(kmax, std::fabs(v));
+    // the smallest nonzero |G|^2 over the grid frequencies K^H acts on (for an oblique
+    // cell a combination of reciprocal vectors can be shorter than each of them)
     const double* B = c->recip;
-    for (int i = 0; i < 3; ++i) {
-      const double bi2 = B[i] * B[i] + B[3 + i] * B[3 + i] + B[6 + i] * B[6 + i];
-      g2min = std::min(g2min, bi2);
-    }
+    for (int a = 0; a < c->N[0]; ++a)
+      for (int b = 0; b < c->N[1]; ++b)
+        for (int d = 0; d < c->N[2]; ++d) {
+          const int j[3] = {signed_index(a, c->N[0]), signed_index(b, c->N[1]), signed_index(d, c->N[2])};
+          if (j[0] == 0 && j[1] == 0 && j[2] == 0) continue;
+          double g2 = 0.0;
+          for (int r = 0; r < 3; ++r) {
+            const double gr = B[3 * r] * j[0] + B[3 * r + 1] * j[1] + B[3 * r + 2] * j[2];
+            g2 += gr * gr;
+          }
+          g2min = std::min(g2min, g2);
+        }
     c->knorm = 4.0 * M_PI / g2min + kmax;
   }
   // ||F_k^-1 Phi_k||_{2,inf} and ||Re F_k^-1 Phi_k||_{2,inf} per k-point (largest
