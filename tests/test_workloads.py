@@ -17,3 +17,17 @@ def test_displacement_is_potential_derivative():
         Vp = gaussian_sum_on_grid(s.lattice, s.dims, pos_p, -s.depth, s.width)
         Vm = gaussian_sum_on_grid(s.lattice, s.dims, pos_m, -s.depth, s.width)
         np.testing.assert_allclose(dV, (Vp - Vm) / (2 * h), atol=1e-7)
+
+
+def test_with_cutoff_keeps_the_atoms_and_resamples_the_potential():
+    import numpy as np
+    from workloads import gaussian_sum_on_grid, make_system, with_cutoff
+    s = make_system("tiny_ortho_k")
+    r = with_cutoff(s, 6.0, (20, 24, 32))
+    assert r.dims == (20, 24, 32) and r.Ecut == 6.0
+    assert np.array_equal(r.positions, s.positions) and np.array_equal(r.kpoints, s.kpoints)
+    assert (r.n_electrons, r.nbands, r.temperature) == (s.n_electrons, s.nbands, s.temperature)
+    direct = gaussian_sum_on_grid(s.lattice, (20, 24, 32), s.positions, -s.depth, s.width)
+    assert np.array_equal(r.V, direct)
+    # the coarse grid's points are a subset of the fine one's: the potential agrees there
+    assert np.allclose(r.V[::2, ::2, ::2], s.V, atol=1e-12)
