@@ -446,6 +446,14 @@ __global__ void k_tc_reduce(const double2* __restrict__ part, int nsys, int maxc
 
 // ----------------------------------------------------------------- host --
 
+// the error flag of the tensor-core kernels: set by any launch whose wait ran out,
+// cleared only when it is created and by tc_check, so no later launch hides it
+static void tc_flag_ready(ikr_ctx* c) {
+  if (c->tc_err.p) return;
+  c->tc_err.reserve(1);
+  IKR_CUDA(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+}
+
 bool tc_proj_ok(ikr_ctx* c, const OrbSet& set) {
   return c->tc_proj && set.maxcnt >= 1 && (c->ld % 2) == 0;
 }
@@ -462,8 +470,7 @@ void proj_coef_tc(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const 
   const int nnt = (maxns + nt - 1) / nt;
   c->ws.cpart.reserve((size_t)nch * L.n * set.maxcnt * 2);
   double2* part = reinterpret_cast<double2*>(c->ws.cpart.p);
-  c->tc_err.reserve(1);
-  IKR_CUDA(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+  tc_flag_ready(c);
   dim3 grid(nch, (unsigned)c->k.size(), (unsigned)(nmt * std::max(nnt, 1)));
   const size_t smem = 2 * kTileBytes + 2 * (size_t)nt * kTK * 4 + 64;
   auto launch = [&](auto kern) {
@@ -488,8 +495,7 @@ void proj_apply_tc(ikr_ctx* c, const SysList& L, const double2* coef, const floa
   const int nparts = (c->ld + 63) / 64;                           // 64 plane waves per tile and dot partial
   const int nt = maxns <= 32 ? 32 : (maxns <= 64 ? 64 : 128);
   const int nnt = std::max(1, (maxns + nt - 1) / nt);
-  c->tc_err.reserve(1);
-  IKR_CUDA(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+  tc_flag_ready(c);
   dim3 grid(nparts, (unsigned)c->k.size(), (unsigned)nnt);
   const size_t smem = 2 * kTileBytes + 2 * (size_t)nt * kTK * 4 + 16 + 32 * (size_t)nt;
   auto launch = [&](auto kern) {
@@ -509,6 +515,7 @@ void tc_check(ikr_ctx* c) {
   int e = 0;
   IKR_CUDA(cudaMemcpyAsync(&e, c->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   IKR_CUDA(cudaStreamSynchronize(c->stream));
+  if (e != 0) IKR_CUDA(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
   IKR_REQUIRE(e == 0, IKR_ERR_TIMEOUT, "tensor-core projection: an mbarrier wait ran out");
 }
 
