@@ -290,6 +290,7 @@ void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::
     float2* b1b = reinterpret_cast<float2*>(w.b1b.p);
     launch_z_inverse<float>(c, L, w.X32.p, ld, nullptr, b1b);
     launch_density<float>(c, n, c->d_b1phi32.p, b1b, w.ca.p, w.cb.p, drho, 1.0 / c->volume, c->d_psir32.p);
+    if (c->tc_proj) tc_check(c);
     return;
   }
   // y_s = F(u . F^-1 phi_s): plane pass on the cached real-space orbitals
@@ -314,6 +315,7 @@ void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::
   occupation_response(c, w.deps.p, w.ca.p, w.cb.p, w.scal.p + 8);
   launch_z_inverse<double>(c, L, w.X.p, ld, nullptr, w.b1b.p);
   launch_density<double>(c, n, c->d_b1phi.p, w.b1b.p, w.ca.p, w.cb.p, drho, 1.0 / c->volume, c->d_psir.p);
+  if (c->tc_proj) tc_check(c);   // the tensor-core products after the last CG of this application
 }
 
 // Ev = v - ||Kv|| chi0(Kv/||Kv||)  (eq. op_discretised).  tol_fn receives ||Kv||.
