@@ -186,6 +186,7 @@ void dielectric_batch(ikr_ctx* c, std::vector<BatchItem>& items, int maxit, int 
   }
   IKR_CUDA(cudaMemcpyAsync(hn.data(), w.bnrm.p, sizeof(double) * 8 * nr, cudaMemcpyDeviceToHost, st));
   IKR_CUDA(cudaStreamSynchronize(st));
+  if (c->tc_proj) tc_check(c);
   for (int j = 0; j < nl; ++j) {
     const int r = live[j];
     RunStats& rs = *items[r].rs;
