@@ -237,6 +237,10 @@ __global__ void __launch_bounds__(128, 1)
   }
   if (!ok) {
     if (lane == 0) atomicExch(err, 1);
+    // a second bounded wait for the MMAs still in flight before their tensor memory is freed
+    // (the phase was flipped after the failed wait)
+    mbar_wait(bar, phase ^ 1);
+    __syncthreads();
   } else {
     // epilogue: lanes 32 w .. 32 w + 31 of tensor memory are rows i0 + 32 w + lane of D
     const int r = 32 * warp + lane;
@@ -369,6 +373,10 @@ __global__ void __launch_bounds__(128, 1)
   }
   if (!ok) {
     if (lane == 0) atomicExch(err, 1);
+    // a second bounded wait for the MMAs still in flight before their tensor memory is freed
+    // (the phase was flipped after the failed wait)
+    mbar_wait(bar, phase ^ 1);
+    __syncthreads();
   } else {
     const int row = r0 + 32 * warp + lane;                         // 2 g + c
     const int g = row >> 1;
