@@ -50,6 +50,15 @@ def parse():
     p.add_argument("--supercell", default=None, metavar="L1,L2,...",
                    help="also run the supercell-size study of Remark rmk:scaling on replicas of the "
                         "10-bohr Gamma-point cell (cfg1) along a_1, e.g. 1,2,4,8")
+    p.add_argument("--schur", action="store_true",
+                   help="also time the bench solve with Schur-complement Sternheimer solves")
+    p.add_argument("--schur-bands", type=int, default=0,
+                   help="with --schur: also time it on a context with this many computed bands per k-point")
+    p.add_argument("--tensor-cores", action="store_true",
+                   help="also time the bench solve with the projections on the tensor cores")
+    p.add_argument("--batch", action="store_true",
+                   help="also time the batched workload: 32 perturbations of the 10-bohr cell (cfg1), "
+                        "lockstep against one after another")
     p.add_argument("--slab-strategies", action="store_true",
                    help="also run every tolerance rule on the full-size metallic slab (cfg3) with Kerker")
     p.add_argument("--cfg4-guaranteed", action="store_true",
@@ -165,6 +174,101 @@ def strategy_sweep(ctx, b, nsys, tau, m, precision):
     return out
 
 
+def timed(fn, stream):
+    """(result, seconds) of fn() between CUDA events on the stream."""
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1) / 1e3
+
+
+def schur_run(ctx, b, nsys, opts, stream, nbands=0):
+    """The bench solve with Schur-complement Sternheimer solves (the extra
+    computed bands split off), against the same solve without; with nbands,
+    also on a context holding that many computed bands per k-point."""
+    import numpy as np
+    import torch
+    (x0, r0), t0 = timed(lambda: ctx.solve_response(b, opts=opts), stream)
+
+    def one(cx):
+        cx.set_schur(True)
+        try:
+            cx.solve_response(b, opts=opts)                    # warm-up of the new shapes
+            (x1, r1), t1 = timed(lambda: cx.solve_response(b, opts=opts), stream)
+            Ex, _ = cx.apply_dielectric(x1, tol=np.full(nsys, 1e-12))
+            tr = float(torch.linalg.norm(b - Ex))
+        finally:
+            cx.set_schur(False)
+        return {"time_s": t1, "n_ham": r1[0]["n_ham"], "n_ham_fp64": r1[0]["n_ham_fp64"], "true_residual": tr,
+                "rel_diff_vs_plain": float(torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0))}
+
+    out = {"time_s_plain": t0, "n_ham_plain": r0[0]["n_ham"], "bands": one(ctx)}
+    if nbands:
+        from paper_2505_02319_gb300 import groundstate
+        from workloads import make_system
+        cx = groundstate.context_for(make_system(WORKLOAD), nbands=nbands)
+        assert cx.groundstate_nsys == nsys
+        out[f"bands_{nbands}"] = one(cx)
+        cx.destroy()
+    return out
+
+
+def tensor_core_run(ctx, b, nsys, opts, stream):
+    """The bench solve with the FP32 projection products on the tensor cores
+    (tcgen05), against the same solve on the CUDA cores."""
+    import numpy as np
+    import torch
+    (x0, r0), t0 = timed(lambda: ctx.solve_response(b, opts=opts), stream)
+    ctx.set_tensor_cores(True)
+    try:
+        ctx.solve_response(b, opts=opts)
+        (x1, r1), t1 = timed(lambda: ctx.solve_response(b, opts=opts), stream)
+        Ex, _ = ctx.apply_dielectric(x1, tol=np.full(nsys, 1e-12))
+        tr = float(torch.linalg.norm(b - Ex))
+    finally:
+        ctx.set_tensor_cores(False)
+    return {"time_s": t1, "time_s_cuda_cores": t0, "n_ham": r1[0]["n_ham"], "n_ham_cuda_cores": r0[0]["n_ham"],
+            "true_residual": tr, "rel_diff_vs_cuda_cores": float(torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0))}
+
+
+def batch_run(tau, m, stream):
+    """cfg5: the 32 perturbations of the 10-bohr Gamma-point cell (16 Gaussian
+    bumps, 16 atom displacements), b_r = chi0 dV_r / ||chi0 dV_r||, solved in
+    lockstep (one CG per round over all 32 x 4 Sternheimer systems) and one
+    after another; mixed precision, bal, tau = 1e-8."""
+    import numpy as np
+    import torch
+    from paper_2505_02319_gb300 import groundstate
+    from workloads import make_system, response_batch
+    s = make_system("cfg1")
+    ctx = groundstate.context_for(s, eigensolver="chfsi")
+    nsys = ctx.groundstate_nsys
+    dvs = response_batch(s)
+    b = torch.stack([ctx.apply_chi0(torch.tensor(dv.ravel(), device="cuda"), tol=np.full(nsys, 1e-12))[0]
+                     for dv in dvs])
+    b = (b / torch.linalg.norm(b, dim=1, keepdim=True)).contiguous()
+    kw = dict(tau=tau, m=m, strategy="bal", precision="mixed")
+    ctx.solve_response(b[:2], **kw)
+    (xb, rb), tb = timed(lambda: ctx.solve_response(b, **kw), stream)
+    os.environ["IKR_BATCH"] = "0"
+    try:
+        (xs, rs), ts = timed(lambda: ctx.solve_response(b, **kw), stream)
+    finally:
+        del os.environ["IKR_BATCH"]
+    res = []
+    for r in range(b.shape[0]):
+        Ex, _ = ctx.apply_dielectric(xb[r].contiguous(), tol=np.full(nsys, 1e-12))
+        res.append(float(torch.linalg.norm(b[r] - Ex)))
+    ctx.destroy()
+    return {"workload": "cfg1 cell, 32 right-hand sides (16 bumps, 16 displacements), 128 systems per round",
+            "time_s_lockstep": tb, "time_s_one_by_one": ts, "speedup": ts / tb,
+            "n_ham_lockstep": int(sum(r["n_ham"] for r in rb)), "n_ham_one_by_one": int(sum(r["n_ham"] for r in rs)),
+            "max_true_residual": max(res), "tau": tau}
 def _rule_run(ctx, b, nsys, rule, tau, m, precision, alpha=0.0):
     """One solve with one tolerance rule: time, N_ham, the solver's residual
     estimate (of T r with Kerker) and the true unpreconditioned residual
@@ -416,6 +520,12 @@ def run_ours(args, rank, world, local_rank):
     }
     if args.strategies:
         out["strategies"] = strategy_sweep(ctx, b, nsys, TAU, M, ikr.MIXED)
+    if args.schur:
+        out["schur"] = schur_run(ctx, b, nsys, opts, stream, args.schur_bands)
+    if args.tensor_cores:
+        out["tensor_cores"] = tensor_core_run(ctx, b, nsys, opts, stream)
+    if args.batch:
+        out["batch"] = batch_run(TAU, M, stream)
     if args.slab_strategies:
         out["slab_strategies"] = slab_strategies(TAU, M)
     if args.cfg4_guaranteed:

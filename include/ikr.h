@@ -188,6 +188,47 @@ ikr_status ikr_set_nonlocal(ikr_ctx* ctx, int ncentres, const double* centres, c
 ikr_status ikr_compute_eigenpairs(ikr_ctx* ctx, int nbands, double tol, int maxit, int degree, double* eigenvalues,
                                   int* iters, double* max_residual, cudaStream_t stream);
 
+/* Schur-complement Sternheimer solves (Sec. 3.4.2 and Sec. 4.1.2, where the
+ * paper uses them in all experiments).  enable = 1: every chi0 application
+ * (ikr_apply_chi0, ikr_apply_dielectric and its adjoint, ikr_solve_response
+ * and its adjoint) solves Q(H_k - eps_n)Q x = b with the extra computed bands
+ * Psi_k = bands N_occ,k + 1 .. nbands of the eigenpairs split off:
+ *   x = Psi a + y,  a = (lambda - eps_n)^-1 Psi^H b,  CG on R(H_k - eps_n)R y = R b,
+ *   R = 1 - [Phi Psi][Phi Psi]^H,
+ * which has the same solution and a larger smallest eigenvalue
+ * (eps_{nbands+1} - eps_n instead of eps_{Nocc+1} - eps_n).  The terms of the
+ * complement in W = R H Psi are dropped: for Rayleigh-Ritz pairs W is the
+ * size of their residual.  enable = 0 restores the plain projected CG.
+ * ikr_solve_sternheimer is not affected.  IKR_ERR_STATE before the eigenpairs
+ * are set (setting new eigenpairs disables it again). */
+ikr_status ikr_set_schur(ikr_ctx* ctx, int enable);
+
+/* The FP32 projection products (eq. discretised_sternheimer: M = Phi^H Y, and
+ * the Q-projection Y - Phi (Phi^H Y) of every FP32 CG iteration), both V_k^H Y
+ * and Y - V_k C, on the 5th-generation tensor cores: tcgen05 MMAs of
+ * kind::tf32 with each operand split into a TF32 high part and the remainder
+ * (three products, FP32 accumulation in tensor memory); V_k^H Y split-K over
+ * thread blocks with a fixed-order reduction of the chunk partials.
+ * enable = 0 returns to the CUDA-core kernels.  IKR_ERR_STATE before the eigenpairs are set.  A
+ * tensor-core launch whose internal wait runs out makes the calling solve
+ * return IKR_ERR_TIMEOUT. */
+ikr_status ikr_set_tensor_cores(ikr_ctx* ctx, int enable);
+
+/* c[s][m] = <phi_m,k, y_s> for the occupied orbitals of k-point k (the
+ * coefficient product of eq. discretised_sternheimer, M = Phi_k^H Y) in FP32
+ * arithmetic: method 0 on the CUDA cores, 1 on the tensor cores (as
+ * ikr_set_tensor_cores).  y: DEVICE, Nb_k x nvec complex64, column-major
+ * (vector s at s * Nb_k); c: HOST, nvec x N_occ,k complex128 (row s).
+ * IKR_ERR_ARG for a bad k, nvec < 1 or NULL pointers; IKR_ERR_TIMEOUT as above. */
+ikr_status ikr_projection_coefficients(ikr_ctx* ctx, int k, int nvec, const void* y, int method, double* c,
+                                       cudaStream_t stream);
+
+/* y <- Q_k y = y - Phi_k (Phi_k^H y), the projector of eq.
+ * discretised_sternheimer, in FP32 arithmetic: method 0 on the CUDA cores, 1
+ * on the tensor cores.  y: DEVICE, Nb_k x nvec complex64, column-major,
+ * overwritten.  Errors as ikr_projection_coefficients. */
+ikr_status ikr_project_out(ikr_ctx* ctx, int k, int nvec, void* y, int method, cudaStream_t stream);
+
 /* Host utility (no GPU): eigenvalues w (ascending, n) and eigenvectors v
  * (column j = eigenvector of w[j]; row-major n x n complex, interleaved) of the
  * Hermitian matrix a (row-major n x n complex, interleaved), by the cyclic
@@ -272,8 +313,14 @@ ikr_status ikr_apply_dielectric(ikr_ctx* ctx, const double* v, double* Ev, const
  * to ||b - E x|| <= tau, choosing every CG tolerance by opts->strategy
  * (Theorem inexact_gmres_dyson, Table strategies).  With kerker_alpha > 0 the
  * left-preconditioned system T E x = T b (eq. precond_dyson) is solved.
- * b, x: DEVICE, nrhs x Ng doubles (right-hand sides solved one after another);
- * x holds x0 on input if opts->use_x0.  report: host array of nrhs (may be NULL).
+ * b, x: DEVICE, nrhs x Ng doubles; x holds x0 on input if opts->use_x0.
+ * report: host array of nrhs (may be NULL).
+ * nrhs > 1: the right-hand sides advance in lockstep, each with its own GMRES
+ * state and tolerances; the E applications of one round share one batched CG
+ * over all their Sternheimer systems, and their right-hand-side and density
+ * passes are FP64-accurate (the FP32 E applications of late steps are not
+ * used).  Each solution meets its own tau.  The environment variable
+ * IKR_BATCH=0 solves them one after another instead.
  * Returns IKR_ERR_NOCONV (best iterate in x) if max_restarts is exceeded. */
 ikr_status ikr_solve_response(ikr_ctx* ctx, int nrhs, const double* b, double* x,
                               const ikr_solve_opts* opts, ikr_report* report,

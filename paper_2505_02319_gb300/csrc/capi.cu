@@ -1,5 +1,6 @@
 // extern "C" entry points (include/ikr.h).  Each wraps the C++ implementation,
 // turns exceptions into status codes and records the message in the context.
+#include <cstdlib>
 #include <cstring>
 #include <chrono>
 #include <cmath>
@@ -71,6 +72,17 @@ ikr_status solve_any(ikr_ctx* c, int nrhs, const double* b, double* x, const ikr
     IKR_REQUIRE(o.strategy >= IKR_AGR && o.strategy <= IKR_FIXED, IKR_ERR_ARG, "unknown strategy");
     IKR_REQUIRE(o.precision == IKR_FP64 || o.precision == IKR_MIXED, IKR_ERR_ARG, "unknown precision");
     IKR_REQUIRE(o.cg_maxit >= 1, IKR_ERR_ARG, "cg_maxit must be >= 1");
+    const char* env = std::getenv("IKR_BATCH");
+    if (nrhs > 1 && !(env && env[0] == '0')) {
+      try {
+        gmres_solve_batch(c, nrhs, b, x, o, report, adjoint);
+      } catch (const Error& e) {
+        if (e.status != IKR_ERR_NOCONV && e.status != IKR_ERR_TIMEOUT) throw;
+        c->err = e.what();
+        worst = e.status;
+      }
+      return;
+    }
     for (int r = 0; r < nrhs; ++r) {
       ikr_report* rep = report ? report + r : nullptr;
       try {
@@ -140,6 +152,90 @@ ikr_status ikr_set_nonlocal(ikr_ctx* c, int ncentres, const double* centres, con
     IKR_REQUIRE(!c->have_gs, IKR_ERR_STATE, "set the nonlocal part before the eigenpairs");
     set_nonlocal(c, ncentres, centres, sigma, D);
   });
+}
+
+ikr_status ikr_set_schur(ikr_ctx* c, int enable) {
+  if (!c) return IKR_ERR_ARG;
+  return guarded(c, [&] {
+    IKR_REQUIRE(c->have_gs, IKR_ERR_STATE, "the ground state is not set");
+    IKR_REQUIRE(c->xmax >= 1, IKR_ERR_ARG, "no extra computed bands above N_occ,k");
+    c->schur = enable != 0;
+  });
+}
+
+ikr_status ikr_set_tensor_cores(ikr_ctx* c, int enable) {
+  if (!c) return IKR_ERR_ARG;
+  return guarded(c, [&] {
+    IKR_REQUIRE(c->have_gs, IKR_ERR_STATE, "the ground state is not set");
+    c->tc_proj = enable != 0;
+  });
+}
+
+ikr_status ikr_projection_coefficients(ikr_ctx* c, int k, int nvec, const void* y, int method, double* coef,
+                                       cudaStream_t stream) {
+  if (!c) return IKR_ERR_ARG;
+  c->stream = stream;
+  const bool old = c->tc_proj;
+  ikr_status s = guarded(c, [&] {
+    IKR_REQUIRE(c->have_gs, IKR_ERR_STATE, "the ground state is not set");
+    IKR_REQUIRE(k >= 0 && k < (int)c->k.size() && nvec >= 1 && y && coef, IKR_ERR_ARG, "invalid arguments");
+    IKR_REQUIRE(method == 0 || method == 1, IKR_ERR_ARG, "method must be 0 or 1");
+    const KPoint& K = c->k[k];
+    std::vector<int> kof(nvec, k), band(nvec, 0);
+    SysList L;
+    make_syslist(c, L, nvec, kof.data(), band.data());
+    ensure_workspace(c, nvec);
+    Workspace& w = c->ws;
+    const int ld = c->ld;
+    IKR_CUDA(cudaMemsetAsync(w.Z32.p, 0, sizeof(float2) * (size_t)nvec * ld, stream));
+    IKR_CUDA(cudaMemcpy2DAsync(w.Z32.p, sizeof(float2) * ld, y, sizeof(float2) * K.nb, sizeof(float2) * K.nb, nvec,
+                               cudaMemcpyDeviceToDevice, stream));
+    c->tc_proj = method == 1;
+    double2* cf = reinterpret_cast<double2*>(w.coef.p);
+    proj_coef<float>(c, L, w.Z32.p, ld, nullptr, cf);
+    if (c->tc_proj) tc_check(c);
+    std::vector<double2> h((size_t)nvec * std::max(c->noccmax, 1));
+    IKR_CUDA(cudaMemcpyAsync(h.data(), cf, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, stream));
+    IKR_CUDA(cudaStreamSynchronize(stream));
+    for (int q = 0; q < nvec; ++q)
+      for (int m = 0; m < K.nocc; ++m) {
+        coef[2 * ((size_t)q * K.nocc + m)] = h[(size_t)q * c->noccmax + m].x;
+        coef[2 * ((size_t)q * K.nocc + m) + 1] = h[(size_t)q * c->noccmax + m].y;
+      }
+  });
+  c->tc_proj = old;
+  return s;
+}
+
+ikr_status ikr_project_out(ikr_ctx* c, int k, int nvec, void* y, int method, cudaStream_t stream) {
+  if (!c) return IKR_ERR_ARG;
+  c->stream = stream;
+  const bool old = c->tc_proj;
+  ikr_status s = guarded(c, [&] {
+    IKR_REQUIRE(c->have_gs, IKR_ERR_STATE, "the ground state is not set");
+    IKR_REQUIRE(k >= 0 && k < (int)c->k.size() && nvec >= 1 && y, IKR_ERR_ARG, "invalid arguments");
+    IKR_REQUIRE(method == 0 || method == 1, IKR_ERR_ARG, "method must be 0 or 1");
+    const KPoint& K = c->k[k];
+    std::vector<int> kof(nvec, k), band(nvec, 0);
+    SysList L;
+    make_syslist(c, L, nvec, kof.data(), band.data());
+    ensure_workspace(c, nvec);
+    Workspace& w = c->ws;
+    const int ld = c->ld;
+    IKR_CUDA(cudaMemsetAsync(w.Z32.p, 0, sizeof(float2) * (size_t)nvec * ld, stream));
+    IKR_CUDA(cudaMemcpy2DAsync(w.Z32.p, sizeof(float2) * ld, y, sizeof(float2) * K.nb, sizeof(float2) * K.nb, nvec,
+                               cudaMemcpyDeviceToDevice, stream));
+    c->tc_proj = method == 1;
+    double2* cf = reinterpret_cast<double2*>(w.coef.p);
+    proj_coef<float>(c, L, w.Z32.p, ld, nullptr, cf);
+    proj_apply<float>(c, L, cf, w.Z32.p, 1.0f, -1.0f, w.Z32.p, ld, nullptr, nullptr, nullptr);
+    if (c->tc_proj) tc_check(c);
+    IKR_CUDA(cudaMemcpy2DAsync(y, sizeof(float2) * K.nb, w.Z32.p, sizeof(float2) * ld, sizeof(float2) * K.nb, nvec,
+                               cudaMemcpyDeviceToDevice, stream));
+    IKR_CUDA(cudaStreamSynchronize(stream));
+  });
+  c->tc_proj = old;
+  return s;
 }
 
 ikr_status ikr_compute_eigenpairs(ikr_ctx* c, int nbands, double tol, int maxit, int degree, double* eigenvalues,

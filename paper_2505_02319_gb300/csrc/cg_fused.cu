@@ -349,10 +349,10 @@ struct FusedPlan {
   size_t smem = 0;
 };
 
-FusedPlan plan_fused(ikr_ctx* c, const SysList& L) {
+FusedPlan plan_fused(ikr_ctx* c, const SysList& L, int maxcnt) {
   FusedPlan p;
   for (int v : L.kcount) p.nsmax = std::max(p.nsmax, v);
-  if (c->cgf_nsmax == p.nsmax) {   // planned before for this shape
+  if (c->cgf_nsmax == p.nsmax && c->cgf_maxcnt == maxcnt) {   // planned before for this shape
     p.ok = c->cgf_ok;
     p.cs = c->cgf_cs;
     p.sl = c->cgf_sl;
@@ -361,8 +361,9 @@ FusedPlan plan_fused(ikr_ctx* c, const SysList& L) {
     return p;
   }
   c->cgf_nsmax = p.nsmax;
+  c->cgf_maxcnt = maxcnt;
   c->cgf_ok = false;
-  if (p.nsmax == 0 || p.nsmax > 64 || c->noccmax > 64) return p;
+  if (p.nsmax == 0 || p.nsmax > 64 || maxcnt > 64) return p;
   // IKR_CG_FUSED=0 selects the unfused sequence of kernels (read when a context plans)
   if (const char* e = std::getenv("IKR_CG_FUSED"))
     if (e[0] == '0') return p;
@@ -378,7 +379,7 @@ FusedPlan plan_fused(ikr_ctx* c, const SysList& L) {
     const int sl = (c->ld + cs - 1) / cs;
     if (sl > 32 * kFU) continue;
     const int lds = sl | 1;
-    const CgFusedLayout lay(p.nsmax, c->noccmax, lds);
+    const CgFusedLayout lay(p.nsmax, maxcnt, lds);
     if (lay.total > (size_t)max_optin) continue;
     if (cs > 8) IKR_CUDA(cudaFuncSetAttribute(k_cg_fused, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     IKR_CUDA(cudaFuncSetAttribute(k_cg_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
@@ -422,22 +423,24 @@ FusedPlan plan_fused(ikr_ctx* c, const SysList& L) {
 
 }  // namespace
 
-bool cg_fused_available(ikr_ctx* c, const SysList& L) { return plan_fused(c, L).ok; }
+bool cg_fused_available(ikr_ctx* c, const SysList& L) { return plan_fused(c, L, c->noccmax).ok; }
 
 bool launch_cg_fused(ikr_ctx* c, const SysList& L, float2* X, float2* Rv, float2* P, const float2* W, double* sys,
-                     int maxit, int* active, int* counter, int* list, const double* zpart, int nzf) {
-  const FusedPlan p = plan_fused(c, L);
+                     int maxit, int* active, int* counter, int* list, const double* zpart, int nzf,
+                     const OrbSet* set) {
+  const OrbSet os = set ? *set : occ_set(c);
+  const FusedPlan p = plan_fused(c, L, os.maxcnt);
   if (!p.ok) return false;
   CgFusedArgs a;
   a.X = X;
   a.Rv = Rv;
   a.P = P;
   a.W = W;
-  a.phi_all = c->d_phi_all32.p;
-  a.phi_off = c->d_phi_off.p;
+  a.phi_all = os.phi32;
+  a.phi_off = os.off;
   a.kin_all = c->d_kin_all32.p;
   a.nb_k = c->d_nb.p;
-  a.nocc_k = c->d_nocc.p;
+  a.nocc_k = os.cnt;
   a.kstart = L.d_kstart.p;
   a.kcount = L.d_kcount.p;
   a.sys = sys;
@@ -452,7 +455,7 @@ bool launch_cg_fused(ikr_ctx* c, const SysList& L, float2* X, float2* Rv, float2
   a.sl = p.sl;
   a.lds = p.lds;
   a.nsmax = p.nsmax;
-  a.noccmax = c->noccmax;
+  a.noccmax = os.maxcnt;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

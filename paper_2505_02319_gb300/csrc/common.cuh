@@ -61,7 +61,10 @@ __device__ __forceinline__ dfloat df_from_double(double d) {
   return dfloat(h, __double2float_rn(d - (double)h));
 }
 
-struct dfloat2 {
+// 16-byte aligned, so that a complex element moves as one 128-bit access
+// (four 32-bit ones otherwise, which collide in shared memory: 4-way bank
+// conflicts on the line layouts of the plane pass)
+struct __align__(16) dfloat2 {
   dfloat x, y;
 };
 

@@ -102,6 +102,8 @@ struct Workspace {
   // projection coefficients (n x noccmax complex, stored as 2 doubles)
   DBuf<double> cpart;           // per-chunk partial sums of Phi^H Y
   DBuf<double> coef, coefM, coefP;
+  DBuf<double> coefX;           // Psi^H b of the Schur-complement solves (n x xmax complex)
+  DBuf<double> xshift;          // per-system shifts eps_s of the Schur-complement solves
   DBuf<double> dpart;           // per-system partial dot products
   DBuf<double> sys;             // per-system CG scalars (see SysField)
   DBuf<double> val;             // per-system reduced dot products
@@ -116,6 +118,11 @@ struct Workspace {
   DBuf<double> scal;            // a few device scalars
   DBuf<double> gm_V;            // GMRES basis (m+1) x Ng
   DBuf<double> gm_h;            // Arnoldi coefficients and partials
+  // lockstep right-hand sides (batch.cu): per item the potential, density and
+  // norms, the right-hand sides and solutions of its systems, Phi^H Y, the
+  // dphi^P coefficients and deps; per right-hand side the Krylov basis and three vectors
+  DBuf<double> bu, bdrho, bnrm, bM, bCP, bdeps, bgm;
+  DBuf<double2> bB, bX;
 };
 
 // offsets into the per-system scalar block (nsys doubles each)
@@ -197,7 +204,7 @@ struct ikr_ctx {
   int zspan = 0;
   bool zreg_ok = false;
   // launch plan of the fused FP32 CG update (cg_fused.cu), for cgf_nsmax systems per k-point
-  int cgf_nsmax = -1, cgf_cs = 0, cgf_sl = 0, cgf_lds = 0;
+  int cgf_nsmax = -1, cgf_maxcnt = -1, cgf_cs = 0, cgf_sl = 0, cgf_lds = 0;
   size_t cgf_smem = 0;
   bool cgf_ok = false;
   ikr::FftPlan plan[3];
@@ -239,6 +246,24 @@ struct ikr_ctx {
   ikr::DBuf<int> d_nocc;        // nk
   ikr::DBuf<int> d_occ_kstart;  // == d_phi_off
   ikr::DBuf<double> d_eps_occ, d_f_occ, d_fp_occ, d_w_occ, d_kappa_occ;  // per occupied system
+  // Schur-complement Sternheimer solves (ikr_set_schur): per k-point the occupied
+  // orbitals followed by the extra computed bands Psi_k (nbands - N_occ,k of them),
+  // vector j of k at (roff[k] + j) * ld; Psi_k starts at xoff[k] = roff[k] + N_occ,k.
+  // reps holds the eigenvalue of every stored vector (same index).
+  bool schur = false;
+  // system list of the batched CG over `batch_items` E applications (batch.cu),
+  // and the position of each of its systems in the per-item blocks
+  int batch_items = -1;
+  // tensor-core projection coefficients (tc_proj.cu; ikr_set_tensor_cores)
+  bool tc_proj = false;
+  ikr::DBuf<int> tc_err;
+  ikr::SysList batch_list;
+  ikr::DBuf<int> d_batch_map;
+  int rmax = 0, xmax = 0;
+  ikr::DBuf<double2> d_rset;
+  ikr::DBuf<float2> d_rset32;
+  ikr::DBuf<int> d_roff, d_rcnt, d_xoff, d_xcnt;
+  ikr::DBuf<double> d_reps;
   std::vector<double> h_kappa_occ;
   int* h_pinned = nullptr;      // pinned host scratch: 64 ints, then doubles
   double* h_pinned_d = nullptr;

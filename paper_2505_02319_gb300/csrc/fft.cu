@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256) k_z_inverse(const typename io<R>::cx* __r
   using C = C_t<R>;
   const int s = blockIdx.y;
   if (active && !active[s]) return;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Nz = pz.n, lds = Nz + 1;
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* A = tw + Nz;
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) k_z_forward(const typename io<R>::cx* __r
   using C = C_t<R>;
   const int s = blockIdx.y;
   if (active && !active[s]) return;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[8];
   const int Nz = pz.n, lds = Nz + 1;
   C* tw = reinterpret_cast<C*>(smem_raw);
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) k_plane(const C_t<R>* __restrict__ b1, in
   using C = C_t<R>;
   const int s = blockIdx.y, iz = blockIdx.x;
   if (active && !active[s]) return;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Nx = px.n, Ny = py.n, ldp = Nx + 1;
   C* tx = reinterpret_cast<C*>(smem_raw);
   C* ty = tx + Nx;
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kDensThreads) k_density(
     double* __restrict__ part, const C_t<R>* __restrict__ psi_real) {
   using C = C_t<R>;
   const int iz = blockIdx.x, g = blockIdx.y;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Nx = px.n, Ny = py.n, ldp = Nx + 1, np = Ny * ldp;
   C* tx = reinterpret_cast<C*>(smem_raw);
   C* ty = tx + Nx;
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(256) k_synth_planes(const C_t<R>* __restrict__
                                                       C_t<R>* __restrict__ out) {
   using C = C_t<R>;
   const int s = blockIdx.y, iz = blockIdx.x;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Nx = px.n, Ny = py.n, ldp = Nx + 1;
   C* tx = reinterpret_cast<C*>(smem_raw);
   C* ty = tx + Nx;
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(256) k_fft_axis(double2* __restrict__ data, Ff
                                                   const double2* __restrict__ tw, int nlines,
                                                   int n_inner, int istride, int ostride, int estride,
                                                   int L) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = p.n, lds = n + 1;
   double2* t = reinterpret_cast<double2*>(smem_raw);
   double2* A = t + n;

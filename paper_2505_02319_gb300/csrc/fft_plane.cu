@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(256) k_plane_t(const typename io<R>::cx* __res
   if (active && !active[s]) return;
   const int iz0 = blockIdx.x * PL;
   const int npl = min(PL, Nz - iz0);
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tx = reinterpret_cast<C*>(smem_raw);
   C* ty = tx + NX;
   C* planes = ty + NY;
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(256) k_synth_t(const typename io<R>::cx* __res
   constexpr int ldp = G::ldp;
   constexpr int TX = Tpl<NX>::v, TY = Tpl<NY>::v;
   const int iz = blockIdx.x, s = blockIdx.y;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tx = reinterpret_cast<C*>(smem_raw);
   C* ty = tx + NX;
   C* plane = ty + NY;
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(256) k_density_t(const typename io<R>::cx* __r
   constexpr int TX = Tpl<NX>::v, TY = Tpl<NY>::v;
   constexpr int NE = (NX * NY + 255) / 256;
   const int iz = blockIdx.x, g = blockIdx.y;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tx = reinterpret_cast<C*>(smem_raw);
   C* ty = tx + NX;
   C* planes = ty + NY;

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) k_proj_partial_w(const typename io<R>::cx
   if (ns == 0) return;
   const int nocc = nocc_k[k], nb = nb_k[k];
   const int g0 = chunk * kPC;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* ph = reinterpret_cast<C*>(smem_raw);           // [g][m], kPC x nocc
   C* ys = ph + kPC * nocc;                          // per warp kPC entries
   const typename io<R>::cx* phi = phi_all + (size_t)phi_off[k] * ld;
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256) k_proj_apply_w(const typename io<R>::cx* 
       for (int sl = threadIdx.x; sl < ns; sl += blockDim.x) dpart[(size_t)(kstart[k] + sl) * nparts + chunk] = 0.0;
     return;
   }
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* ph = reinterpret_cast<C*>(smem_raw);           // [m][g]
   C* cwall = ph + kPC * nocc;                       // per warp: the coefficients of its system
   const typename io<R>::cx* phi = phi_all + (size_t)phi_off[k] * ld;
@@ -587,12 +587,42 @@ int proj_chunks(ikr_ctx* c, int fp_bytes) {
 int proj_chunks(ikr_ctx* c) { return std::max(proj_chunks(c, 4), proj_chunks(c, 8)); }
 int cg_chunks(ikr_ctx* c) { return (c->ld + kEC - 1) / kEC; }
 
+OrbSet occ_set(ikr_ctx* c) {
+  OrbSet o;
+  o.phi = c->d_phi_all.p;
+  o.phi32 = c->d_phi_all32.p;
+  o.off = c->d_phi_off.p;
+  o.cnt = c->d_nocc.p;
+  o.maxcnt = c->noccmax;
+  return o;
+}
+OrbSet schur_set(ikr_ctx* c) {
+  OrbSet o;
+  o.phi = c->d_rset.p;
+  o.phi32 = c->d_rset32.p;
+  o.off = c->d_roff.p;
+  o.cnt = c->d_rcnt.p;
+  o.maxcnt = c->rmax;
+  return o;
+}
+OrbSet extra_set(ikr_ctx* c) {
+  OrbSet o;
+  o.phi = c->d_rset.p;
+  o.phi32 = c->d_rset32.p;
+  o.off = c->d_xoff.p;
+  o.cnt = c->d_xcnt.p;
+  o.maxcnt = c->xmax;
+  return o;
+}
+
 template <typename R>
-void proj_coef(ikr_ctx* c, const SysList& L, const C_t<R>* Y, int ldy, const int* active, double2* coef) {
+void proj_coef(ikr_ctx* c, const SysList& L, const C_t<R>* Y, int ldy, const int* active, double2* coef,
+               const OrbSet* set) {
   ProfScope ps(c, kKidProjCoef, 2, L.n, (int)sizeof(R));
+  const OrbSet os = set ? *set : occ_set(c);
   if (sizeof(R) == 8) {
     const int nch = (c->ld + kPC - 1) / kPC;
-    const int nm = c->noccmax;
+    const int nm = os.maxcnt;
     c->ws.cpart.reserve((size_t)nch * L.n * nm * 2);
     double2* part = reinterpret_cast<double2*>(c->ws.cpart.p);
     const size_t smem = sizeof(double2) * (kPC * nm + 8 * kPC);
@@ -600,53 +630,54 @@ void proj_coef(ikr_ctx* c, const SysList& L, const C_t<R>* Y, int ldy, const int
     const double2* Yd = reinterpret_cast<const double2*>(Y);
     if (c->emulate_fp64) {   // FP64-accurate products of the mixed path on the FP32 units
       set_smem_attr((const void*)k_proj_partial_w<dfloat>, smem);
-      k_proj_partial_w<dfloat><<<grid, 256, smem, c->stream>>>(c->d_phi_all.p, c->ld, c->d_phi_off.p, c->d_nocc.p,
+      k_proj_partial_w<dfloat><<<grid, 256, smem, c->stream>>>(os.phi, c->ld, os.off, os.cnt,
                                                                 c->d_nb.p, L.d_kstart.p, L.d_kcount.p, Yd, ldy,
                                                                 active, L.n, nm, part);
     } else {
       set_smem_attr((const void*)k_proj_partial_w<double>, smem);
-      k_proj_partial_w<double><<<grid, 256, smem, c->stream>>>(c->d_phi_all.p, c->ld, c->d_phi_off.p, c->d_nocc.p,
+      k_proj_partial_w<double><<<grid, 256, smem, c->stream>>>(os.phi, c->ld, os.off, os.cnt,
                                                                 c->d_nb.p, L.d_kstart.p, L.d_kcount.p, Yd, ldy,
                                                                 active, L.n, nm, part);
     }
     IKR_CUDA(cudaGetLastError());
     const long long threads = 32LL * L.n * nm;
     k_proj_reduce<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(part, nch, kPC, L.n, nm, L.d_k.p,
-                                                                            c->d_nocc.p, c->d_nb.p, active, coef);
+                                                                            os.cnt, c->d_nb.p, active, coef);
     IKR_CUDA(cudaGetLastError());
     return;
   }
-  if constexpr (sizeof(R) == 4) proj_coef32(c, L, Y, ldy, active, coef);
+  if constexpr (sizeof(R) == 4) proj_coef32(c, L, Y, ldy, active, coef, os);
 }
 
 template <typename R>
 void proj_apply(ikr_ctx* c, const SysList& L, const double2* coef, const C_t<R>* in, R alpha, R beta,
-                C_t<R>* out, int ldy, const C_t<R>* dv, double* dpart, const int* active) {
+                C_t<R>* out, int ldy, const C_t<R>* dv, double* dpart, const int* active, const OrbSet* set) {
   ProfScope ps(c, kKidProjApply, 1, L.n, (int)sizeof(R));
+  const OrbSet os = set ? *set : occ_set(c);
   if (sizeof(R) == 8) {
     const int nch = proj_chunks(c, 8);
-    const size_t smem = sizeof(double2) * ((kPC + 8) * c->noccmax);
+    const size_t smem = sizeof(double2) * ((kPC + 8) * os.maxcnt);
     dim3 grid(nch, (unsigned)c->k.size());
     const double2* ind = reinterpret_cast<const double2*>(in);
     double2* outd = reinterpret_cast<double2*>(out);
     const double2* dvd = reinterpret_cast<const double2*>(dv);
     if (c->emulate_fp64) {
       set_smem_attr((const void*)k_proj_apply_w<dfloat>, smem);
-      k_proj_apply_w<dfloat><<<grid, 256, smem, c->stream>>>(c->d_phi_all.p, c->ld, c->d_phi_off.p, c->d_nocc.p,
-                                                              c->d_nb.p, L.d_kstart.p, L.d_kcount.p, coef, c->noccmax,
+      k_proj_apply_w<dfloat><<<grid, 256, smem, c->stream>>>(os.phi, c->ld, os.off, os.cnt,
+                                                              c->d_nb.p, L.d_kstart.p, L.d_kcount.p, coef, os.maxcnt,
                                                               ind, (double)alpha, (double)beta, outd, ldy, dvd, dpart,
                                                               nch, active);
     } else {
       set_smem_attr((const void*)k_proj_apply_w<double>, smem);
-      k_proj_apply_w<double><<<grid, 256, smem, c->stream>>>(c->d_phi_all.p, c->ld, c->d_phi_off.p, c->d_nocc.p,
-                                                              c->d_nb.p, L.d_kstart.p, L.d_kcount.p, coef, c->noccmax,
+      k_proj_apply_w<double><<<grid, 256, smem, c->stream>>>(os.phi, c->ld, os.off, os.cnt,
+                                                              c->d_nb.p, L.d_kstart.p, L.d_kcount.p, coef, os.maxcnt,
                                                               ind, (double)alpha, (double)beta, outd, ldy, dvd, dpart,
                                                               nch, active);
     }
     IKR_CUDA(cudaGetLastError());
     return;
   }
-  if constexpr (sizeof(R) == 4) proj_apply32(c, L, coef, in, alpha, beta, out, ldy, dv, dpart, active);
+  if constexpr (sizeof(R) == 4) proj_apply32(c, L, coef, in, alpha, beta, out, ldy, dv, dpart, active, os);
 }
 
 void sys_reduce(ikr_ctx* c, const double* part, int nparts, int nsys, const int* active, double* out) {
@@ -697,6 +728,31 @@ void chi0_sys(ikr_ctx* c, const SysList& L, const double2* M, double* deps, doub
   k_chi0_sys<<<(tot + 255) / 256, 256, 0, c->stream>>>(
       M, c->noccmax, L.d_k.p, L.d_band.p, c->d_nocc.p, c->d_occ_kstart.p, c->d_eps_occ.p, c->d_f_occ.p,
       c->d_fp_occ.p, L.n, c->T > 0.0 ? 1 : 0, deps, coefP);
+  IKR_CUDA(cudaGetLastError());
+}
+
+// a[s][j] = <psi_j, b_s> / (lambda_j - eps_s): the Psi_k component of the
+// Schur-complement solution (lambda_j >= eps_{Nocc+1,k} > eps_s, checked when
+// the eigenpairs were set).
+__global__ void k_deflate_coef(double2* __restrict__ a, int xmax, int nsys, const int* __restrict__ sys_k,
+                               const int* __restrict__ xcnt, const int* __restrict__ xoff,
+                               const double* __restrict__ reps, const double* __restrict__ shift) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nsys * xmax) return;
+  const int s = idx / xmax, j = idx - s * xmax;
+  const int k = sys_k[s];
+  if (j >= xcnt[k]) return;
+  const double inv = 1.0 / (reps[xoff[k] + j] - shift[s]);
+  const double2 v = a[idx];
+  a[idx] = make_double2(v.x * inv, v.y * inv);
+}
+
+void deflate_coef(ikr_ctx* c, const SysList& L, double2* a, const double* shift) {
+  ProfScope ps(c, kKidScalar, 1);
+  const int tot = L.n * c->xmax;
+  if (tot == 0) return;
+  k_deflate_coef<<<(tot + 255) / 256, 256, 0, c->stream>>>(a, c->xmax, L.n, L.d_k.p, c->d_xcnt.p, c->d_xoff.p,
+                                                           c->d_reps.p, shift);
   IKR_CUDA(cudaGetLastError());
 }
 
@@ -807,9 +863,10 @@ void to_fp64(ikr_ctx* c, const float2* in, size_t n, double2* out) {
 }
 
 #define IKR_INST(R)                                                                                \
-  template void proj_coef<R>(ikr_ctx*, const SysList&, const C_t<R>*, int, const int*, double2*); \
+  template void proj_coef<R>(ikr_ctx*, const SysList&, const C_t<R>*, int, const int*, double2*,  \
+                             const OrbSet*);                                                       \
   template void proj_apply<R>(ikr_ctx*, const SysList&, const double2*, const C_t<R>*, R, R,      \
-                              C_t<R>*, int, const C_t<R>*, double*, const int*);                  \
+                              C_t<R>*, int, const C_t<R>*, double*, const int*, const OrbSet*);   \
   template void cg_xr<R>(ikr_ctx*, const SysList&, int, CgVecs<R>&, const double*, const int*,     \
                          double*);                                                                 \
   template void cg_p<R>(ikr_ctx*, const SysList&, int, CgVecs<R>&, const double*, const int*);

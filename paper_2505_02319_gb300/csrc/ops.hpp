@@ -68,24 +68,53 @@ template <typename R> const R* kin_all_ptr(ikr_ctx* c);
 template <> inline const double* kin_all_ptr<double>(ikr_ctx* c) { return c->d_kin_all.p; }
 template <> inline const float* kin_all_ptr<float>(ikr_ctx* c) { return c->d_kin_all32.p; }
 
+// A set of orthonormal vectors per k-point for the projections, stored like the
+// occupied orbitals: vector j of k-point k at (off[k] + j) * ld, cnt[k] of them.
+// The projections use the occupied orbitals Phi_k unless another set is given.
+struct OrbSet {
+  const double2* phi = nullptr;
+  const float2* phi32 = nullptr;
+  const int* off = nullptr;     // device, one per k-point
+  const int* cnt = nullptr;     // device, one per k-point
+  int maxcnt = 0;
+};
+OrbSet occ_set(ikr_ctx* c);     // Phi_k
+OrbSet schur_set(ikr_ctx* c);   // [Phi_k Psi_k]: the occupied and the extra computed bands
+OrbSet extra_set(ikr_ctx* c);   // Psi_k
+
 // ops.cu
 // Fused FP32 CG update after the H_k application (cg_fused.cu): false when the
 // shape does not fit a thread-block cluster per k-point (then nothing is launched)
+// set: project z on the complement of this orbital set (default: Phi_k)
 bool launch_cg_fused(ikr_ctx* c, const SysList& L, float2* X, float2* Rv, float2* P, const float2* W, double* sys,
-                     int maxit, int* active, int* counter, int* list, const double* zpart, int nzf);
+                     int maxit, int* active, int* counter, int* list, const double* zpart, int nzf,
+                     const OrbSet* set = nullptr);
 // FP32 projections (proj32.cu)
 int proj_chunks32();
-void proj_coef32(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef);
+void proj_coef32(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef,
+                 const OrbSet& set);
 void proj_apply32(ikr_ctx* c, const SysList& L, const double2* coef, const float2* in, float alpha, float beta,
-                  float2* out, int ldy, const float2* dv, double* dpart, const int* active);
+                  float2* out, int ldy, const float2* dv, double* dpart, const int* active, const OrbSet& set);
+// Tensor-core projection products (tc_proj.cu): the FP32 V^H Y of proj_coef32
+// and Y - V C of proj_apply32 by tcgen05 MMAs
+bool tc_proj_ok(ikr_ctx* c, const OrbSet& set);
+void proj_coef_tc(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef,
+                  const OrbSet& set);
+void proj_apply_tc(ikr_ctx* c, const SysList& L, const double2* coef, const float2* in, float alpha, float beta,
+                   float2* out, int ldy, const float2* dv, double* dpart, const int* active, const OrbSet& set);
+void tc_check(ikr_ctx* c);    // IKR_ERR_TIMEOUT if a tensor-core launch gave up on a wait
 int proj_chunks(ikr_ctx* c);                  // the largest count (workspace sizing)
 int proj_chunks(ikr_ctx* c, int fp_bytes);    // dot partials per system written by proj_apply
 int cg_chunks(ikr_ctx* c);
+// coef[s][m] = <v_m, y_s> for the vectors v of `set` (default: Phi_k), stride set->maxcnt
 template <typename R>
-void proj_coef(ikr_ctx* c, const SysList& L, const C_t<R>* Y, int ldy, const int* active, double2* coef);
+void proj_coef(ikr_ctx* c, const SysList& L, const C_t<R>* Y, int ldy, const int* active, double2* coef,
+               const OrbSet* set = nullptr);
+// out = alpha in + beta sum_m v_m coef[s][m] (and the dot partials with dv)
 template <typename R>
 void proj_apply(ikr_ctx* c, const SysList& L, const double2* coef, const C_t<R>* in, R alpha, R beta,
-                C_t<R>* out, int ldy, const C_t<R>* dv, double* dpart, const int* active);
+                C_t<R>* out, int ldy, const C_t<R>* dv, double* dpart, const int* active,
+                const OrbSet* set = nullptr);
 void sys_reduce(ikr_ctx* c, const double* part, int nparts, int nsys, const int* active, double* out);
 template <typename R>
 void cg_xr(ikr_ctx* c, const SysList& L, int mode, CgVecs<R>& v, const double* sys, const int* active,
@@ -96,6 +125,8 @@ void cg_scalars(ikr_ctx* c, int stage, double* sys, const double* part, int npar
                 int* active, int* counter, int* list = nullptr);
 void count_active(ikr_ctx* c, const int* active, int n, int* dout);
 void chi0_sys(ikr_ctx* c, const SysList& L, const double2* M, double* deps, double2* coefP);
+// a[s][j] /= lambda_j - shift[s] for the extra bands j of k_s (stride c->xmax)
+void deflate_coef(ikr_ctx* c, const SysList& L, double2* a, const double* shift);
 void occupation_response(ikr_ctx* c, const double* deps, double* coef_a, double* coef_b, double* deF);
 void apply_K(ikr_ctx* c, const double* v, double* Kv, double* d_norm);
 void apply_kerker(ikr_ctx* c, const double* v, double* Tv, double alpha);

@@ -212,35 +212,44 @@ __global__ void __launch_bounds__(kAT)
 
 int proj_chunks32() { return kPG; }
 
-void proj_coef32(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef) {
+void proj_coef32(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef,
+                 const OrbSet& set) {
+  if (tc_proj_ok(c, set)) {
+    proj_coef_tc(c, L, Y, ldy, active, coef, set);
+    return;
+  }
   const int nch = (c->ld + kKG - 1) / kKG;
-  const int nm = c->noccmax;
+  const int nm = set.maxcnt;
   c->ws.cpart.reserve((size_t)nch * L.n * nm * 2);
   double2* part = reinterpret_cast<double2*>(c->ws.cpart.p);
   int maxns = 0;
   for (int v : L.kcount) maxns = std::max(maxns, v);
   const int nst = std::max(1, (maxns + kCS - 1) / kCS), nmt = std::max(1, (nm + kCM - 1) / kCM);
   dim3 grid(nch, (unsigned)c->k.size(), nst * nmt);
-  k_pc32<<<grid, kCT, 0, c->stream>>>(c->d_phi_all32.p, c->ld, c->d_phi_off.p, c->d_nocc.p, c->d_nb.p,
+  k_pc32<<<grid, kCT, 0, c->stream>>>(set.phi32, c->ld, set.off, set.cnt, c->d_nb.p,
                                       L.d_kstart.p, L.d_kcount.p, Y, ldy, active, L.n, nm, nst, nch, part);
   IKR_CUDA(cudaGetLastError());
   const long long threads = 32LL * L.n * nm;
-  k_pr<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(part, L.n, nm, nch, L.d_k.p, c->d_nocc.p,
+  k_pr<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(part, L.n, nm, nch, L.d_k.p, set.cnt,
                                                                   c->d_nb.p, active, coef);
   IKR_CUDA(cudaGetLastError());
 }
 
 void proj_apply32(ikr_ctx* c, const SysList& L, const double2* coef, const float2* in, float alpha, float beta,
-                  float2* out, int ldy, const float2* dv, double* dpart, const int* active) {
+                  float2* out, int ldy, const float2* dv, double* dpart, const int* active, const OrbSet& set) {
+  if (tc_proj_ok(c, set)) {
+    proj_apply_tc(c, L, coef, in, alpha, beta, out, ldy, dv, dpart, active, set);
+    return;
+  }
   const int nch = (c->ld + kPG - 1) / kPG;
-  const int nm = std::max(c->noccmax, 1);
+  const int nm = std::max(set.maxcnt, 1);
   int maxns = 0;
   for (int v : L.kcount) maxns = std::max(maxns, v);
   const size_t smem = sizeof(float2) * (size_t)nm * (kPG + kAS);
   IKR_CUDA(cudaFuncSetAttribute(k_pa32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(nch, (unsigned)c->k.size(), std::max(1, (maxns + kAS - 1) / kAS));
-  k_pa32<<<grid, kAT, smem, c->stream>>>(c->d_phi_all32.p, c->ld, c->d_phi_off.p, c->d_nocc.p, c->d_nb.p,
-                                         L.d_kstart.p, L.d_kcount.p, coef, c->noccmax, in, alpha, beta, out, ldy, dv,
+  k_pa32<<<grid, kAT, smem, c->stream>>>(set.phi32, c->ld, set.off, set.cnt, c->d_nb.p,
+                                         L.d_kstart.p, L.d_kcount.p, coef, set.maxcnt, in, alpha, beta, out, ldy, dv,
                                          dpart, nch, active);
   IKR_CUDA(cudaGetLastError());
 }

@@ -448,6 +448,41 @@ void set_eigenpairs(ikr_ctx* c, const ikr_eigenpairs* eig) {
                                K.nocc, cudaMemcpyDeviceToDevice, st));
   }
   to_fp32(c, c->d_phi_all.p, (size_t)S * ld, c->d_phi_all32.p);
+  // all computed bands per k-point (occupied, then extra) for the Schur-complement solves
+  {
+    std::vector<int> roff(nk), rcnt(nk), xoff(nk), xcnt(nk);
+    std::vector<double> reps;
+    int tot = 0;
+    c->rmax = c->xmax = 0;
+    for (int ik = 0; ik < nk; ++ik) {
+      const KPoint& K = c->k[ik];
+      roff[ik] = tot;
+      rcnt[ik] = nb;
+      xoff[ik] = tot + K.nocc;
+      xcnt[ik] = nb - K.nocc;
+      c->rmax = std::max(c->rmax, nb);
+      c->xmax = std::max(c->xmax, nb - K.nocc);
+      for (int n = 0; n < nb; ++n) reps.push_back(K.eps[n]);
+      tot += nb;
+    }
+    c->d_rset.reserve((size_t)tot * ld);
+    c->d_rset32.reserve((size_t)tot * ld);
+    IKR_CUDA(cudaMemsetAsync(c->d_rset.p, 0, sizeof(double2) * tot * ld, st));
+    for (int ik = 0; ik < nk; ++ik) {
+      const KPoint& K = c->k[ik];
+      IKR_CUDA(cudaMemcpy2DAsync(c->d_rset.p + (size_t)roff[ik] * ld, sizeof(double2) * ld,
+                                 eig->eigenvectors[ik], sizeof(double2) * K.nb, sizeof(double2) * K.nb, nb,
+                                 cudaMemcpyDeviceToDevice, st));
+    }
+    to_fp32(c, c->d_rset.p, (size_t)tot * ld, c->d_rset32.p);
+    upload(c->d_roff, roff, st);
+    upload(c->d_rcnt, rcnt, st);
+    upload(c->d_xoff, xoff, st);
+    upload(c->d_xcnt, xcnt, st);
+    upload(c->d_reps, reps, st);
+    c->schur = false;
+    c->batch_items = -1;
+  }
   // preconditioner constants kappa_n = max(1, <phi_n, |k+G|^2/2 phi_n>)
   std::vector<double2> hphi((size_t)S * ld);
   IKR_CUDA(cudaMemcpyAsync(hphi.data(), c->d_phi_all.p, sizeof(double2) * S * ld, cudaMemcpyDeviceToHost, st));

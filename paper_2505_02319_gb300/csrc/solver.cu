@@ -47,7 +47,7 @@ void ensure_workspace(ikr_ctx* c, int n) {
   w.b1b.reserve(nf);
   for (auto* b : {&w.X, &w.R, &w.P, &w.Z, &w.W, &w.B, &w.Y}) b->reserve(nv);
   for (auto* b : {&w.X32, &w.R32, &w.P32, &w.Z32, &w.W32, &w.B32}) b->reserve(nv);
-  const size_t nm = (size_t)std::max(n, 1) * std::max(c->noccmax, 1);
+  const size_t nm = (size_t)std::max(n, 1) * std::max(std::max(c->noccmax, c->rmax), 1);
   w.coef.reserve(2 * nm);
   w.coefM.reserve(2 * nm);
   w.coefP.reserve(2 * nm);
@@ -107,9 +107,12 @@ template void hamiltonian<float>(ikr_ctx*, int, const float2*, float2*, int, int
 // range(Q) (Remark rmk:sternheimer_solution); A p = (H - eps) p then already
 // lies in range(Q) up to the eigenpair residual.  Preconditioner:
 // z = Q diag(1/(kappa_s + |k+G|^2/2)) r.  B must be in range(Q).
+// zset: project z on the complement of another set of eigenvectors than Phi_k
+// (the Schur-complement solves below: Q is then R = 1 - [Phi Psi][Phi Psi]^H
+// and B must be in range(R)).
 template <typename R>
 CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, const std::vector<double>& shift,
-                 const std::vector<double>& kappa, const std::vector<double>& tol, int maxit) {
+                 const std::vector<double>& kappa, const std::vector<double>& tol, int maxit, const OrbSet* zset) {
   const int n = L.n;
   CgStats st;
   st.iters.assign(n, 0);
@@ -140,8 +143,8 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
   double2* coef = reinterpret_cast<double2*>(w.coef.p);
   // initial state: x = 0, r = b, z = Q M^-1 r, p = z
   cg_xr<R>(c, L, 0, v, sys, act, nullptr);
-  proj_coef<R>(c, L, v.Z, c->ld, act, coef);
-  proj_apply<R>(c, L, coef, v.Z, R(1), R(-1), v.Z, c->ld, v.R, w.dpart.p, act);
+  proj_coef<R>(c, L, v.Z, c->ld, act, coef, zset);
+  proj_apply<R>(c, L, coef, v.Z, R(1), R(-1), v.Z, c->ld, v.R, w.dpart.p, act, zset);
   cg_scalars(c, 0, sys, w.dpart.p, pch, n, maxit, act, nullptr);
   cg_p<R>(c, L, 0, v, sys, act);
   c->active_hint = n;
@@ -159,11 +162,13 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
     apply_nonlocal<R>(c, L, v.P, c->ld, v.W, act, w.dpart.p, zf_chunks(c, (int)sizeof(R)));
     bool fused = false;
     if constexpr (sizeof(R) == 4) {
-      // alpha, x, r, stopping test, z = Q M^-1 r, beta and p in one launch
-      ProfScope ps(c, kKidCgVec, 1);
-      IKR_CUDA(cudaMemsetAsync(dcount, 0, sizeof(int), strm));
-      fused = launch_cg_fused(c, L, v.X, v.R, v.P, v.W, sys, maxit, act, dcount, w.alist.p, w.dpart.p,
-                              zf_chunks(c, 4));
+      if (!c->tc_proj) {   // the fused kernel projects on the CUDA cores
+        // alpha, x, r, stopping test, z = Q M^-1 r (or R M^-1 r), beta and p in one launch
+        ProfScope ps(c, kKidCgVec, 1);
+        IKR_CUDA(cudaMemsetAsync(dcount, 0, sizeof(int), strm));
+        fused = launch_cg_fused(c, L, v.X, v.R, v.P, v.W, sys, maxit, act, dcount, w.alist.p, w.dpart.p,
+                                zf_chunks(c, 4), zset);
+      }
     }
     if (!fused) {
       cg_scalars(c, 1, sys, w.dpart.p, zf_chunks(c, (int)sizeof(R)), n, maxit, act, dcount);
@@ -171,8 +176,8 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
       cg_xr<R>(c, L, 1, v, sys, act, w.dpart.p);
       cg_scalars(c, 2, sys, w.dpart.p, cch, n, maxit, act, dcount, w.alist.p);
       // z = Q z, beta, p = z + beta p
-      proj_coef<R>(c, L, v.Z, c->ld, act, coef);
-      proj_apply<R>(c, L, coef, v.Z, R(1), R(-1), v.Z, c->ld, v.R, w.dpart.p, act);
+      proj_coef<R>(c, L, v.Z, c->ld, act, coef, zset);
+      proj_apply<R>(c, L, coef, v.Z, R(1), R(-1), v.Z, c->ld, v.R, w.dpart.p, act, zset);
       cg_scalars(c, 3, sys, w.dpart.p, pch, n, maxit, act, nullptr);
       cg_p<R>(c, L, 1, v, sys, act);
     }
@@ -183,6 +188,7 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
   }
   IKR_CUDA(cudaMemcpyAsync(hs.data(), sys, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, strm));
   IKR_CUDA(cudaStreamSynchronize(strm));
+  if (c->tc_proj) tc_check(c);
   for (int s = 0; s < n; ++s) {
     st.iters[s] = (int)hs[kSysIters * n + s];
     int code = (int)hs[kSysStatus * n + s];
@@ -197,9 +203,44 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
   return st;
 }
 template CgStats cg_solve<double>(ikr_ctx*, const SysList&, const double2*, double2*, const std::vector<double>&,
-                                  const std::vector<double>&, const std::vector<double>&, int);
+                                  const std::vector<double>&, const std::vector<double>&, int, const OrbSet*);
 template CgStats cg_solve<float>(ikr_ctx*, const SysList&, const float2*, float2*, const std::vector<double>&,
-                                 const std::vector<double>&, const std::vector<double>&, int);
+                                 const std::vector<double>&, const std::vector<double>&, int, const OrbSet*);
+
+// The Sternheimer solves of chi0: the projected CG above, or (ikr_set_schur)
+// its Schur-complement form over the extra computed bands Psi_k (Sec. 3.4.2,
+// Sec. 4.1.2).  With R = Q - Psi Psi^H, the solution of Q (H - eps) Q x = b is
+//   x = Psi a + y,   a = M^-1 (Psi^H b - W^H y),   M = Psi^H (H - eps) Psi,
+//   S y = R b - W M^-1 Psi^H b,   S = R (H - eps) R - W M^-1 W^H,   W = R H Psi,
+// and CG runs on S, whose smallest eigenvalue is eps_{Nocc+Nx+1} - eps instead
+// of eps_{Nocc+1} - eps.  The extra bands are Rayleigh-Ritz pairs of the
+// eigensolver, so M = diag(lambda_j - eps) and W = R (H Psi - Psi Lambda) is
+// the size of their residual: the W terms are dropped, and the solve becomes
+//   a = (lambda - eps)^-1 Psi^H b,  R (H - eps) R y = R b,  x = y + Psi a.
+// B is overwritten with R b.
+template <typename R>
+CgStats sternheimer_solve(ikr_ctx* c, const SysList& L, C_t<R>* Bv, C_t<R>* Xv, const std::vector<double>& shift,
+                          const std::vector<double>& kappa, const std::vector<double>& tol, int maxit) {
+  if (!c->schur) return cg_solve<R>(c, L, Bv, Xv, shift, kappa, tol, maxit);
+  const int n = L.n;
+  if (n == 0) return cg_solve<R>(c, L, Bv, Xv, shift, kappa, tol, maxit);
+  const OrbSet xs = extra_set(c), rs = schur_set(c);
+  Workspace& w = c->ws;
+  w.coefX.reserve((size_t)2 * n * std::max(c->xmax, 1));
+  w.xshift.reserve(n);
+  double2* a = reinterpret_cast<double2*>(w.coefX.p);
+  proj_coef<R>(c, L, Bv, c->ld, nullptr, a, &xs);
+  proj_apply<R>(c, L, a, Bv, R(1), R(-1), Bv, c->ld, nullptr, nullptr, nullptr, &xs);
+  CgStats st = cg_solve<R>(c, L, Bv, Xv, shift, kappa, tol, maxit, &rs);
+  IKR_CUDA(cudaMemcpyAsync(w.xshift.p, shift.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+  deflate_coef(c, L, a, w.xshift.p);
+  proj_apply<R>(c, L, a, Xv, R(1), R(1), Xv, c->ld, nullptr, nullptr, nullptr, &xs);
+  return st;
+}
+template CgStats sternheimer_solve<double>(ikr_ctx*, const SysList&, double2*, double2*, const std::vector<double>&,
+                                           const std::vector<double>&, const std::vector<double>&, int);
+template CgStats sternheimer_solve<float>(ikr_ctx*, const SysList&, float2*, float2*, const std::vector<double>&,
+                                          const std::vector<double>&, const std::vector<double>&, int);
 
 // ------------------------------------------------------------------- chi0 --
 // drho = chi0 (pot_scale * u) for the occupied systems (eqs. chi0, kchi0).
@@ -241,7 +282,7 @@ void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::
     proj_coef<float>(c, L, Y, ld, nullptr, M);
     chi0_sys(c, L, M, w.deps.p, CP);
     proj_apply<float>(c, L, M, Y, -1.0f, 1.0f, w.B32.p, ld, nullptr, nullptr, nullptr);
-    CgStats st = cg_solve<float>(c, L, w.B32.p, w.X32.p, shift, kappa, tol, maxit);
+    CgStats st = sternheimer_solve<float>(c, L, w.B32.p, w.X32.p, shift, kappa, tol, maxit);
     st.fp32 = true;
     rs.add(st);
     if (c->T > 0.0) proj_apply<float>(c, L, CP, w.X32.p, 1.0f, 1.0f, w.X32.p, ld, nullptr, nullptr, nullptr);
@@ -249,6 +290,7 @@ void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::
     float2* b1b = reinterpret_cast<float2*>(w.b1b.p);
     launch_z_inverse<float>(c, L, w.X32.p, ld, nullptr, b1b);
     launch_density<float>(c, n, c->d_b1phi32.p, b1b, w.ca.p, w.cb.p, drho, 1.0 / c->volume, c->d_psir32.p);
+    if (c->tc_proj) tc_check(c);
     return;
   }
   // y_s = F(u . F^-1 phi_s): plane pass on the cached real-space orbitals
@@ -262,9 +304,9 @@ void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::
   proj_apply<double>(c, L, M, w.Y.p, -1.0, 1.0, w.B.p, ld, nullptr, nullptr, nullptr);
   CgStats st;
   if (precision == IKR_MIXED) {
-    st = mixed_solve(c, L, w.B.p, w.X.p, shift, kappa, tol, maxit);
+    st = mixed_solve(c, L, w.B.p, w.X.p, shift, kappa, tol, maxit, true);
   } else {
-    st = cg_solve<double>(c, L, w.B.p, w.X.p, shift, kappa, tol, maxit);
+    st = sternheimer_solve<double>(c, L, w.B.p, w.X.p, shift, kappa, tol, maxit);
   }
   rs.add(st);
   // dphi = dphi^Q + dphi^P
@@ -273,6 +315,7 @@ void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::
   occupation_response(c, w.deps.p, w.ca.p, w.cb.p, w.scal.p + 8);
   launch_z_inverse<double>(c, L, w.X.p, ld, nullptr, w.b1b.p);
   launch_density<double>(c, n, c->d_b1phi.p, w.b1b.p, w.ca.p, w.cb.p, drho, 1.0 / c->volume, c->d_psir.p);
+  if (c->tc_proj) tc_check(c);   // the tensor-core products after the last CG of this application
 }
 
 // Ev = v - ||Kv|| chi0(Kv/||Kv||)  (eq. op_discretised).  tol_fn receives ||Kv||.
@@ -346,8 +389,6 @@ void dielectric_adjoint_core(ikr_ctx* c, const double* v, double* Ev, const TolF
 
 // ---------------------------------------------------------- Algorithm 1 --
 
-namespace {
-
 // smallest singular value of the m x n (m >= n) column-major matrix a by
 // one-sided Jacobi rotations (Hestenes).
 double sigma_min(std::vector<double> a, int m, int n) {
@@ -383,7 +424,6 @@ double sigma_min(std::vector<double> a, int m, int n) {
   return smin;
 }
 
-}  // namespace
 
 std::vector<double> strategy_tolerances(ikr_ctx* c, const ikr_solve_opts& o, int i, double s, double rprev,
                                         double kv_norm, double b_norm) {

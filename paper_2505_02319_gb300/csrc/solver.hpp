@@ -29,6 +29,7 @@ void herm_jacobi(int n, std::vector<std::complex<double>>& A, std::vector<double
 
 struct CgStats {
   std::vector<int> iters, status;   // status: 1 converged, 2 numeric, 3 iteration cap
+  std::vector<int> checks;          // FP64 residual applications per system (mixed solves)
   std::vector<double> res;          // final recursive residual norms
   long long n_ham = 0, n_ham_fp64 = 0;
   int max_iters = 0, noconv = 0, numeric = 0;
@@ -59,13 +60,23 @@ template <typename R>
 void hamiltonian(ikr_ctx* c, int k, const C_t<R>* psi, C_t<R>* hpsi, int ld, int nvec);
 template <typename R>
 CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, const std::vector<double>& shift,
-                 const std::vector<double>& kappa, const std::vector<double>& tol, int maxit);
+                 const std::vector<double>& kappa, const std::vector<double>& tol, int maxit,
+                 const OrbSet* zset = nullptr);
+// cg_solve, or its Schur-complement form when the context has it enabled (B is then overwritten)
+template <typename R>
+CgStats sternheimer_solve(ikr_ctx* c, const SysList& L, C_t<R>* Bv, C_t<R>* Xv, const std::vector<double>& shift,
+                          const std::vector<double>& kappa, const std::vector<double>& tol, int maxit);
+// schur: the FP32 solves take the Schur-complement form when the context has it
+// enabled (only for occupied systems, whose shifts lie below the extra bands)
 CgStats mixed_solve(ikr_ctx* c, const SysList& L, const double2* Bv, double2* Xv, const std::vector<double>& shift,
-                    const std::vector<double>& kappa, const std::vector<double>& tol, int maxit);
+                    const std::vector<double>& kappa, const std::vector<double>& tol, int maxit,
+                    bool schur = false);
 void chi0_core(ikr_ctx* c, const double* u, const double* pot_scale, const std::vector<double>& tol,
                int maxit, int precision, double* drho, RunStats& rs, bool fp32 = false);
 void dielectric_core(ikr_ctx* c, const double* v, double* Ev, const TolFn& tol_fn, int maxit, int precision,
                      RunStats& rs, double allowed = 0.0);
+// smallest singular value of the m x n column-major matrix a (m >= n)
+double sigma_min(std::vector<double> a, int m, int n);
 std::vector<double> strategy_tolerances(ikr_ctx* c, const ikr_solve_opts& o, int i, double s, double rprev,
                                         double kv_norm, double b_norm);
 void hamiltonian_noalloc(ikr_ctx* c, int k, const double2* psi, double2* hpsi, int nvec);
@@ -73,5 +84,9 @@ void dielectric_adjoint_core(ikr_ctx* c, const double* v, double* Ev, const TolF
                              int precision, RunStats& rs, double allowed = 0.0);
 void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o, ikr_report* rep,
                  bool adjoint = false);
+// Algorithm 1 for nrhs right-hand sides in lockstep, the E applications of a
+// round batched into one CG (batch.cu); reps: nrhs reports or NULL
+void gmres_solve_batch(ikr_ctx* c, int nrhs, const double* b, double* x, const ikr_solve_opts& o,
+                       ikr_report* reps, bool adjoint = false);
 
 }  // namespace ikr

@@ -37,10 +37,11 @@ def dense_eigenpairs(ctx: ikr.Context, nbands: int, batch: int = 512):
     return np.array(evals), evecs
 
 
-def context_for(system, nbands=None, eigensolver="dense", eig_tol=1e-10) -> ikr.Context:
+def context_for(system, nbands=None, eigensolver="dense", eig_tol=1e-10, schur=False) -> ikr.Context:
     """Context with ground state for a workloads.System.  ``eigensolver``:
     "dense" (H_k assembled and diagonalised, small bases) or "chfsi" (the
-    library's GPU Chebyshev-filtered subspace iteration, any basis size)."""
+    library's GPU Chebyshev-filtered subspace iteration, any basis size).
+    ``schur``: Schur-complement Sternheimer solves over the bands above N_occ,k."""
     ctx = ikr.Context.setup_groundstate(system.lattice, system.dims, system.Ecut, system.kpoints,
                                         system.kweights, system.V, system.temperature,
                                         system.n_electrons)
@@ -57,4 +58,6 @@ def context_for(system, nbands=None, eigensolver="dense", eig_tol=1e-10) -> ikr.
     ctx.nbands = nb
     ctx.ngrid = int(np.prod(system.dims))
     ctx.groundstate_nsys = int(ctx.groundstate_info(nb, ctx.ngrid)["nocc"].sum())
+    if schur:
+        ctx.set_schur(True)
     return ctx

@@ -82,6 +82,10 @@ def _load():
         "ikr_set_eigenpairs": (I, [P, ct.POINTER(Eigenpairs), S]),
         "ikr_compute_eigenpairs": (I, [P, I, D, I, I, ct.POINTER(D), ct.POINTER(I), ct.POINTER(D), S]),
         "ikr_set_nonlocal": (I, [P, I, ct.POINTER(D), ct.POINTER(D), ct.POINTER(D), S]),
+        "ikr_set_schur": (I, [P, I]),
+        "ikr_set_tensor_cores": (I, [P, I]),
+        "ikr_projection_coefficients": (I, [P, I, I, P, I, ct.POINTER(D), S]),
+        "ikr_project_out": (I, [P, I, I, P, I, S]),
         "ikr_hermitian_eigh": (I, [I, ct.POINTER(D), ct.POINTER(D), ct.POINTER(D)]),
         "ikr_num_kpoints": (I, [P]),
         "ikr_basis_size": (I, [P, I, ct.POINTER(I)]),
@@ -197,6 +201,34 @@ class Context:
         sg, sp = _dbl(sigma)
         dd, dp = _dbl(D)
         self._check(_LIB.ikr_set_nonlocal(self._h, len(cen), cp, sp, dp, _stream()))
+
+    def set_schur(self, enable=True):
+        """Schur-complement Sternheimer solves over the extra computed bands
+        (ikr_set_schur): same chi0, better conditioned CG."""
+        self._check(_LIB.ikr_set_schur(self._h, 1 if enable else 0))
+
+    def set_tensor_cores(self, enable=True):
+        """FP32 projection coefficients on the tensor cores (ikr_set_tensor_cores)."""
+        self._check(_LIB.ikr_set_tensor_cores(self._h, 1 if enable else 0))
+
+    def projection_coefficients(self, k, y, method=0):
+        """<phi_m, y_s> for the occupied orbitals of k-point k, FP32 arithmetic:
+        y a (nvec, Nb_k) complex64 CUDA tensor; method 0 CUDA cores, 1 tensor
+        cores.  Returns a (nvec, N_occ,k) complex128 numpy array."""
+        yy = y.reshape(-1, y.shape[-1]).contiguous()
+        nvec = yy.shape[0]
+        nocc = int(self.groundstate_info(self.nbands, self.ngrid)["nocc"][k])
+        out = np.zeros((nvec, nocc), dtype=np.complex128)
+        self._check(_LIB.ikr_projection_coefficients(self._h, int(k), nvec, _dptr(yy), int(method),
+                                                      out.ctypes.data_as(ct.POINTER(ct.c_double)), _stream()))
+        return out
+
+    def project_out(self, k, y, method=0):
+        """Q_k y = y - Phi_k (Phi_k^H y) for a (nvec, Nb_k) complex64 CUDA tensor
+        (in place; returned); method 0 CUDA cores, 1 tensor cores."""
+        self._check(_LIB.ikr_project_out(self._h, int(k), int(y.reshape(-1, y.shape[-1]).shape[0]), _dptr(y),
+                                         int(method), _stream()))
+        return y
 
     def compute_eigenpairs(self, nbands, tol=1e-10, maxit=200, degree=12):
         """Lowest ``nbands`` eigenpairs of every H_k on the GPU (Chebyshev-filtered

@@ -68,3 +68,7 @@ def test_null_arguments_are_rejected(lib):
     assert not h.value
     assert lib._LIB.ikr_solve_response(None, 1, None, None, None, None, None) == lib.IKR_ERR_ARG
     assert lib._LIB.ikr_basis_size(None, 0, None) == lib.IKR_ERR_ARG
+    assert lib._LIB.ikr_set_schur(None, 1) == lib.IKR_ERR_ARG
+    assert lib._LIB.ikr_set_tensor_cores(None, 1) == lib.IKR_ERR_ARG
+    assert lib._LIB.ikr_projection_coefficients(None, 0, 1, None, 1, None, None) == lib.IKR_ERR_ARG
+    assert lib._LIB.ikr_project_out(None, 0, 1, None, 1, None) == lib.IKR_ERR_ARG
