@@ -196,10 +196,19 @@ def systems(gs):
 
 
 def orbital_row_norm(gs, kb, real_part):
-    """||F_k^{-1} Phi_k||_{2,inf} (or of its real part): the largest row norm."""
+    """||F_k^{-1} Phi_k||_{2,inf} (or of its real part): the largest row norm.
+
+    The real part is taken in the gauge in which each orbital is as real as
+    possible (Sec. "Dropping the imaginary part of the orbitals": where a
+    real representation exists the real part loses nothing).  Multiplying
+    u_n by e^{-i theta} gives sum_r (Re)^2 = (sum |u|^2 + Re(e^{-2i theta}
+    sum u^2))/2, largest at theta = arg(sum_r u_n(r)^2)/2; the result no
+    longer depends on the phases the eigensolver returned."""
     psi = dft.F_inv(kb.vecs[:, :kb.nocc].T, kb.flat, gs.dims, gs.volume)
     if real_part:
-        psi = psi.real
+        sq = (psi * psi).reshape(psi.shape[0], -1).sum(axis=1)
+        theta = 0.5 * np.angle(sq)
+        psi = (psi * np.exp(-1j * theta).reshape((-1,) + (1,) * (psi.ndim - 1))).real
     return float(np.sqrt((np.abs(psi) ** 2).sum(axis=0)).max())
 
 
