@@ -123,6 +123,8 @@ typedef struct {
   double* history;             /* optional host array (caller-owned), receives ||r~_i|| per step */
   int history_cap;             /* its capacity; history_len <= history_cap entries are written */
   int history_len;
+  double first_min_cg_tol;     /* smallest CG tolerance of the solve's first E application */
+  double first_kv_norm;        /* ||K v|| of that application (the tolerance rules' ||K v_i||) */
 } ikr_report;
 
 typedef struct {

@@ -213,6 +213,8 @@ struct Rhs {
   ikr_status status = IKR_OK;
   std::vector<double> Hraw, Rm, cs, sn, g, hist;
   double min_tol = 1e300, max_tol = 0.0;
+  double first_tol = 0.0, first_kvn = 0.0;
+  bool first_seen = false;
   RunStats rs;
 };
 
@@ -263,7 +265,13 @@ void gmres_solve_batch(ikr_ctx* c, int nrhs, const double* b, double* x, const i
     q.sn.assign(m, 0.0);
     q.g.assign(m + 1, 0.0);
   }
-  auto track = [](Rhs& q, const std::vector<double>& t) {
+  auto track = [](Rhs& q, const std::vector<double>& t, double kvn) {
+    if (!q.first_seen) {
+      q.first_seen = true;
+      q.first_kvn = kvn;
+      q.first_tol = 1e300;
+      for (double v : t) q.first_tol = std::min(q.first_tol, v);
+    }
     for (double v : t) {
       q.min_tol = std::min(q.min_tol, v);
       q.max_tol = std::max(q.max_tol, v);
@@ -373,7 +381,7 @@ void gmres_solve_batch(ikr_ctx* c, int nrhs, const double* b, double* x, const i
           it.rs = &q.rs;
           it.tol_fn = [&, r](double kvn) {
             auto t = strategy_tolerances(c, o, 0, R[r].s, 1.0, kvn, R[r].b_norm);
-            track(R[r], t);
+            track(R[r], t, kvn);
             return t;
           };
           items.push_back(it);
@@ -397,7 +405,7 @@ void gmres_solve_batch(ikr_ctx* c, int nrhs, const double* b, double* x, const i
         const int i = q.i;
         it.tol_fn = [&, r, i](double kvn) {
           auto t = strategy_tolerances(c, o, i, R[r].s, R[r].rprev, kvn, R[r].b_norm);
-          track(R[r], t);
+          track(R[r], t, kvn);
           return t;
         };
         items.push_back(it);
@@ -441,6 +449,8 @@ void gmres_solve_batch(ikr_ctx* c, int nrhs, const double* b, double* x, const i
     rep->kv_norm = q.rs.kv_norm;
     rep->min_cg_tol = q.min_tol;
     rep->max_cg_tol = q.max_tol;
+    rep->first_min_cg_tol = q.first_tol;
+    rep->first_kv_norm = q.first_kvn;
     rep->ms = ms;
     rep->history_len = 0;
     if (rep->history && rep->history_cap > 0) {

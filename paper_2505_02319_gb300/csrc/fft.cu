@@ -336,25 +336,54 @@ __global__ void __launch_bounds__(256) k_synth_planes(const C_t<R>* __restrict__
   }
 }
 
-// sum over n systems of |psi_s(r)|^2 and (Re psi_s(r))^2 at every grid point
-// (planes of the cached real-space orbitals; the order of r does not matter)
-__global__ void k_orbital_sq_sums(const double2* __restrict__ psir, int nsys, size_t ng,
-                                  double* __restrict__ abs2, double* __restrict__ re2) {
+// Phase of the most-real gauge of every orbital: with S_s = sum_r psi_s(r)^2,
+// e^{-i theta_s} psi_s, theta_s = arg(S_s)/2, has the largest sum_r (Re)^2
+// (sum_r (Re e^{-i theta} psi)^2 = (sum |psi|^2 + Re(e^{-2i theta} S))/2), so its
+// real part loses nothing where the orbital has a real representation (Sec.
+// "Dropping the imaginary part of the orbitals").  One block per orbital,
+// fixed-order reduction; rot[s] = (cos theta_s, sin theta_s).
+__global__ void __launch_bounds__(256) k_orbital_phase(const double2* __restrict__ psir, size_t ng,
+                                                       double2* __restrict__ rot) {
+  __shared__ double sh[8];
+  const double2* p = psir + (size_t)blockIdx.x * ng;
+  double a = 0.0, b = 0.0;
+  for (size_t r = threadIdx.x; r < ng; r += blockDim.x) {
+    const double2 v = p[r];
+    a += v.x * v.x - v.y * v.y;
+    b += 2.0 * v.x * v.y;
+  }
+  a = block_sum(a, sh);
+  __syncthreads();
+  b = block_sum(b, sh);
+  if (threadIdx.x == 0) {
+    const double th = 0.5 * atan2(b, a);
+    rot[blockIdx.x] = make_double2(cos(th), sin(th));
+  }
+}
+
+// sum over n systems of |psi_s(r)|^2 and (Re e^{-i theta_s} psi_s(r))^2 at every
+// grid point (planes of the cached real-space orbitals; the order of r does not matter)
+__global__ void k_orbital_sq_sums(const double2* __restrict__ psir, const double2* __restrict__ rot, int nsys,
+                                  size_t ng, double* __restrict__ abs2, double* __restrict__ re2) {
   for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < ng; r += (size_t)gridDim.x * blockDim.x) {
     double a = 0.0, b = 0.0;
     for (int s = 0; s < nsys; ++s) {
       const double2 v = psir[(size_t)s * ng + r];
+      const double2 q = rot[s];
+      const double re = v.x * q.x + v.y * q.y;
       a += v.x * v.x + v.y * v.y;
-      b += v.x * v.x;
+      b += re * re;
     }
     abs2[r] = a;
     re2[r] = b;
   }
 }
 
-void orbital_sq_sums(ikr_ctx* c, const double2* psir, int nsys, double* abs2, double* re2) {
-  ProfScope ps(c, kKidGridOps, 1);
-  k_orbital_sq_sums<<<152 * 8, 256, 0, c->stream>>>(psir, nsys, c->Ng, abs2, re2);
+void orbital_sq_sums(ikr_ctx* c, const double2* psir, int nsys, double* abs2, double* re2, double2* rot) {
+  ProfScope ps(c, kKidGridOps, 2);
+  k_orbital_phase<<<nsys, 256, 0, c->stream>>>(psir, c->Ng, rot);
+  IKR_CUDA(cudaGetLastError());
+  k_orbital_sq_sums<<<152 * 8, 256, 0, c->stream>>>(psir, rot, nsys, c->Ng, abs2, re2);
   IKR_CUDA(cudaGetLastError());
 }
 

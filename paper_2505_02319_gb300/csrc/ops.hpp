@@ -62,7 +62,9 @@ void launch_density(ikr_ctx* c, int nsys, const C_t<R>* b1phi, const C_t<R>* b1d
 template <typename R>
 void to_plane_layout(ikr_ctx* c, const double* in, R* out, double scale, const double* dscale);
 void full_fft(ikr_ctx* c, double2* data, bool inverse);
-void orbital_sq_sums(ikr_ctx* c, const double2* psir, int nsys, double* abs2, double* re2);
+// |psi_s|^2 and (Re e^{-i theta_s} psi_s)^2 summed over the orbitals, theta_s of
+// the most-real gauge (rot: nsys scratch entries, receives (cos, sin) theta_s)
+void orbital_sq_sums(ikr_ctx* c, const double2* psir, int nsys, double* abs2, double* re2, double2* rot);
 
 template <typename R> const R* kin_all_ptr(ikr_ctx* c);
 template <> inline const double* kin_all_ptr<double>(ikr_ctx* c) { return c->d_kin_all.p; }

@@ -556,12 +556,15 @@ void set_eigenpairs(ikr_ctx* c, const ikr_eigenpairs* eig) {
   }
   // ||F_k^-1 Phi_k||_{2,inf} and ||Re F_k^-1 Phi_k||_{2,inf} per k-point (largest
   // row norm over grid points; F^-1 phi = psi / sqrt|Omega| for the unnormalised
-  // syntheses psi of the cached planes)
+  // syntheses psi of the cached planes); the real part of every orbital is taken in
+  // its most-real gauge, so neither norm depends on the eigenvectors' phases
   c->ws.grid1.reserve(c->Ng);
   c->ws.grid2.reserve(c->Ng);
   c->ws.scal.reserve(64);
+  c->ws.cgrid.reserve(c->Ng);   // the orbitals' gauge phases (N_occ,k <= Ng entries)
   for (int ik = 0; ik < nk; ++ik) {
-    orbital_sq_sums(c, c->d_psir.p + (size_t)off[ik] * c->Ng, noccs[ik], c->ws.grid1.p, c->ws.grid2.p);
+    orbital_sq_sums(c, c->d_psir.p + (size_t)off[ik] * c->Ng, noccs[ik], c->ws.grid1.p, c->ws.grid2.p,
+                    c->ws.cgrid.p);
     grid_max(c, c->ws.grid1.p, c->Ng, c->ws.scal.p);
     grid_max(c, c->ws.grid2.p, c->Ng, c->ws.scal.p + 1);
     double mx[2] = {0, 0};

@@ -498,7 +498,15 @@ void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o
   double min_tol = 1e300, max_tol = 0.0;
   std::vector<double> hist;
   ikr_status status = IKR_OK;
-  auto track = [&](const std::vector<double>& t) {
+  double first_tol = 0.0, first_kvn = 0.0;
+  bool first_seen = false;
+  auto track = [&](const std::vector<double>& t, double kvn) {
+    if (!first_seen) {
+      first_seen = true;
+      first_kvn = kvn;
+      first_tol = 1e300;
+      for (double v : t) first_tol = std::min(first_tol, v);
+    }
     for (double v : t) {
       min_tol = std::min(min_tol, v);
       max_tol = std::max(max_tol, v);
@@ -510,7 +518,7 @@ void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o
     if (x0_nonzero) {
       auto tf = [&](double kvn) {
         auto t = strategy_tolerances(c, o, 0, s, 1.0, kvn, b_norm);
-        track(t);
+        track(t, kvn);
         return t;
       };
       if (adjoint) dielectric_adjoint_core(c, x, wv, tf, o.cg_maxit, o.precision, rs, o.tau / 3.0);
@@ -548,7 +556,7 @@ void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o
       }
       auto tf = [&](double kvn) {
         auto t = strategy_tolerances(c, o, i, s, rprev, kvn, b_norm);
-        track(t);
+        track(t, kvn);
         return t;
       };
       if (adjoint)
@@ -644,6 +652,8 @@ void gmres_solve(ikr_ctx* c, const double* b, double* x, const ikr_solve_opts& o
     rep->kv_norm = rs.kv_norm;
     rep->min_cg_tol = min_tol;
     rep->max_cg_tol = max_tol;
+    rep->first_min_cg_tol = first_tol;
+    rep->first_kv_norm = first_kvn;
     rep->ms = now_ms() - t0;
     rep->history_len = 0;
     if (rep->history && rep->history_cap > 0) {

@@ -48,7 +48,7 @@ class Report(ct.Structure):
                 ("est_residual", ct.c_double), ("sigma", ct.c_double), ("b_norm", ct.c_double),
                 ("kv_norm", ct.c_double), ("min_cg_tol", ct.c_double), ("max_cg_tol", ct.c_double),
                 ("ms", ct.c_double), ("history", ct.POINTER(ct.c_double)), ("history_cap", ct.c_int),
-                ("history_len", ct.c_int)]
+                ("history_len", ct.c_int), ("first_min_cg_tol", ct.c_double), ("first_kv_norm", ct.c_double)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_ if name != "history"}

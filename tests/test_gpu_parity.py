@@ -136,8 +136,11 @@ def test_mixed_precision_reaches_tau(name):
 @pytest.mark.parametrize("strategy", ["agr", "bal", "grt", "D10", "D100", "D10n", "grt_exact"])
 def test_strategies(strategy):
     """Every tolerance rule of Table strategies (k-form Table strategies_k)
-    drives Algorithm 1 to ||r~|| <= tau/3; the smallest CG tolerance of the
-    solve is the oracle's rule at the first step (s = 1, ||r~_0|| = ||b||)."""
+    drives Algorithm 1 to ||r~|| <= tau/3.  At the first E application the
+    library's ||K v_1|| and its smallest CG tolerance equal the oracle's (s = 1,
+    ||r~_0|| = ||b||), for every rule; for grt and grt_exact this compares the
+    orbital row norms (real part in the most-real gauge) and the gaps as well.
+    For the rules without ||K v_i|| that tolerance is also the solve's smallest."""
     from oracle import gmres, response
     from workloads import perturbation
     name = "tiny_ortho_k"
@@ -150,8 +153,12 @@ def test_strategies(strategy):
     assert r["status"] == 0 and r["est_residual"] <= tau / 3
     true = np.linalg.norm(b - response.dielectric(gs, x.cpu().numpy().reshape(s.dims)))
     assert true <= (tau if strategy == "grt_exact" else 100 * tau)
+    # the first E application is at v_1 = b / ||b|| (x0 = 0, s = 1, ||r~_0|| = ||b|| = 1)
+    kvn = float(np.linalg.norm(response.apply_K(b, gs)))
+    assert abs(r["first_kv_norm"] - kvn) <= 1e-10 * kvn
+    first = gmres.cg_tolerances(gs, strategy, tau, 1, m, 1.0, 1.0, kvn, 1.0)
+    assert abs(r["first_min_cg_tol"] - first.min()) <= 1e-9 * first.min()
     if strategy in ("agr", "bal", "D10", "D100", "D10n"):
-        first = gmres.cg_tolerances(gs, strategy, tau, 1, m, 1.0, 1.0, 1.0, 1.0)
         assert abs(r["min_cg_tol"] - first.min()) <= 1e-12 * first.min()
 
 
