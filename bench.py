@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--cfg4-guaranteed", action="store_true",
                    help="also solve the 64-atom cell with Kleinman-Bylander projectors (cfg4) with the "
                         "guaranteed rule grt_exact, beside bal")
+    p.add_argument("--no-cpu-baseline", action="store_true",
+                   help="leave out the oracle's timed solve (for runs of the studies only)")
     p.add_argument("--profile-run", action="store_true",
                    help="only setup, warm-up and the timed steps (for ncu); prints no bench line")
     return p.parse_args()
@@ -246,7 +248,7 @@ def batch_run(tau, m, stream):
     from paper_2505_02319_gb300 import groundstate
     from workloads import make_system, response_batch
     s = make_system("cfg1")
-    ctx = groundstate.context_for(s, eigensolver="chfsi")
+    ctx = groundstate.context_for(s)
     nsys = ctx.groundstate_nsys
     dvs = response_batch(s)
     b = torch.stack([ctx.apply_chi0(torch.tensor(dv.ravel(), device="cuda"), tol=np.full(nsys, 1e-12))[0]
@@ -269,15 +271,17 @@ def batch_run(tau, m, stream):
             "time_s_lockstep": tb, "time_s_one_by_one": ts, "speedup": ts / tb,
             "n_ham_lockstep": int(sum(r["n_ham"] for r in rb)), "n_ham_one_by_one": int(sum(r["n_ham"] for r in rs)),
             "max_true_residual": max(res), "tau": tau}
-def _rule_run(ctx, b, nsys, rule, tau, m, precision, alpha=0.0):
+def _rule_run(ctx, b, nsys, rule, tau, m, precision, alpha=0.0, timeout_s=240.0):
     """One solve with one tolerance rule: time, N_ham, the solver's residual
     estimate (of T r with Kerker) and the true unpreconditioned residual
-    ||b - E x|| from an FP64 E application at tight CG tolerances."""
+    ||b - E x|| from an FP64 E application at tight CG tolerances.  A solve
+    that runs past timeout_s stops with status IKR_ERR_TIMEOUT (reported)."""
     import numpy as np
     import torch
     torch.cuda.synchronize()
     t0 = time.time()
-    x, rep = ctx.solve_response(b, tau=tau, m=m, strategy=rule, precision=precision, kerker_alpha=alpha)
+    x, rep = ctx.solve_response(b, tau=tau, m=m, strategy=rule, precision=precision, kerker_alpha=alpha,
+                                timeout_s=timeout_s)
     torch.cuda.synchronize()
     dt = time.time() - t0
     Ex, _ = ctx.apply_dielectric(x, tol=np.full(nsys, 1e-12))
@@ -299,7 +303,7 @@ def slab_strategies(tau, m):
     from workloads import make_system, perturbation
     s = make_system("cfg3")
     t0 = time.time()
-    ctx = groundstate.context_for(s, eigensolver="chfsi", eig_tol=1e-9)
+    ctx = groundstate.context_for(s, eig_tol=1e-9)
     setup = time.time() - t0
     nsys = ctx.groundstate_nsys
     b, _ = ctx.apply_chi0(torch.tensor(perturbation(s).ravel(), device="cuda"), tol=np.full(nsys, 1e-12))
@@ -325,13 +329,17 @@ def cfg4_guaranteed(tau, m):
     from workloads import make_system, perturbation
     s = make_system("cfg4")
     t0 = time.time()
-    ctx = groundstate.context_for(s, eigensolver="chfsi", eig_tol=1e-9)
+    ctx = groundstate.context_for(s, eig_tol=1e-9)
     setup = time.time() - t0
     nsys = ctx.groundstate_nsys
     b, _ = ctx.apply_chi0(torch.tensor(perturbation(s).ravel(), device="cuda"), tol=np.full(nsys, 1e-12))
     b = (b / torch.linalg.norm(b)).contiguous()
     out = {"workload": "cfg4, 256 KB projectors, mixed precision", "tau": tau, "m": m, "setup_s": setup,
            "rules": {rule: _rule_run(ctx, b, nsys, rule, tau, m, "mixed") for rule in ("bal", "grt_exact")}}
+    # Schur-complement solves (Sec. 3.4.2): the 8 computed bands above the gap split off
+    ctx.set_schur(True)
+    out["schur_rules"] = {rule: _rule_run(ctx, b, nsys, rule, tau, m, "mixed") for rule in ("bal", "grt_exact")}
+    ctx.set_schur(False)
     ctx.destroy()
     return out
 
@@ -358,7 +366,7 @@ def supercell_study(ells, tau, m, precision):
     for ell in ells:
         S = supercell(base, ell, kgrid=(1, 1, 1))
         t0 = time.time()
-        ctx = groundstate.context_for(S, eigensolver="chfsi")
+        ctx = groundstate.context_for(S)
         torch.cuda.synchronize()
         setup_s = time.time() - t0
         nsys = ctx.groundstate_nsys
@@ -371,12 +379,12 @@ def supercell_study(ells, tau, m, precision):
         for name in ("agr", "bal", "grt", "grt_exact", "D10", "D100", "D10n"):
             torch.cuda.synchronize()
             t1 = time.time()
-            x, rep = ctx.solve_response(b, tau=tau, m=m, strategy=name, precision=precision)
+            x, rep = ctx.solve_response(b, tau=tau, m=m, strategy=name, precision=precision, timeout_s=240.0)
             torch.cuda.synchronize()
             dt = time.time() - t1
             Ex, _ = ctx.apply_dielectric(x, tol=tight)
             tr = float(torch.linalg.norm(b - Ex))
-            row["strategies"][name] = {"n_ham": rep[0]["n_ham"], "true_residual": tr,
+            row["strategies"][name] = {"status": rep[0]["status"], "n_ham": rep[0]["n_ham"], "true_residual": tr,
                                        "residual_over_tau": tr / tau, "time_s": dt}
         rows.append(row)
         ctx.destroy()
@@ -494,7 +502,9 @@ def run_ours(args, rank, world, local_rank):
     g = ctx.fft_geometry()
     geom = (s.dims[0], s.dims[1], s.dims[2], g["ncols"], g["nxa"])
     peaks, src = measured_peaks()
-    roof = roofline(prof["plane"], geom, peaks)
+    dev = ikr.device_peaks()
+    alu = alu_peaks(dev, clk.get("sm_mhz") or dev["sm_clock_mhz"])
+    roof = roofline(prof["plane"], geom, peaks, alu, dev)
     value = t_max / args.steps
     out = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -534,20 +544,31 @@ def run_ours(args, rank, world, local_rank):
         out["supercell_study"] = supercell_study([int(v) for v in args.supercell.split(",")], 1e-9, 10,
                                                  ikr.FP64)
     if rank == 0:
-        out["cpu_baseline"] = cpu_baseline(s, rep["e_applies"])
+        out["device_peaks"] = dev
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(s)
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
 
 
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flops x max SM clock
-FP32_INSTR_PEAK = FP32_PEAK_TFLOPS / 2              # FP32 instructions (FMA = 1), in T/s
-FP64_PEAK_TFLOPS = 1.20                              # FP64 FMA-chain rate measured on a GB300
 # FP32 instructions per FP64-equivalent flop of the double-float FFT: an add is
 # TwoSum + two low-part adds (8), a product one FMUL + three FFMA (4); the
 # radix-4/3 butterflies and twiddles of the plane pass mix about 2 adds : 1 product
 DF64_INSTR_PER_FLOP = (2 * 8 + 4) / 3.0
-DF64_PEAK_TFLOPS = FP32_INSTR_PEAK / DF64_INSTR_PER_FLOP
+
+
+def alu_peaks(dev, sm_mhz):
+    """Peaks of the ALU rooflines, derived from unit counts and clocks: the
+    device's SM count x 128 FP32 lanes x 2 flops per FMA x the SM clock sampled
+    during the timed steps; the double-float peak is the FP32 instruction rate
+    over DF64_INSTR_PER_FLOP.  ``dev`` (ikr.device_peaks) also carries the
+    rates the FMA-chain and butterfly kernels measured on the device, reported
+    beside the derived peaks as their check."""
+    fp32 = dev["sms"] * 128 * 2 * sm_mhz * 1e6 / 1e12
+    return {"fp32": fp32, "df64": fp32 / 2 / DF64_INSTR_PER_FLOP, "sms": dev["sms"], "sm_mhz": sm_mhz}
+
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per system of one
 # launch of each plane kernel, from one ncu capture of a launch with every
 # system active (k_plane_r: 22.89 MB read + 7 KB written for 252 systems;
@@ -556,7 +577,7 @@ TRAFFIC_PER_UNIT_FP32 = (22.888e6 + 7.2e3) / 252
 TRAFFIC_PER_UNIT_DF64 = (41.832e6 + 4.479e6) / 251
 
 
-def roofline(d, geom, peaks):
+def roofline(d, geom, peaks, alu, dev):
     """Roofline of the plane pass (the H_k application of the Sternheimer CG),
     from the library's CUDA events over the timed steps: achieved = algorithmic
     flops of the units (system-plane passes) the launches processed / their
@@ -574,10 +595,12 @@ def roofline(d, geom, peaks):
         gbs = d["units_fp32"] * b32 / t / 1e9
         entries.append((d["ms_fp32"], {
             "kernel": "k_plane_r<48,48> (H_k plane pass of the FP32 CG)", "bound": "alu",
-            "achieved": tfl, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tfl / FP32_PEAK_TFLOPS,
+            "achieved": tfl, "peak": alu["fp32"], "unit": "TFLOP/s", "frac": tfl / alu["fp32"],
             "traffic": TRAFFIC_PER_UNIT_FP32 * d["units_fp32"] / calls if geom[:3] == (48, 48, 48) else None,
             "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled to the average launch)",
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+            "peak_source": f"derived: {alu['sms']} SMs (device) x 128 FP32 lanes x 2 x {alu['sm_mhz']:.0f} MHz "
+                           f"(median SM clock sampled during the timed steps)",
+            "measured_fma_tflops": dev["fp32_fma_tflops"], "measured_butterfly_tflops": dev["fp32_butterfly_tflops"],
             "total_ms": d["ms_fp32"], "avg_launch_ms": d["ms_fp32"] / calls,
             "units_per_launch": d["units_fp32"] / calls, "algorithmic_flops_per_unit": f32,
             "algorithmic_bytes_per_unit": b32, "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / peaks["hbm_gbs"]}))
@@ -587,13 +610,14 @@ def roofline(d, geom, peaks):
         tfl = d["units_fp64"] * f64 / t / 1e12
         entries.append((d["ms_fp64"], {
             "kernel": "k_plane_t<dfloat,48,48> (FP64-accurate plane pass, double-float on the FP32 pipe)",
-            "bound": "alu", "achieved": tfl, "peak": DF64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64-equivalent)",
-            "frac": tfl / DF64_PEAK_TFLOPS,
+            "bound": "alu", "achieved": tfl, "peak": alu["df64"], "unit": "TFLOP/s (FP64-equivalent)",
+            "frac": tfl / alu["df64"],
             "traffic": TRAFFIC_PER_UNIT_DF64 * d["units_fp64"] / calls if geom[:3] == (48, 48, 48) else None,
             "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled to the average launch)",
-            "peak_source": f"derived: FP32 instruction peak / {DF64_INSTR_PER_FLOP:.2f} FP32 instructions "
-                           f"per double-float flop",
-            "vs_native_fp64_peak": tfl / FP64_PEAK_TFLOPS,
+            "peak_source": f"derived: FP32 instruction peak ({alu['sms']} SMs x 128 x {alu['sm_mhz']:.0f} MHz) / "
+                           f"{DF64_INSTR_PER_FLOP:.2f} FP32 instructions per double-float flop",
+            "measured_butterfly_tflops": dev["df64_butterfly_tflops"],
+            "vs_measured_fp64_fma": tfl / dev["fp64_fma_tflops"],
             "total_ms": d["ms_fp64"], "avg_launch_ms": d["ms_fp64"] / calls,
             "units_per_launch": d["units_fp64"] / calls, "algorithmic_flops_per_unit": f64,
             "algorithmic_bytes_per_unit": b64}))
@@ -607,50 +631,76 @@ def roofline(d, geom, peaks):
 
 
 # ------------------------------------------------------------ CPU baseline --
-def cpu_baseline(system, e_applies):
-    """The oracle, as it stands, on a bounded sample of the workload: its exact
-    chi0 (pseudo-inverse Sternheimer solutions from dense diagonalisation) for
-    the first k-point, scaled to a full E application (x number of k-points,
-    plus one K^Hxc application) and to a solve (x the E applications the GPU
-    solve used).  Dense diagonalisation (setup) is not timed."""
+def oracle_solves(system, n, tau=TAU, m=M):
+    """The oracle, as it stands, solving the bench's Dyson equation n times on
+    the host cores: the ground state by dense diagonalisation of every H_k
+    (setup, untimed), b = chi0 dV0 / ||chi0 dV0||, then restarted GMRES(m) with
+    exact E applications (chi0 from the pseudo-inverse Sternheimer solutions of
+    the full eigendecomposition) until ||b - E x|| <= tau.  Returns the wall
+    times of the solves, the E applications of one solve, the setup time and
+    the true residual of the last solution."""
     import numpy as np
-    from oracle import groundstate as ogs, response as oresp
+    from oracle import gmres, groundstate as ogs, response as oresp
     from workloads import perturbation
+    t0 = time.time()
+    gs = ogs.solve(system)
+    b = oresp.chi0(gs, perturbation(system))
+    b /= np.linalg.norm(b)
+    kxc = oresp.exchange_kernel(gs.rho)
+    setup = time.time() - t0
+    count = [0]
+
+    def E(v):
+        count[0] += 1
+        return oresp.dielectric(gs, v, kxc)
+
+    times = []
+    x = None
+    for _ in range(n):
+        count[0] = 0
+        t0 = time.time()
+        x, _ = gmres.gmres(E, b, tol=tau, m=m)
+        times.append(time.time() - t0)
+    true = float(np.linalg.norm(b - oresp.dielectric(gs, x, kxc)))
+    return times, count[0], setup, true
+
+
+def _sample_text(n_e, setup, true, nsolves):
+    return (f"{nsolves} full oracle solve(s) of the workload: GMRES(m={M}) with exact E applications "
+            f"({n_e} per solve, exact chi0 over all k-points from the dense eigendecomposition) to "
+            f"||b - E x|| <= {TAU:g} (true residual {true:.2e}); dense diagonalisation untimed ({setup:.1f} s)")
+
+
+def cpu_baseline(system):
+    """One full oracle solve of the bench problem on the host cores (about
+    10-40 s of CPU work), reported beside the GPU number."""
     cores = len(os.sched_getaffinity(0))
-    k0 = system.kpoints[:1]
-    sub = type(system)(**{**system.__dict__, "kpoints": k0, "kweights": np.ones(1)})
-    gs = ogs.solve(sub)
-    dV = perturbation(system)
-    t0 = time.time()
-    oresp.chi0(gs, dV)
-    t_k = time.time() - t0
-    t0 = time.time()
-    oresp.apply_K(dV, gs)
-    t_K = time.time() - t0
-    t_E = len(system.kpoints) * t_k + t_K
-    return {"value": t_E * e_applies, "unit": "s", "cores": cores, "kind": "oracle",
-            "sample": f"oracle chi0 of k-point 1 of {len(system.kpoints)} ({t_k:.2f} s) + one K apply "
-                      f"({t_K:.3f} s), scaled x{len(system.kpoints)} k-points and x{e_applies} E applications "
-                      f"of one solve"}
+    times, n_e, setup, true = oracle_solves(system, 1)
+    return {"value": times[0], "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": _sample_text(n_e, setup, true, 1)}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle (there is no reference implementation to
+    install; the reference holds only the paper), on the bench's workload,
+    metric and unit.  Each timed step is one full oracle solve; at most 3 are
+    timed (steps reports how many) so that the run ends within a few minutes;
+    value is their median."""
     if rank != 0:
         return
     from workloads import make_system
     s = make_system(WORKLOAD)
-    e_applies = 20   # E applications of one solve at tau = 1e-8 (GPU solve: 19 + restart residual)
-    vals = []
-    cb = None
-    for _ in range(max(args.steps, 1)):
-        cb = cpu_baseline(s, e_applies)
-        vals.append(cb["value"])
-    v = statistics.median(vals)
-    cb["value"] = v
-    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False, "scaling": "weak",
+    n = max(1, min(args.steps, 3))
+    times, n_e, setup, true = oracle_solves(s, n)
+    v = statistics.median(times)
+    cores = len(os.sched_getaffinity(0))
+    cb = {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": _sample_text(n_e, setup, true, n)}
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": n,
+           "warmup": 0, "ms_per_step": 1e3 * v, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD + ": " + WORKLOAD_DESC, "parallelism": "CPU oracle"},
+           "config": {"workload": WORKLOAD + ": " + WORKLOAD_DESC, "tau": TAU, "m": M,
+                      "parallelism": f"CPU oracle, {cores} host cores"},
+           "step_times_s": times, "setup_s": setup,
            "cpu_baseline": cb, "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

@@ -231,6 +231,17 @@ ikr_status ikr_projection_coefficients(ikr_ctx* ctx, int k, int nvec, const void
  * overwritten.  Errors as ikr_projection_coefficients. */
 ikr_status ikr_project_out(ikr_ctx* ctx, int k, int nvec, void* y, int method, cudaStream_t stream);
 
+/* Arithmetic throughput of the current device, measured by FMA-chain and
+ * radix-4 butterfly kernels timed with CUDA events on `stream` (about 0.1 s).
+ * The paper has no counterpart: these are the measured references of the ALU
+ * rooflines of the plane passes, whose grid stays on chip.  out: HOST, 6
+ * doubles: [0] number of SMs, [1] FP32 FMA TFLOP/s, [2] FP64 FMA TFLOP/s,
+ * [3] FP32 and [4] double-float radix-4 butterflies in TFLOP/s (3 complex
+ * products and 8 complex sums = 34 real flops per butterfly, a double-float
+ * operation counted as one flop), [5] the device's reported SM clock in MHz.
+ * IKR_ERR_ARG for NULL, IKR_ERR_CUDA if a launch fails. */
+ikr_status ikr_device_peaks(double* out, cudaStream_t stream);
+
 /* Host utility (no GPU): eigenvalues w (ascending, n) and eigenvectors v
  * (column j = eigenvector of w[j]; row-major n x n complex, interleaved) of the
  * Hermitian matrix a (row-major n x n complex, interleaved), by the cyclic
@@ -253,7 +264,10 @@ ikr_status ikr_groundstate_info(const ikr_ctx* ctx, double* f, int* nocc, double
  *   H_k psi = |k+G|^2/2 psi + F_k (V . F_k^{-1} psi)
  * with F^{-1} = w^{-1} W^{-1} Z and F = w Z^T W (eq. fft_ifft).
  * psi, hpsi: DEVICE, Nb_k x nvec complex128 (IKR_FP64) or complex64 (IKR_MIXED:
- * arithmetic in FP32).  psi and hpsi must not overlap. */
+ * arithmetic in FP32).  psi and hpsi must not overlap.  IKR_ERR_ARG for a
+ * grid whose Nx x Ny plane has no compiled kernel shape and does not fit in a
+ * block's shared memory (the shapes compiled are 10x12, 12x12, 24x24, 32x32,
+ * 40x40, 48x48 and 96x96). */
 ikr_status ikr_apply_hamiltonian(ikr_ctx* ctx, int k, const void* psi, void* hpsi, int nvec,
                                  int precision, cudaStream_t stream);
 
@@ -266,9 +280,14 @@ ikr_status ikr_apply_hamiltonian(ikr_ctx* ctx, int k, const void* psi, void* hps
  * allocator.  The context itself is created beforehand (that allocates).
  * Scratch: one static 32 MiB device array in the library, which every GPU
  * that loads the library holds until the process exits.  Each vector needs
- * 2 * 16 * N3 * ncols bytes (ncols from ikr_fft_geometry); vectors are
+ * 2 * 16 * N3 * ncp bytes (ncp: ncols of ikr_fft_geometry rounded up to a
+ * multiple of 16); vectors are
  * processed in chunks that fit, and a grid whose single vector does not fit
- * is rejected with IKR_ERR_ARG.  The first call on a device looks up the
+ * is rejected with IKR_ERR_ARG.  The plane pass is the one
+ * ikr_apply_hamiltonian runs (the compiled kernel of the grid's plane shape
+ * where there is one); a grid without one whose plane does not fit in a
+ * block's shared memory (about Nx, Ny > 85) is rejected with IKR_ERR_ARG, as
+ * by ikr_apply_hamiltonian.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current:
  * make that first call before any stream capture.  All calls in the process
  * share the array and its contents persist between calls; calls that overlap

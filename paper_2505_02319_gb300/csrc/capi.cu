@@ -269,6 +269,18 @@ ikr_status ikr_compute_eigenpairs(ikr_ctx* c, int nbands, double tol, int maxit,
   return s;
 }
 
+ikr_status ikr_device_peaks(double* out, cudaStream_t stream) {
+  if (!out) return IKR_ERR_ARG;
+  try {
+    ikr::device_peaks(out, stream);
+  } catch (const ikr::Error& e) {
+    return e.status;
+  } catch (...) {
+    return IKR_ERR_CUDA;
+  }
+  return IKR_OK;
+}
+
 ikr_status ikr_hermitian_eigh(int n, const double* a, double* w, double* v) {
   if (n < 1 || !a || !w || !v) return IKR_ERR_ARG;
   try {

@@ -19,6 +19,17 @@
 
 namespace ikr {
 
+// shared memory a block may use on sm_103a, and the error for a plane of a grid
+// with no compiled shape that does not fit (the runtime-size plane kernel keeps
+// the whole Ny x Nx plane twice)
+constexpr size_t kMaxPlaneSmem = 227 * 1024;
+static std::string plane_smem_message(const ikr_ctx* c, size_t smem) {
+  return "the " + std::to_string(c->N[0]) + " x " + std::to_string(c->N[1]) +
+         " grid plane has no compiled kernel shape and needs " + std::to_string(smem) +
+         " bytes of shared memory, more than the " + std::to_string(kMaxPlaneSmem) + " a block may use";
+}
+
+
 namespace {
 
 template <typename R> const C_t<R>* tw_ptr(ikr_ctx* c, int axis);
@@ -521,6 +532,7 @@ void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, 
   if (launch_plane_fast<R>(c, L.n, b1, pot, pot_scale, active, b4, real_in)) return;
   const int Nx = c->N[0], Ny = c->N[1], Nz = c->N[2];
   const size_t smem = sizeof(C_t<R>) * (Nx + Ny + 2 * (size_t)Ny * (Nx + 1)) + sizeof(int) * c->nxa;
+  IKR_REQUIRE(smem <= kMaxPlaneSmem, IKR_ERR_ARG, plane_smem_message(c, smem));
   set_smem(k_plane<R>, smem);
   dim3 grid(Nz, L.n);
   k_plane<R><<<grid, 256, smem, c->stream>>>(b1, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa,
@@ -703,17 +715,22 @@ void launch_hamiltonian_raw(ikr_ctx* c, int n, const int* d_sysk, const double2*
   const size_t smz = sizeof(double2) * (Nz + 2 * LZ * (Nz + 1));
   const size_t smp = sizeof(double2) * (Nx + Ny + 2 * (size_t)Ny * (Nx + 1)) + sizeof(int) * c->nxa;
   set_smem(k_z_inverse<double>, smz);
-  set_smem(k_plane<double>, smp);
   set_smem(k_z_forward<double>, smz);
   dim3 gz((c->nc + LZ - 1) / LZ, n);
   k_z_inverse<double><<<gz, 256, smz, c->stream>>>(psi, ld, d_sysk, c->k_colinfo.p, c->nc, c->ncp, c->plan[2],
                                                    c->d_tw[2].p, nullptr, LZ, b1);
   IKR_CUDA(cudaGetLastError());
-  dim3 gp(Nz, n);
-  k_plane<double><<<gp, 256, smp, c->stream>>>(b1, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa, c->plan[0],
-                                               c->plan[1], Nz, c->d_tw[0].p, c->d_tw[1].p, c->d_Vt.p, nullptr,
-                                               nullptr, b4, nullptr);
-  IKR_CUDA(cudaGetLastError());
+  // the compiled plane shape where there is one (what ikr_apply_hamiltonian runs), else the
+  // runtime-size kernel, whose whole plane must fit in shared memory
+  if (!launch_plane_fast<double>(c, n, b1, c->d_Vt.p, nullptr, nullptr, b4, nullptr)) {
+    IKR_REQUIRE(smp <= kMaxPlaneSmem, IKR_ERR_ARG, plane_smem_message(c, smp));
+    set_smem(k_plane<double>, smp);
+    dim3 gp(Nz, n);
+    k_plane<double><<<gp, 256, smp, c->stream>>>(b1, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa,
+                                                 c->plan[0], c->plan[1], Nz, c->d_tw[0].p, c->d_tw[1].p,
+                                                 c->d_Vt.p, nullptr, nullptr, b4, nullptr);
+    IKR_CUDA(cudaGetLastError());
+  }
   k_z_forward<double><<<gz, 256, smz, c->stream>>>(b4, c->nc, c->ncp, d_sysk, c->k_colinfo.p, c->plan[2],
                                                    c->d_tw[2].p, LZ, hpsi, ld, c->ld, psi, nullptr,
                                                    c->d_kin_all.p, nullptr, nullptr);

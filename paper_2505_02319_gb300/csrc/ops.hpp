@@ -143,4 +143,9 @@ void grid_max(ikr_ctx* c, const double* v, size_t n, double* dout);
 void to_fp32(ikr_ctx* c, const double2* in, size_t n, float2* out);
 void to_fp64(ikr_ctx* c, const float2* in, size_t n, double2* out);
 
+// measured arithmetic throughput of the current device (peaks.cu): out[0] SMs,
+// [1] FP32 FMA TFLOP/s, [2] FP64 FMA TFLOP/s, [3] FP32 and [4] double-float radix-4
+// butterfly TFLOP/s, [5] the device's reported maximum SM clock in MHz
+void device_peaks(double* out, cudaStream_t st);
+
 }  // namespace ikr

@@ -107,6 +107,7 @@ def _load():
         "ikr_profile_start": (I, [P, ct.c_uint]),
         "ikr_profile_read": (I, [P, ct.POINTER(KernelStat), I]),
         "ikr_fft_geometry": (I, [P, ct.POINTER(I)]),
+        "ikr_device_peaks": (I, [ct.POINTER(ct.c_double), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -153,6 +154,19 @@ def default_opts(**kw):
             v = {"fp64": FP64, "mixed": MIXED}[v]
         setattr(o, k, v)
     return o
+
+
+def device_peaks():
+    """Measured arithmetic throughput of the current device (ikr_device_peaks):
+    SMs, FP32 and FP64 FMA TFLOP/s, FP32 and double-float radix-4 butterfly
+    TFLOP/s, and the device's reported SM clock (MHz)."""
+    out = (ct.c_double * 6)()
+    st = _LIB.ikr_device_peaks(out, _stream())
+    if st != IKR_OK:
+        raise IkrError(st, "device_peaks failed")
+    keys = ("sms", "fp32_fma_tflops", "fp64_fma_tflops", "fp32_butterfly_tflops", "df64_butterfly_tflops",
+            "sm_clock_mhz")
+    return {k: (int(v) if k == "sms" else float(v)) for k, v in zip(keys, out)}
 
 
 class Context:

@@ -46,23 +46,28 @@ def test_single_process_and_efficiency():
 
 def test_roofline_picks_dominant_kernel_and_scales_traffic():
     """The roofline object: algorithmic flops of the units over the summed event
-    time, against the derived FP32 / double-float peaks; the kernel with the
-    larger total time is reported and the other attached; the DRAM traffic of a
-    launch scales with the units it processed."""
+    time, against the FP32 / double-float peaks derived from the device's SM
+    count and the sampled clock; the kernel with the larger total time is
+    reported and the other attached; the DRAM traffic of a launch scales with
+    the units it processed."""
     import bench
     geom = (48, 48, 48, 288, 20)
     peaks = {"hbm_gbs": 6800.0}
+    dev = {"sms": 152, "fp32_fma_tflops": 78.0, "fp64_fma_tflops": 1.2, "fp32_butterfly_tflops": 60.0,
+           "df64_butterfly_tflops": 6.5, "sm_clock_mhz": 2070.0}
+    alu = bench.alu_peaks(dev, 2070.0)
+    assert math.isclose(alu["fp32"], 152 * 128 * 2 * 2.07e9 / 1e12)
+    assert math.isclose(alu["df64"], alu["fp32"] / 2 / bench.DF64_INSTR_PER_FLOP)
     d = dict(ms_fp32=20.0, units_fp32=40000, calls_fp32=300, ms_fp64=25.0, units_fp64=7000, calls_fp64=35)
-    r = bench.roofline(d, geom, peaks)
+    r = bench.roofline(d, geom, peaks, alu, dev)
     assert r["kernel"].startswith("k_plane_t<dfloat")                    # 25 ms > 20 ms
     _, f64 = bench.plane_pass_work(geom, 8)
     assert math.isclose(r["achieved"], 7000 * f64 / 25e-3 / 1e12, rel_tol=1e-12)
-    assert math.isclose(r["frac"], r["achieved"] / bench.DF64_PEAK_TFLOPS, rel_tol=1e-12)
+    assert math.isclose(r["frac"], r["achieved"] / alu["df64"], rel_tol=1e-12)
     assert math.isclose(r["traffic"], bench.TRAFFIC_PER_UNIT_DF64 * 7000 / 35, rel_tol=1e-12)
     o = r["other_plane_kernel"]
     _, f32 = bench.plane_pass_work(geom, 4)
-    assert math.isclose(o["frac"], 40000 * f32 / 20e-3 / 1e12 / bench.FP32_PEAK_TFLOPS, rel_tol=1e-12)
-    assert math.isclose(bench.FP32_PEAK_TFLOPS, 152 * 128 * 2 * 2.07e9 / 1e12)
+    assert math.isclose(o["frac"], 40000 * f32 / 20e-3 / 1e12 / alu["fp32"], rel_tol=1e-12)
     # another grid: no traffic figure (the captures are of the 48^3 grid)
-    assert bench.roofline(d, (32, 32, 32, 200, 15), peaks)["traffic"] is None
-    assert bench.roofline(dict(d, ms_fp64=0.0, units_fp64=0), geom, peaks)["kernel"].startswith("k_plane_r")
+    assert bench.roofline(d, (32, 32, 32, 200, 15), peaks, alu, dev)["traffic"] is None
+    assert bench.roofline(dict(d, ms_fp64=0.0, units_fp64=0), geom, peaks, alu, dev)["kernel"].startswith("k_plane_r")

@@ -19,7 +19,7 @@ def test_cfg3_kerker_mixed_solve_true_residual():
     from paper_2505_02319_gb300 import groundstate
     from workloads import perturbation
     s = system("cfg3")
-    ctx = groundstate.context_for(s, eigensolver="chfsi", eig_tol=1e-9)
+    ctx = groundstate.context_for(s, eig_tol=1e-9)
     assert max(ctx.eig_residuals) <= 1e-9
     nocc = ctx.groundstate_info(ctx.nbands, s.n_grid)["nocc"]
     assert nocc.max() < ctx.nbands and nocc.sum() > 900

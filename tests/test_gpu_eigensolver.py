@@ -5,6 +5,7 @@ FP64 parity tolerance, and the cfg2 spectrum against the dense GPU path."""
 import numpy as np
 import pytest
 
+import gpu_common
 from gpu_common import dev, oracle_state, rel, system
 
 pytestmark = pytest.mark.gpu
@@ -12,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 def _ctx(name, **kw):
     from paper_2505_02319_gb300 import groundstate
-    return groundstate.context_for(system(name), eigensolver="chfsi", **kw)
+    return groundstate.context_for(system(name), **kw)
 
 
 @pytest.mark.parametrize("name", ["tiny_insulator", "tiny_ortho_k", "tiny_metal", "cfg1"])
@@ -37,5 +38,5 @@ def test_cfg2_spectrum_matches_dense():
     ctx = _ctx("cfg2")
     ev_chfsi, res = ctx.eigenvalues, ctx.eig_residuals
     assert max(res) <= 1e-10
-    ev_dense, _ = groundstate.dense_eigenpairs(ctx, s.nbands)
+    ev_dense, _ = gpu_common.dense_eigenpairs(ctx, s.nbands)
     assert np.max(np.abs(ev_chfsi - ev_dense)) < 1e-9

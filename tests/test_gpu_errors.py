@@ -6,6 +6,7 @@ import ctypes as ct
 import numpy as np
 import pytest
 
+import gpu_common
 from gpu_common import context, dev, system, torch
 
 pytestmark = pytest.mark.gpu
@@ -23,13 +24,13 @@ def test_no_gap_is_reported():
     s = system("tiny_insulator")
     ctx = ikr.Context.setup_groundstate(s.lattice, s.dims, s.Ecut, s.kpoints, s.kweights, s.V,
                                         s.temperature, s.n_electrons)
-    ev, vecs = groundstate.dense_eigenpairs(ctx, 4)
+    ev, vecs = gpu_common.dense_eigenpairs(ctx, 4)
     ev = ev.copy()
     ev[0, 2] = ev[0, 1]            # degenerate HOMO/LUMO
     with pytest.raises(ikr.IkrError) as e:
         ctx.set_eigenpairs(ev, vecs)
     assert e.value.status == ikr.IKR_ERR_NOGAP
-    ctx.set_eigenpairs(*groundstate.dense_eigenpairs(ctx, 4))   # still usable
+    ctx.set_eigenpairs(*gpu_common.dense_eigenpairs(ctx, 4))   # still usable
 
 
 def test_nonfinite_rhs_is_numeric_error():

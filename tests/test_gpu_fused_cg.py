@@ -10,6 +10,7 @@ import os
 import numpy as np
 import pytest
 
+import gpu_common
 from gpu_common import dev, oracle_state, system
 
 pytestmark = pytest.mark.gpu
@@ -19,7 +20,7 @@ def _run(name, b, fused):
     from paper_2505_02319_gb300 import groundstate
     os.environ["IKR_CG_FUSED"] = "1" if fused else "0"
     try:
-        ctx = groundstate.context_for(system(name))
+        ctx = gpu_common.dense_context_for(system(name))
         ctx.profile_start()
         x, rep = ctx.solve_response(dev(b), tau=1e-8, strategy="grt_exact", precision="mixed")
         prof = ctx.profile_read()

@@ -26,7 +26,7 @@ def test_kb_hamiltonian_fp32():
 def test_kb_eigensolver_matches_oracle():
     from paper_2505_02319_gb300 import groundstate
     s, gs = system("tiny_kb"), oracle_state("tiny_kb")
-    ctx = groundstate.context_for(s, eigensolver="chfsi", eig_tol=1e-11)
+    ctx = groundstate.context_for(s, eig_tol=1e-11)
     for k, kb in enumerate(gs.kblocks):
         assert np.max(np.abs(ctx.eigenvalues[k] - kb.eps[:ctx.nbands])) < 1e-10
 

@@ -8,15 +8,20 @@ take fewer Hamiltonian applications than the plain projected CG."""
 import numpy as np
 import pytest
 
+import gpu_common
 from gpu_common import dev, oracle_state, rel, system, torch
 
 pytestmark = pytest.mark.gpu
 
 
-def _context(name, **kw):
+def _context(name, dense=True, **kw):
+    """dense: the ground state of the dense diagonalisation (test helper); else
+    the library's eigensolver."""
     import __graft_entry__
     __graft_entry__.build()
     from paper_2505_02319_gb300 import groundstate
+    if dense:
+        return gpu_common.dense_context_for(system(name), **kw)
     return groundstate.context_for(system(name), **kw)
 
 
@@ -36,7 +41,7 @@ def test_schur_chi0_with_gpu_eigenpairs():
     from oracle import response
     from workloads import perturbation
     s, gs = system("tiny_kb"), oracle_state("tiny_kb")
-    ctx = _context("tiny_kb", eigensolver="chfsi", eig_tol=1e-11, schur=True)
+    ctx = _context("tiny_kb", dense=False, eig_tol=1e-11, schur=True)
     dV = perturbation(s)
     d_gpu, _ = ctx.apply_chi0(dev(dV), tol=None)
     assert rel(d_gpu.cpu().numpy(), response.chi0(gs, dV)) < 1e-9
@@ -60,7 +65,7 @@ def test_schur_mixed_solve_reaches_tau(name):
 def test_schur_needs_fewer_hamiltonian_applications_on_cfg1():
     from workloads import perturbation
     s = system("cfg1")
-    ctx = _context("cfg1", eigensolver="chfsi")
+    ctx = _context("cfg1", dense=False)
     nsys = ctx.groundstate_nsys
     b, _ = ctx.apply_chi0(dev(perturbation(s)), tol=np.full(nsys, 1e-12))
     b = (b / torch.linalg.norm(b)).contiguous()

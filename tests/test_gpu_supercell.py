@@ -8,6 +8,7 @@ insulator then runs the mixed-precision solve with the guaranteed rule."""
 import numpy as np
 import pytest
 
+import gpu_common
 from gpu_common import dev, oracle_state, rel, system, torch
 
 pytestmark = pytest.mark.gpu
@@ -16,10 +17,9 @@ pytestmark = pytest.mark.gpu
 def _supercell_context(name, ell, **kw):
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2505_02319_gb300 import groundstate
     from workloads import supercell
     S = supercell(system(name), ell, **kw)
-    return S, groundstate.context_for(S)
+    return S, gpu_common.dense_context_for(S)
 
 
 @pytest.mark.parametrize("name", ["tiny_ortho_k", "tiny_metal"])

@@ -6,14 +6,14 @@ the mixed-precision Dyson solve with the tensor-core projections reaching tau.""
 import numpy as np
 import pytest
 
+import gpu_common
 from gpu_common import context, dev, oracle_state, system, torch
 
 pytestmark = pytest.mark.gpu
 
 
 def _orbitals(ctx, name):
-    from paper_2505_02319_gb300 import groundstate
-    _, vecs = groundstate.dense_eigenpairs(ctx, ctx.nbands)
+    _, vecs = gpu_common.dense_eigenpairs(ctx, ctx.nbands)
     return vecs
 
 
@@ -87,7 +87,7 @@ def test_tensor_cores_with_schur_sets_in_chi0():
     from workloads import perturbation
     s, gs = system("tiny_metal"), oracle_state("tiny_metal")
     from paper_2505_02319_gb300 import groundstate
-    ctx = groundstate.context_for(s, schur=True)
+    ctx = gpu_common.dense_context_for(s, schur=True)
     ctx.set_tensor_cores(True)
     dV = perturbation(s)
     nsys = ctx.groundstate_nsys

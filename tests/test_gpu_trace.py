@@ -14,6 +14,7 @@ import os
 import numpy as np
 import pytest
 
+import gpu_common
 from gpu_common import context, dev, system, torch
 
 pytestmark = pytest.mark.gpu
@@ -65,7 +66,7 @@ def test_cfg1_fp64_solve_follows_the_oracle(schur):
     name = "cfg1_bal_schur_fp64.txt" if schur else "cfg1_bal_fp64.txt"
     g = _golden(os.path.join(os.path.dirname(GOLDEN), name))
     s = system("cfg1")
-    ctx = groundstate.context_for(s, schur=schur)
+    ctx = gpu_common.dense_context_for(s, schur=schur)
     nsys = ctx.groundstate_nsys
     b, _ = ctx.apply_chi0(dev(perturbation(s)), tol=np.full(nsys, 1e-12))
     b = (b / torch.linalg.norm(b)).contiguous()
@@ -92,7 +93,7 @@ def test_metallic_slab_kerker_solve_follows_the_oracle():
     from workloads import make_system, perturbation, with_cutoff, with_kgrid
     g = _golden(os.path.join(os.path.dirname(GOLDEN), "slab_bal_kerker_fp64.txt"))
     s = with_cutoff(with_kgrid(make_system("cfg3"), (2, 2, 1)), 2.5, (12, 12, 64))
-    ctx = groundstate.context_for(s)
+    ctx = gpu_common.dense_context_for(s)
     nsys = ctx.groundstate_nsys
     b, _ = ctx.apply_chi0(dev(perturbation(s)), tol=np.full(nsys, 1e-12))
     b = (b / torch.linalg.norm(b)).contiguous()
@@ -119,7 +120,7 @@ def test_cfg2_schur_fp64_solve_follows_the_oracle():
     from workloads import perturbation
     g = _golden(os.path.join(os.path.dirname(GOLDEN), "cfg2_bal_schur_fp64.txt"))
     s = system("cfg2")
-    ctx = groundstate.context_for(s, schur=True)
+    ctx = gpu_common.dense_context_for(s, schur=True)
     nsys = ctx.groundstate_nsys
     b, _ = ctx.apply_chi0(dev(perturbation(s)), tol=np.full(nsys, 1e-12))
     b = (b / torch.linalg.norm(b)).contiguous()
