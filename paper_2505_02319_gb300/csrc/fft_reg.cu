@@ -243,12 +243,167 @@ __global__ void __launch_bounds__(RegGeom<NX, NY>::NTH)
   }
 }
 
+// Compact variant for z-transformed input (the CG's H_k applications): shared
+// memory holds only the nxa active x positions of every row, column l at
+// shifted position pxlo + l (setup checks that the active positions form one
+// run).  The y-lines act only on those columns, and an x-line reads and writes
+// only them as well (its inactive inputs are zero, its inactive outputs are
+// dropped), so nothing else of the plane is ever needed: ~42 KB per block of
+// PL = 4 systems instead of ~85 KB.  With PL NY / 2 threads every thread takes
+// two rows of the x phase and at most one line of each y phase (544 line
+// transforms in 6 transform-times for 96 threads, against 4 for 192 threads
+// with 58 % of them idle in the y phases), and five blocks fit an SM.
+// Bank layout as RegGeom: odd row stride, plane stride 4 mod 16 elements.
+template <int NX, int NY> struct RcGeom {
+  static constexpr int PL = 4;
+  static constexpr int NTH = (PL * NY / 2 + 31) / 32 * 32;
+  static constexpr int ldp = NX | 1;                      // potential row stride
+  static constexpr int SH = NX / 2;
+  __host__ __device__ static constexpr int ldc(int nxa) { return nxa | 1; }
+  __host__ __device__ static constexpr int ps(int nxa) {
+    return NY * (nxa | 1) + ((4 - NY * (nxa | 1)) % 16 + 16) % 16;
+  }
+  static size_t smem(int nxa) {
+    return sizeof(float2) * (size_t)PL * ps(nxa) + sizeof(float) * (size_t)NY * ldp + sizeof(int) * 3 * (size_t)nxa;
+  }
+};
+
+template <int NX, int NY, int MINB>
+__global__ void __launch_bounds__(RcGeom<NX, NY>::NTH, MINB)
+    k_plane_rc(const float2* __restrict__ b1, int nc, int ncp, const int* __restrict__ col_xy,
+               const int* __restrict__ xr, int nxa, int pxlo, unsigned long long xmask, int Nz,
+               const float* __restrict__ pot, const double* __restrict__ pot_scale,
+               const int* __restrict__ active, int nsys, const int* __restrict__ list,
+               float2* __restrict__ b4) {
+  using G = RcGeom<NX, NY>;
+  constexpr int PL = G::PL, NTH = G::NTH, ldp = G::ldp, SH = G::SH;
+  const int ldc = G::ldc(nxa), PS = G::ps(nxa);
+  const int iz = blockIdx.x;
+  __shared__ int live[PL];   // system of slot j, or -1
+  extern __shared__ float4 smem_rc[];
+  float2* planes = reinterpret_cast<float2*>(smem_rc);
+  float* pot_s = reinterpret_cast<float*>(planes + PL * PS);
+  int* xr_s = reinterpret_cast<int*>(pot_s + NY * ldp);
+  if (threadIdx.x < PL) {
+    const int i = blockIdx.y * PL + threadIdx.x;
+    int s = -1;
+    if (i < nsys) {
+      s = list ? list[i] : i;
+      if (active && !active[s]) s = -1;
+    }
+    live[threadIdx.x] = s;
+  }
+  __syncthreads();
+  int nlive = 0;
+#pragma unroll
+  for (int j = 0; j < PL; ++j) nlive += live[j] >= 0;
+  if (nlive == 0) return;   // uniform over the block
+  const float2 zero = make_float2(0.f, 0.f);
+  const int2* cxy = reinterpret_cast<const int2*>(col_xy);
+  for (int e = threadIdx.x; e < NY * NX; e += NTH) {
+    const int iy = e / NX, ix = e - iy * NX;
+    cp_async4(pot_s + iy * ldp + ix, pot + (size_t)iz * NY * NX + e);
+  }
+  for (int e = threadIdx.x; e < 3 * nxa; e += NTH) cp_async4(xr_s + e, xr + e);
+  for (int e = threadIdx.x; e < PL * nc; e += NTH) {
+    const int j = e / nc, col = e - j * nc;
+    if (live[j] < 0) continue;
+    const int2 xy = cxy[col];
+    const int px = xy.x + SH >= NX ? xy.x + SH - NX : xy.x + SH;
+    cp_async8(planes + j * PS + xy.y * ldc + (px - pxlo), b1 + ((size_t)live[j] * Nz + iz) * ncp + col);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // inverse y-lines of the active columns (column l: only its y-interval is non-zero)
+  for (int it = threadIdx.x; it < PL * nxa; it += NTH) {
+    const int l = it / PL, j = it - l * PL;
+    if (live[j] < 0) continue;
+    const int ylo = xr_s[3 * l + 1], span = xr_s[3 * l + 2];
+    float2* colp = planes + j * PS + l;
+    float2 v[NY];
+#pragma unroll
+    for (int y = 0; y < NY; ++y) {
+      int d = y - ylo;
+      d += d < 0 ? NY : 0;
+      v[y] = d <= span ? colp[y * ldc] : zero;
+    }
+    CtFft<float2, NY, true>::run(v);
+#pragma unroll
+    for (int y = 0; y < NY; ++y) colp[y * ldc] = v[y];
+  }
+  __syncthreads();
+  // x-lines: inverse transform of the active inputs, potential, forward transform,
+  // active outputs kept; shifted position (x + SH) mod NX sits at column (that - pxlo)
+  {
+    const float sc = pot_scale ? (float)*pot_scale : 1.f;
+    for (int it = threadIdx.x; it < PL * NY; it += NTH) {
+      const int iy = it / PL, j = it - iy * PL;
+      if (live[j] < 0) continue;
+      const int base = j * PS + iy * ldc - pxlo;
+      const float* prow = pot_s + iy * ldp;
+      float2 v[NX];
+#pragma unroll
+      for (int x = 0; x < NX; ++x) v[x] = ((xmask >> x) & 1ull) ? planes[base + (x + SH) % NX] : zero;
+      CtFft<float2, NX, true>::run(v);
+#pragma unroll
+      for (int x = 0; x < NX; ++x) v[x] = cscale(v[x], prow[x] * sc);
+      CtFft<float2, NX, false>::run(v);
+#pragma unroll
+      for (int x = 0; x < NX; ++x)
+        if ((xmask >> x) & 1ull) planes[base + (x + SH) % NX] = v[x];
+    }
+  }
+  __syncthreads();
+  // forward y-lines of the active columns; only the column's interval is kept
+  for (int it = threadIdx.x; it < PL * nxa; it += NTH) {
+    const int l = it / PL, j = it - l * PL;
+    if (live[j] < 0) continue;
+    const int ylo = xr_s[3 * l + 1], span = xr_s[3 * l + 2];
+    float2* colp = planes + j * PS + l;
+    float2 v[NY];
+#pragma unroll
+    for (int y = 0; y < NY; ++y) v[y] = colp[y * ldc];
+    CtFft<float2, NY, false>::run(v);
+#pragma unroll
+    for (int y = 0; y < NY; ++y) {
+      int d = y - ylo;
+      d += d < 0 ? NY : 0;
+      if (d <= span) colp[y * ldc] = v[y];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < PL * nc; e += NTH) {
+    const int j = e / nc, col = e - j * nc;
+    if (live[j] < 0) continue;
+    const int2 xy = cxy[col];
+    const int px = xy.x + SH >= NX ? xy.x + SH - NX : xy.x + SH;
+    b4[((size_t)live[j] * Nz + iz) * ncp + col] = planes[j * PS + xy.y * ldc + (px - pxlo)];
+  }
+}
+
 namespace {
 
 template <int NX, int NY>
 bool try_reg(ikr_ctx* c, int nsys, const float2* b1, const float* pot, const double* pot_scale, const int* active,
              float2* b4, const float2* real_in, const int* list) {
   if (c->N[0] != NX || c->N[1] != NY) return false;
+  if (!real_in && c->xr_contig && c->plane_rc) {
+    using H = RcGeom<NX, NY>;
+    const size_t smem = H::smem(c->nxa);
+    if (smem <= 200 * 1024) {
+      auto launch = [&](auto kern) {
+        IKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dim3 grid(c->N[2], (nsys + H::PL - 1) / H::PL);
+        kern<<<grid, H::NTH, smem, c->stream>>>(b1, c->nc, c->ncp, c->d_col_xy.p, c->d_xr.p, c->nxa, c->pxlo,
+                                               c->xmask, c->N[2], pot, pot_scale, active, nsys, list, b4);
+        IKR_CUDA(cudaGetLastError());
+      };
+      // register bound: 5 blocks per SM (128 registers) or 4 (up to 168)
+      if (c->plane_rc == 4) launch(k_plane_rc<NX, NY, 4>);
+      else launch(k_plane_rc<NX, NY, 5>);
+      return true;
+    }
+  }
   using G = RegGeom<NX, NY>;
   const size_t smem = G::smem(c->nxa);
   if (smem > 200 * 1024) return false;

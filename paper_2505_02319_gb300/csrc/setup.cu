@@ -3,6 +3,7 @@
 // Fermi level, density rho and exchange kernel K^xc[rho]).
 #include <algorithm>
 #include <array>
+#include <cstdlib>
 #include <cmath>
 #include <map>
 
@@ -203,6 +204,19 @@ void setup_system(ikr_ctx* c, const ikr_system* sys) {
     for (const auto& r : rows) xr.insert(xr.end(), r.begin(), r.end());
     c->xmask = mask;
     c->reg_plane_ok = ok;
+    // the shifted active x positions form one run px_lo, px_lo + 1, ... (a sphere's
+    // projection is an interval): the compact plane layout of k_plane_rc needs that
+    bool contig = !rows.empty();
+    for (size_t l = 0; l < rows.size(); ++l) contig = contig && rows[l][0] == rows[0][0] + (int)l;
+    c->xr_contig = contig;
+    c->pxlo = rows.empty() ? 0 : rows[0][0];
+    // IKR_PLANE_RC=0 selects the full-plane FP32 kernel instead of the compact one,
+    // IKR_PLANE_RC=4 the compact one compiled for 4 blocks per SM (read when the
+    // context is created)
+    if (const char* e = std::getenv("IKR_PLANE_RC")) {
+      const int v = std::atoi(e);
+      c->plane_rc = (v == 0 || v == 4) ? v : 5;
+    }
     upload(c->d_xr, xr, st);
   }
   // per-k column info and kinetic energies
