@@ -361,7 +361,7 @@ SUPERCELL_BUMP = (0.3, 0.6, 0.45)       # fractional position of dV0 in the base
 
 
 def supercell_study(ells, tau, m, precision):
-    """Remark rmk:scaling on the GPU: the base cell repeated ell times along a_1
+    """Remark rmk:scaling on the GPU: the base cell repeated ell times along a_3
     (Gamma point, N_occ, |Omega| and N_g linear in ell), the same localised
     Gaussian bump dV0 in every supercell, b = chi0 dV0, and every tolerance
     rule once per size.  Reports N_ham, the true residual ||b - E x|| (tight FP64
@@ -376,7 +376,7 @@ def supercell_study(ells, tau, m, precision):
     center = base.lattice @ np.array(SUPERCELL_BUMP)
     rows = []
     for ell in ells:
-        S = supercell(base, ell, kgrid=(1, 1, 1))
+        S = supercell(base, ell, axis=2, kgrid=(1, 1, 1))      # long axis z: the planes stay 32 x 32
         t0 = time.time()
         ctx = groundstate.context_for(S)
         torch.cuda.synchronize()
@@ -402,7 +402,7 @@ def supercell_study(ells, tau, m, precision):
         ctx.destroy()
         del ctx
         torch.cuda.empty_cache()
-    return {"base": SUPERCELL_BASE, "axis": 0, "kpoints": "Gamma", "tau": tau, "m": m,
+    return {"base": SUPERCELL_BASE, "axis": 2, "kpoints": "Gamma", "tau": tau, "m": m,
             "precision": "fp64" if precision == 0 else "mixed", "rows": rows}
 
 
@@ -540,21 +540,31 @@ def run_ours(args, rank, world, local_rank):
         "dominant_class": dominant,
         "setup_s": setup_s,
     }
+    def study(key, fn):
+        """Runs one optional study; its result (or its error) goes into the line and,
+        as it finishes, to stderr, so that a later failure loses nothing."""
+        try:
+            out[key] = fn()
+        except Exception as e:                       # recorded, the other studies still run
+            out[key] = {"error": f"{type(e).__name__}: {e}"}
+        sys.stderr.write(json.dumps({key: out[key]}) + "\n")
+        sys.stderr.flush()
+
     if args.strategies:
-        out["strategies"] = strategy_sweep(ctx, b, nsys, TAU, M, ikr.MIXED)
+        study("strategies", lambda: strategy_sweep(ctx, b, nsys, TAU, M, ikr.MIXED))
     if args.schur:
-        out["schur"] = schur_run(ctx, b, nsys, opts, stream, args.schur_bands)
+        study("schur", lambda: schur_run(ctx, b, nsys, opts, stream, args.schur_bands))
     if args.tensor_cores:
-        out["tensor_cores"] = tensor_core_run(ctx, b, nsys, opts, stream)
+        study("tensor_cores", lambda: tensor_core_run(ctx, b, nsys, opts, stream))
     if args.batch:
-        out["batch"] = batch_run(TAU, M, stream)
+        study("batch", lambda: batch_run(TAU, M, stream))
     if args.slab_strategies:
-        out["slab_strategies"] = slab_strategies(TAU, M)
+        study("slab_strategies", lambda: slab_strategies(TAU, M))
     if args.cfg4_guaranteed:
-        out["cfg4_guaranteed"] = cfg4_guaranteed(TAU, M)
+        study("cfg4_guaranteed", lambda: cfg4_guaranteed(TAU, M))
     if args.supercell:
-        out["supercell_study"] = supercell_study([int(v) for v in args.supercell.split(",")], 1e-9, 10,
-                                                 ikr.FP64)
+        study("supercell_study", lambda: supercell_study([int(v) for v in args.supercell.split(",")], 1e-9, 10,
+                                                         ikr.FP64))
     if rank == 0:
         out["device_peaks"] = dev
         if not args.no_cpu_baseline:

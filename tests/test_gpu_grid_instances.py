@@ -7,14 +7,13 @@ The oracle cannot diagonalise those systems at their full cut-offs, but the
 instances depend only on the grid: the same cells, atoms, k-points and grids
 at a reduced cut-off (the slab at 2.5 Ha with 2 x 2 x 1 k-points, N_b,k about
 1,100; the projector cell at 1.5 Ha with its 256 Kleinman-Bylander projectors,
-N_b about 750, Fermi-Dirac T = 0.01 Ha so that the reduced basis needs no gap)
-run exactly the kernels of the full-size runs.  Checks: H_k in FP64 (1e-12)
+N_b = 739, still an insulator: eps_129 - eps_128 = 8e-4 Ha) run exactly the
+kernels of the full-size runs.  Checks: H_k in FP64 (1e-12)
 and FP32 (2e-6) against the oracle's dense H_k, chi0 with dense ground states
 against the oracle's (1e-10), and for the slab the mixed-precision Kerker solve
 with the guaranteed rule reaching tau on ||T (b - E x)|| with the oracle's E
 (reading A10).  The slab's own reduced grid (12 x 12 x 64), which the oracle
 strategy study uses, gets the same solve check."""
-import dataclasses
 import functools
 
 import numpy as np
@@ -34,7 +33,7 @@ def reduced(name):
     elif name == "slab_study_grid":
         s = with_kgrid(with_cutoff(make_system("cfg3"), 2.5, (12, 12, 64)), (2, 2, 1))
     elif name == "kb_cell_full_grid":
-        s = dataclasses.replace(with_cutoff(make_system("cfg4"), 1.5, (96, 96, 96)), temperature=0.01)
+        s = with_cutoff(make_system("cfg4"), 1.5, (96, 96, 96))
     else:
         raise ValueError(name)
     return s

@@ -31,3 +31,17 @@ def test_with_cutoff_keeps_the_atoms_and_resamples_the_potential():
     assert np.array_equal(r.V, direct)
     # the coarse grid's points are a subset of the fine one's: the potential agrees there
     assert np.allclose(r.V[::2, ::2, ::2], s.V, atol=1e-12)
+
+
+def test_separable_gaussian_sum_equals_the_image_sum():
+    """For an orthorhombic cell the product of the three axis image sums is the
+    sum over the image box (same terms, another order)."""
+    import math
+    from workloads.systems import _gaussian_sum_images
+    for name, dims in (("tiny_ortho_k", (10, 12, 16)), ("cfg2", (24, 24, 24))):
+        s = make_system(name)
+        reach = 9.0 * s.width
+        nimg = [int(math.ceil(reach / np.linalg.norm(s.lattice[:, i]))) + 1 for i in range(3)]
+        fast = gaussian_sum_on_grid(s.lattice, dims, s.positions, -s.depth, s.width)
+        slow = _gaussian_sum_images(s.lattice, dims, s.positions, -s.depth, s.width, nimg)
+        np.testing.assert_allclose(fast, slow, rtol=1e-13, atol=1e-14 * np.abs(slow).max())

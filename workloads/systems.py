@@ -80,11 +80,34 @@ def _grid_points(lattice, dims):
 
 def gaussian_sum_on_grid(lattice, dims, centers, amplitude, width):
     """sum_c sum_R amplitude * exp(-|r - c - R|^2 / (2 width^2)) on the grid,
-    with enough periodic images R for the tail to fall below 1e-16."""
-    r = _grid_points(lattice, dims)
-    out = np.zeros(dims, dtype=np.float64)
+    with enough periodic images R for the tail to fall below 1e-16.
+
+    For an orthorhombic cell the images R = sum_a n_a a_a form a product set
+    and the Gaussian is a product over the Cartesian axes, so the image sum is
+    the product of three one-dimensional image sums (the same terms, summed in
+    another order); other cells take the direct sum over images."""
     reach = 9.0 * width
     nimg = [int(math.ceil(reach / np.linalg.norm(lattice[:, i]))) + 1 for i in range(3)]
+    lattice = np.asarray(lattice, dtype=np.float64)
+    if np.array_equal(lattice, np.diag(np.diag(lattice))):
+        out = np.zeros(dims, dtype=np.float64)
+        L = np.diag(lattice)
+        x = [np.arange(n) / n * L[a] for a, n in enumerate(dims)]
+        for c in np.atleast_2d(centers):
+            g = []
+            for a in range(3):
+                n = np.arange(-nimg[a], nimg[a] + 1, dtype=np.float64)
+                d = x[a][:, None] - (c[a] + n[None, :] * L[a])
+                g.append(np.exp(-d * d / (2.0 * width * width)).sum(axis=1))
+            out += amplitude * (g[0][:, None, None] * g[1][None, :, None] * g[2][None, None, :])
+        return out
+    return _gaussian_sum_images(lattice, dims, centers, amplitude, width, nimg)
+
+
+def _gaussian_sum_images(lattice, dims, centers, amplitude, width, nimg):
+    """The direct sum over the periodic images (any cell)."""
+    r = _grid_points(lattice, dims)
+    out = np.zeros(dims, dtype=np.float64)
     for c in np.atleast_2d(centers):
         for n in itertools.product(*[range(-m, m + 1) for m in nimg]):
             shift = lattice @ np.array(n, dtype=np.float64)
