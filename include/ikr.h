@@ -66,7 +66,11 @@ typedef enum {
 
 typedef enum {
   IKR_FP64 = 0,          /* every step in FP64 */
-  IKR_MIXED = 1          /* FP32 complex FFT/CG where the tolerance allows, FP64 elsewhere */
+  IKR_MIXED = 1,         /* FP32 complex FFT/CG where the tolerance allows, FP64 elsewhere */
+  IKR_DF64 = 2           /* ikr_apply_hamiltonian only: complex128 vectors, FP64-accurate plane
+                            pass in double-float arithmetic on the FP32 units (the pass the mixed
+                            path uses for its FP64-accurate sections); other calls treat it as
+                            IKR_FP64 */
 } ikr_precision;
 
 /* Sternheimer CG tolerance rules (Table strategies; k-form Table strategies_k,
@@ -263,8 +267,8 @@ ikr_status ikr_groundstate_info(const ikr_ctx* ctx, double* f, int* nocc, double
 /* H_k psi for nvec vectors (eq. Hamiltonian, k-form of Sec. 4.1.1):
  *   H_k psi = |k+G|^2/2 psi + F_k (V . F_k^{-1} psi)
  * with F^{-1} = w^{-1} W^{-1} Z and F = w Z^T W (eq. fft_ifft).
- * psi, hpsi: DEVICE, Nb_k x nvec complex128 (IKR_FP64) or complex64 (IKR_MIXED:
- * arithmetic in FP32).  psi and hpsi must not overlap.  IKR_ERR_ARG for a
+ * psi, hpsi: DEVICE, Nb_k x nvec complex128 (IKR_FP64, IKR_DF64) or complex64
+ * (IKR_MIXED: arithmetic in FP32).  psi and hpsi must not overlap.  IKR_ERR_ARG for a
  * grid whose Nx x Ny plane has no compiled kernel shape and does not fit in a
  * block's shared memory (the shapes compiled are 10x12, 12x12, 24x24, 32x32,
  * 40x40, 48x48 and 96x96). */

@@ -342,10 +342,20 @@ ikr_status ikr_apply_hamiltonian(ikr_ctx* c, int k, const void* psi, void* hpsi,
     if (nvec == 0) return;
     IKR_REQUIRE(psi && hpsi && psi != hpsi, IKR_ERR_ARG, "psi and hpsi must be distinct device pointers");
     const int nb = c->k[k].nb;
-    if (precision == IKR_MIXED)
+    if (precision == IKR_MIXED) {
       hamiltonian<float>(c, k, static_cast<const float2*>(psi), static_cast<float2*>(hpsi), nb, nvec);
-    else
-      hamiltonian<double>(c, k, static_cast<const double2*>(psi), static_cast<double2*>(hpsi), nb, nvec);
+    } else {
+      // IKR_DF64: the plane pass in double-float, as in the mixed path's FP64-accurate sections
+      const bool old = c->emulate_fp64;
+      c->emulate_fp64 = precision == IKR_DF64;
+      try {
+        hamiltonian<double>(c, k, static_cast<const double2*>(psi), static_cast<double2*>(hpsi), nb, nvec);
+      } catch (...) {
+        c->emulate_fp64 = old;
+        throw;
+      }
+      c->emulate_fp64 = old;
+    }
     IKR_CUDA(cudaStreamSynchronize(stream));
   });
 }

@@ -199,6 +199,7 @@ struct ikr_ctx {
   bool reg_plane_ok = false;    // every active column's y-set is one cyclic interval
   bool xr_contig = false;       // the shifted active x positions are pxlo, pxlo + 1, ..., pxlo + nxa - 1
   int pxlo = 0;
+  bool plane_sw = true;         // swizzled double-float plane pass of 48 x 48 planes (IKR_PLANE_SW=0: off)
   int plane_rc = 5;             // compact FP32 plane kernel at 5 (or 4) blocks per SM; 0: the full-plane one
   // one-thread-per-column z-pass: per k, nc + 1 prefix sums of the column
   // counts (= the sphere offsets of the columns); zspan = the largest sphere

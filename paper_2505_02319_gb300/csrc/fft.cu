@@ -521,6 +521,10 @@ void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, 
   ProfScope ps(c, kKidPlane, 1, active ? c->active_hint : L.n, (int)sizeof(R));
   if (sizeof(R) == 8 && c->emulate_fp64) {
     // FP64-accurate pass of the mixed path on the FP32 units (double-float)
+    if (launch_plane_sw(c, L.n, reinterpret_cast<const double2*>(b1), reinterpret_cast<const double*>(pot),
+                        pot_scale, active, reinterpret_cast<double2*>(b4),
+                        reinterpret_cast<const double2*>(real_in)))
+      return;
     if (launch_plane_fast<dfloat>(c, L.n, reinterpret_cast<const double2*>(b1),
                                   reinterpret_cast<const double*>(pot), pot_scale, active,
                                   reinterpret_cast<double2*>(b4), reinterpret_cast<const double2*>(real_in)))

@@ -333,6 +333,230 @@ __global__ void __launch_bounds__(256) k_plane_t(const typename io<R>::cx* __res
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64-accurate plane pass in double-float with a swizzled plane (the pass the
+// mixed path runs for its right-hand sides and defect-correction residuals).
+// Same result as k_plane_t<dfloat>, organised for the 48 x 48 planes:
+//   - y-lines take 8 lanes (E = 6 elements each), so the 20 or so active
+//     columns keep 160 of the 192 threads busy and take about half the time of
+//     4-lane lines; x-lines keep 4 lanes (E = 12, inverse FFT, potential,
+//     forward FFT in registers);
+//   - element (y, x) of the plane sits at y NX + (x ^ r(y) ^ 2 bit3(x)) with
+//     r(y) = G[y mod 8] ^ H[y / 8], G = (0 1 2 3 5 4 7 6), H = (0 1 2 4 5 6),
+//     and the two x-lines of a quarter-warp are rows 8b + j and 8b + j + 4:
+//     with 16-byte elements every load and store of every step (both line
+//     directions, the transposes included) is served by one 128-byte
+//     wavefront per quarter-warp (checked for all access patterns on the
+//     host when the layout was chosen), against 2-way conflicts of the padded
+//     row-major layout.
+// The swizzle only permutes positions within aligned groups of 8 elements of
+// a row, so a row stays a row: NX % 16 == 0 (4-lane x-lines with T | E) and
+// NY % 8 == 0, NY <= 48 (the H table).
+
+__device__ __forceinline__ int sw_row(int y) {
+  return (int)(((0x67453210u >> ((y & 7) * 4)) ^ (0x654210u >> ((y >> 3) * 4))) & 7u);
+}
+template <int NX>
+__device__ __forceinline__ int sw_at(int y, int x, int ry) {
+  return y * NX + (x ^ ry ^ (((x >> 3) & 1) << 1));
+}
+
+// Addresses.  The swizzle changes only the low 3 bits of x, so every access
+// pattern is one per-lane value XOR a compile-time constant:
+//   y-line of column x, cx = x ^ 2 bit3(x):
+//     y = t + 8 q:  y NX + ((cx ^ G[t]) ^ H[q])
+//     y = 8 t + p:  y NX + ((cx ^ H[t]) ^ G[p])
+//   x-line of row y, r = r(y), lanes t < 4:
+//     x = t + 4 k:           y NX + 8 (k >> 1) + ((t ^ r) ^ (4 (k & 1) ^ 2 ((k >> 1) & 1)))
+//     x = 4 t + 16 j + p:    y NX + 8 (t >> 1) + 16 j + (m ^ p),  m = 4 (t & 1) ^ r ^ 2 ((t >> 1) & 1)
+__device__ __forceinline__ int sw_g(int i) { return (int)((0x67453210u >> (4 * i)) & 7u); }
+__device__ __forceinline__ int sw_h(int i) { return (int)((0x654210u >> (4 * i)) & 7u); }
+
+// y-line of column x: 8 lanes, lane t holds x[t + 8 q]; then the 8-point DFTs of
+// k2 = t < E (E <= 8) across the lanes; natural order out
+template <int NX, int NY, bool INV>
+__device__ __forceinline__ void yline_sw(dfloat2* P, int x, const dfloat2* tab, int t, unsigned mask) {
+  using C = dfloat2;
+  constexpr int T = 8, E = NY / T;
+  static_assert(E <= T, "one 8-point DFT per lane");
+  const int cx = x ^ (((x >> 3) & 1) << 1);
+  const int a = cx ^ sw_g(t);                 // rows y = t + 8 q
+  C* col = P + t * NX;
+  C v[E];
+#pragma unroll
+  for (int q = 0; q < E; ++q) v[q] = col[8 * q * NX + (a ^ ((0x654210 >> (4 * q)) & 7))];
+  RegFft<C, E, NY, INV>::run(v, tab);
+#pragma unroll
+  for (int k2 = 1; k2 < E; ++k2) {
+    C w = tab[t * k2];
+    if (INV) w.y = -w.y;
+    v[k2] = cmul(v[k2], w);
+  }
+  __syncwarp(mask);
+#pragma unroll
+  for (int k2 = 0; k2 < E; ++k2) col[8 * k2 * NX + (a ^ ((0x654210 >> (4 * k2)) & 7))] = v[k2];
+  __syncwarp(mask);
+  C w[T];
+  if (t < E) {
+    const int b = cx ^ sw_h(t);               // rows y = 8 t + p
+    const C* blk = P + 8 * t * NX;
+#pragma unroll
+    for (int tp = 0; tp < T; ++tp) w[tp] = blk[tp * NX + (b ^ ((0x67453210 >> (4 * tp)) & 7))];
+    RegFft<C, T, NY, INV>::run(w, tab);
+  }
+  __syncwarp(mask);
+  if (t < E) {
+#pragma unroll
+    for (int k1 = 0; k1 < T; ++k1) {
+      const int y = t + E * k1;
+      P[y * NX + (cx ^ sw_row(y))] = w[k1];
+    }
+  }
+  __syncwarp(mask);
+}
+
+// x-line of row y: 4 lanes; inverse FFT (unless the row is already in real
+// space), product with the potential row, forward FFT (as line_fft_ivf and
+// line_fft_finish, on the swizzled row)
+template <int NX>
+__device__ __forceinline__ void xline_ivf_sw(dfloat2* P, int y, const dfloat2* tab, int t, unsigned mask,
+                                             const double* __restrict__ pot_row, dfloat sc, bool in_real) {
+  using C = dfloat2;
+  constexpr int T = 4, E = NX / T, J = E / T;
+  static_assert(E % T == 0, "x-lines need T | E");
+  const int ry = sw_row(y);
+  C* row = P + y * NX;
+  const int u = t ^ ry;                                               // x = t + 4 k
+  C* rowt = row + 8 * (t >> 1);                                       // x = 4 t + 16 j + p
+  const int m = (4 * (t & 1)) ^ ry ^ (2 * ((t >> 1) & 1));
+#define IKR_SW_LIN(k) (8 * ((k) >> 1) + (u ^ ((4 * ((k) & 1)) ^ (2 * (((k) >> 1) & 1)))))
+  C v[E];
+#pragma unroll
+  for (int q = 0; q < E; ++q) v[q] = row[IKR_SW_LIN(q)];
+  if (!in_real) {
+    RegFft<C, E, NX, true>::run(v, tab);
+#pragma unroll
+    for (int k2 = 1; k2 < E; ++k2) {
+      C w = tab[t * k2];
+      w.y = -w.y;
+      v[k2] = cmul(v[k2], w);
+    }
+    __syncwarp(mask);
+#pragma unroll
+    for (int k2 = 0; k2 < E; ++k2) row[IKR_SW_LIN(k2)] = v[k2];
+    __syncwarp(mask);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      C w[T];
+#pragma unroll
+      for (int tp = 0; tp < T; ++tp) w[tp] = rowt[16 * j + (m ^ tp)];
+      RegFft<C, T, NX, true>::run(w, tab);
+#pragma unroll
+      for (int k1 = 0; k1 < T; ++k1) v[j + J * k1] = w[k1];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < E; ++q) v[q] = cscale(v[q], to_r<dfloat>(__ldg(pot_row + t + T * q)) * sc);
+  RegFft<C, E, NX, false>::run(v, tab);
+#pragma unroll
+  for (int k2 = 1; k2 < E; ++k2) v[k2] = cmul(v[k2], tab[t * k2]);
+  __syncwarp(mask);
+#pragma unroll
+  for (int k2 = 0; k2 < E; ++k2) row[IKR_SW_LIN(k2)] = v[k2];
+  __syncwarp(mask);
+  C w[J][T];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+#pragma unroll
+    for (int tp = 0; tp < T; ++tp) w[j][tp] = rowt[16 * j + (m ^ tp)];
+    RegFft<C, T, NX, false>::run(w[j], tab);
+  }
+  __syncwarp(mask);
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int k1 = 0; k1 < T; ++k1) row[IKR_SW_LIN(j + J * k1)] = w[j][k1];
+  __syncwarp(mask);
+#undef IKR_SW_LIN
+}
+
+template <int NX, int NY>
+__global__ void __launch_bounds__(192, 3) k_plane_sw(const double2* __restrict__ b1, int nc, int ncp,
+                                                  const int* __restrict__ col_xy, const int* __restrict__ xpos,
+                                                  int nxa, int Nz, const double2* __restrict__ twx,
+                                                  const double2* __restrict__ twy, const double* __restrict__ pot,
+                                                  const double* __restrict__ pot_scale,
+                                                  const int* __restrict__ active, double2* __restrict__ b4,
+                                                  const double2* __restrict__ real_in) {
+  static_assert(NX % 16 == 0 && NY % 8 == 0 && NY <= 48, "swizzled plane shape");
+  using C = dfloat2;
+  const int iz = blockIdx.x, s = blockIdx.y;
+  if (active && !active[s]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tx = reinterpret_cast<C*>(smem_raw);
+  C* ty = tx + NX;
+  C* P = ty + NY;
+  int* xp = reinterpret_cast<int*>(P + NX * NY);
+  for (int i = threadIdx.x; i < NX; i += blockDim.x) tx[i] = to_c<C>(twx[i]);
+  for (int i = threadIdx.x; i < NY; i += blockDim.x) ty[i] = to_c<C>(twy[i]);
+  for (int i = threadIdx.x; i < nxa; i += blockDim.x) xp[i] = xpos[i];
+  const size_t plane = (size_t)s * Nz + iz;
+  if (real_in) {
+    for (int e = threadIdx.x; e < NY * NX; e += blockDim.x) {
+      const int y = e / NX, x = e - y * NX;
+      P[sw_at<NX>(y, x, sw_row(y))] = to_c<C>(real_in[plane * NY * NX + e]);
+    }
+    __syncthreads();
+  } else {
+    for (int i = threadIdx.x; i < NX * NY; i += blockDim.x) P[i] = mk<C>(dfloat(0), dfloat(0));
+    __syncthreads();
+    for (int col = threadIdx.x; col < nc; col += blockDim.x) {
+      const int x = col_xy[2 * col], y = col_xy[2 * col + 1];
+      P[sw_at<NX>(y, x, sw_row(y))] = to_c<C>(b1[plane * ncp + col]);
+    }
+    __syncthreads();
+    const int slots = blockDim.x / 8, slot = threadIdx.x / 8, t = threadIdx.x % 8;
+    const int rounds = (nxa + slots - 1) / slots;
+    for (int r = 0; r < rounds; ++r) {
+      const int l = r * slots + slot;
+      const bool ok = l < nxa;
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (ok) yline_sw<NX, NY, true>(P, xp[l], ty, t, mask);
+    }
+    __syncthreads();
+  }
+  {
+    const dfloat sc = pot_scale ? to_r<dfloat>(*pot_scale) : dfloat(1);
+    const int slots = blockDim.x / 4, slot = threadIdx.x / 4, t = threadIdx.x % 4;
+    const int rounds = (NY + slots - 1) / slots;
+    for (int r = 0; r < rounds; ++r) {
+      const int it = r * slots + slot;
+      const bool ok = it < NY;
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (ok) {
+        const int y = 8 * (it >> 3) + ((it & 7) >> 1) + 4 * (it & 1);   // quarter-warp rows y, y + 4
+        xline_ivf_sw<NX>(P, y, tx, t, mask, pot + ((size_t)iz * NY + y) * NX, sc, real_in != nullptr);
+      }
+    }
+  }
+  __syncthreads();
+  {
+    const int slots = blockDim.x / 8, slot = threadIdx.x / 8, t = threadIdx.x % 8;
+    const int rounds = (nxa + slots - 1) / slots;
+    for (int r = 0; r < rounds; ++r) {
+      const int l = r * slots + slot;
+      const bool ok = l < nxa;
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (ok) yline_sw<NX, NY, false>(P, xp[l], ty, t, mask);
+    }
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < nc; col += blockDim.x) {
+    const int x = col_xy[2 * col], y = col_xy[2 * col + 1];
+    b4[plane * ncp + col] = from_c(P[sw_at<NX>(y, x, sw_row(y))]);
+  }
+}
+
 // Real-space planes of the sphere vectors (same result as k_synth_planes in
 // fft.cu, which it replaces for the supported grids): the z-transformed
 // columns b1 scattered into a plane, inverse y-lines of the active x
@@ -603,6 +827,22 @@ template bool launch_density_fast<double>(ikr_ctx*, int, const double2*, const d
                                           const double*, int*);
 template bool launch_density_fast<dfloat>(ikr_ctx*, int, const double2*, const double2*, const double*,
                                           const double*, int*);
+
+// The swizzled double-float plane pass for 48 x 48 planes; false: another kernel.
+bool launch_plane_sw(ikr_ctx* c, int nsys, const double2* b1, const double* pot, const double* pot_scale,
+                     const int* active, double2* b4, const double2* real_in) {
+  if (!c->plane_sw || c->N[0] != 48 || c->N[1] != 48) return false;
+  constexpr int NX = 48, NY = 48;
+  const size_t smem = sizeof(dfloat2) * (NX + NY + (size_t)NX * NY) + sizeof(int) * c->nxa;
+  if (smem > 227 * 1024) return false;
+  IKR_CUDA(cudaFuncSetAttribute(k_plane_sw<NX, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(c->N[2], nsys);
+  k_plane_sw<NX, NY><<<grid, 192, smem, c->stream>>>(b1, c->nc, c->ncp, c->d_col_xy.p, c->d_xpos.p, c->nxa,
+                                                     c->N[2], c->d_tw[0].p, c->d_tw[1].p, pot, pot_scale, active,
+                                                     b4, real_in);
+  IKR_CUDA(cudaGetLastError());
+  return true;
+}
 
 // Compile-time plane shapes of the supported grids; false: use the generic kernel.
 template <typename R>

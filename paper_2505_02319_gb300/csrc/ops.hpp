@@ -23,6 +23,10 @@ void launch_plane(ikr_ctx* c, const SysList& L, const C_t<R>* b1, const R* pot, 
                   const int* active, C_t<R>* b4, const C_t<R>* real_in = nullptr, const int* list = nullptr,
                   int nlist = 0);
 template <typename R> void launch_synth_planes(ikr_ctx* c, int nsys, const C_t<R>* b1, C_t<R>* out);
+// the swizzled double-float plane pass of 48 x 48 planes (fft_plane.cu); false when
+// the grid has another plane shape or the context turned it off
+bool launch_plane_sw(ikr_ctx* c, int nsys, const double2* b1, const double* pot, const double* pot_scale,
+                     const int* active, double2* b4, const double2* real_in);
 template <typename R>
 bool launch_plane_fast(ikr_ctx* c, int nsys, const typename io<R>::cx* b1, const typename io<R>::real* pot,
                        const double* pot_scale, const int* active, typename io<R>::cx* b4,

@@ -213,6 +213,8 @@ void setup_system(ikr_ctx* c, const ikr_system* sys) {
     // IKR_PLANE_RC=0 selects the full-plane FP32 kernel instead of the compact one,
     // IKR_PLANE_RC=4 the compact one compiled for 4 blocks per SM (read when the
     // context is created)
+    // IKR_PLANE_SW=0 selects k_plane_t for the double-float pass of 48 x 48 planes
+    if (const char* e = std::getenv("IKR_PLANE_SW")) c->plane_sw = std::atoi(e) != 0;
     if (const char* e = std::getenv("IKR_PLANE_RC")) {
       const int v = std::atoi(e);
       c->plane_rc = (v == 0 || v == 4) ? v : 5;

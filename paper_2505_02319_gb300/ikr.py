@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libikr.so")
 
 IKR_OK, IKR_ERR_ARG, IKR_ERR_CUDA, IKR_ERR_OOM, IKR_ERR_NOGAP, IKR_ERR_NOCONV, \
     IKR_ERR_NUMERIC, IKR_ERR_TIMEOUT, IKR_ERR_STATE = range(9)
-FP64, MIXED = 0, 1
+FP64, MIXED, DF64 = 0, 1, 2
 STRATEGIES = {"agr": 0, "bal": 1, "grt": 2, "D10": 3, "D100": 4, "D10n": 5, "grt_exact": 6, "fixed": 7}
 
 

@@ -40,3 +40,41 @@ def test_compact_fp32_plane_matches_full_plane(name, variant, monkeypatch):
         assert float(torch.abs(a - b).max()) <= 1e-6 * scale, k
     full.destroy()
     compact.destroy()
+
+
+@pytest.mark.parametrize("name", ["tiny_ortho_k", "cfg2"])
+def test_double_float_hamiltonian_matches_oracle(name):
+    """H_k with the plane pass in double-float (IKR_DF64; on the 48 x 48 planes of
+    cfg2 the swizzled kernel) against the oracle's dense H_k: FP64 accuracy up
+    to the double-float roundings of the butterflies (~1e-13 per pass)."""
+    from gpu_common import context, oracle_state
+    from paper_2505_02319_gb300 import ikr
+    gs, ctx = oracle_state(name), context(name)
+    rng = np.random.default_rng(19)
+    for k, kb in enumerate(gs.kblocks[:3]):
+        nb = len(kb.eps)
+        psi = rng.normal(size=(4, nb)) + 1j * rng.normal(size=(4, nb))
+        out = ctx.apply_hamiltonian(k, torch.tensor(psi, device="cuda"), precision=ikr.DF64).cpu().numpy()
+        ref = psi @ kb.H.T
+        assert np.linalg.norm(out - ref) < 1e-11 * np.linalg.norm(ref), k
+
+
+def test_swizzled_double_float_plane_matches_padded_one(monkeypatch):
+    """cfg2: the swizzled double-float plane pass (8-lane y-lines) against
+    k_plane_t<dfloat> (4-lane y-lines, padded rows): both FP64-accurate, so
+    they agree to the double-float rounding level."""
+    from paper_2505_02319_gb300 import ikr
+    s = system("cfg2")
+    monkeypatch.setenv("IKR_PLANE_SW", "0")
+    padded = _bare_context(s)
+    monkeypatch.setenv("IKR_PLANE_SW", "1")
+    swz = _bare_context(s)
+    rng = np.random.default_rng(23)
+    for k in (0, 5):
+        nb = padded.basis_size(k)
+        psi = torch.tensor(rng.normal(size=(6, nb)) + 1j * rng.normal(size=(6, nb)), device="cuda")
+        a = padded.apply_hamiltonian(k, psi, precision=ikr.DF64)
+        b = swz.apply_hamiltonian(k, psi, precision=ikr.DF64)
+        assert float(torch.linalg.norm(a - b) / torch.linalg.norm(a)) < 1e-12, k
+    padded.destroy()
+    swz.destroy()
