@@ -167,7 +167,6 @@ struct Profiler {
 }  // namespace ikr
 
 namespace ikr {
-void release_blas(void* handle);   // kb.cu
 }  // namespace ikr
 
 struct ikr_ctx {
@@ -241,8 +240,7 @@ struct ikr_ctx {
   ikr::DBuf<double2> d_kb;
   ikr::DBuf<float2> d_kb32;
   ikr::DBuf<double> d_kbD;
-  ikr::DBuf<float> d_kbD32;
-  void* cublas = nullptr;       // cublasHandle_t of the nonlocal products (created on first use)
+  ikr::DBuf<int> d_kboff, d_kbcnt;   // the projectors as a vector set: row k nproj + j, nproj per k
   ikr::DBuf<float4> d_psir_df; // the real-space orbital planes as double-float (x.hi, x.lo, y.hi, y.lo)
   ikr::DBuf<double2> d_phi_all; // occupied orbitals, vector s of occ at s * ld (complex128)
   ikr::DBuf<float2> d_phi_all32;
@@ -276,7 +274,6 @@ struct ikr_ctx {
   int active_hint = 0;          // systems active in the next masked launch (for accounting)
   bool emulate_fp64 = false;    // FP64 plane passes in double-float on the FP32 units (mixed path)
   ~ikr_ctx() {
-    if (cublas) ikr::release_blas(cublas);
     if (h_pinned) cudaFreeHost(h_pinned);
     for (auto& v : prof.ev)
       for (auto e : v) cudaEventDestroy(e);

@@ -8,37 +8,22 @@
 //   <e_q | beta> = e^{-i q.R} betahat(q) / sqrt(Omega),  q = k + G,
 //   betahat_s(q)   = (4 pi s^2)^{3/4} exp(-s^2 q^2 / 2),
 //   betahat_p,a(q) = -i s^2 q_a sqrt(2)/s (pi s^2)^{-3/4} (2 pi s^2)^{3/2} exp(-s^2 q^2 / 2).
-// The projector blocks B_k (Nb_k x nproj) are built once on the GPU; an
-// application out += B_k diag(D) B_k^H in is two complex GEMMs per k-point
-// (cuBLAS: the only dense contractions of the term) around a scaling kernel,
-// which also folds <in, V_nl in> = sum_j D_j |(B^H in)_j|^2 into the first
-// <p, Ap> partial of a CG iteration.
-#include <cublas_v2.h>
-
+// The projector blocks B_k (Nb_k x nproj) are built once on the GPU.  An
+// application out += B_k diag(D) B_k^H in treats the projectors of every
+// k-point as a vector set, exactly like the occupied orbitals of the
+// Q-projection: C = B_k^H in and out += B_k C run on the library's own
+// projection kernels (FP64 and double-float on the CUDA cores; FP32 on the
+// CUDA cores or, with ikr_set_tensor_cores, as tcgen05 MMAs with the three-term
+// TF32 split), all k-points in one launch each; between them a scaling kernel
+// applies diag(D) and folds <in, V_nl in> = sum_j D_j |(B^H in)_j|^2 into the
+// first <p, Ap> partial of a CG iteration.
 #include <cmath>
 
 #include "solver.hpp"
 
 namespace ikr {
 
-void release_blas(void* handle) { cublasDestroy(static_cast<cublasHandle_t>(handle)); }
-
 namespace {
-
-void blas_check(cublasStatus_t s, const char* what) {
-  if (s != CUBLAS_STATUS_SUCCESS) throw Error(IKR_ERR_CUDA, std::string("cuBLAS failed: ") + what);
-}
-
-cublasHandle_t blas(ikr_ctx* c) {
-  if (!c->cublas) {
-    cublasHandle_t h = nullptr;
-    blas_check(cublasCreate(&h), "create");
-    c->cublas = h;
-  }
-  cublasHandle_t h = static_cast<cublasHandle_t>(c->cublas);
-  blas_check(cublasSetStream(h, c->stream), "stream");
-  return h;
-}
 
 // B_k for one k-point: projector j = 4 a + ch of centre a (ch: s, p_x, p_y, p_z)
 __global__ void k_kb_build(const int* __restrict__ miller, int nb, int ld, double k0, double k1, double k2,
@@ -75,24 +60,24 @@ __global__ void k_kb_build(const int* __restrict__ miller, int nb, int ld, doubl
   }
 }
 
-// C_js <- D_j C_js for the systems of one k-point; with pap, also
-// pap[s * nparts] += sum_j D_j |C_js|^2 (before the scaling; one warp per system)
-template <typename C, typename Rr>
-__global__ void k_kb_scale(C* __restrict__ Cm, int nproj, int count, const Rr* __restrict__ D, int s0,
+// C_js <- D_j C_js for every system s (coefficients [s][nproj]); with pap,
+// also pap[s * nparts] += sum_j D_j |C_js|^2 (before the scaling) for the
+// active systems; one warp per system
+__global__ void k_kb_scale(double2* __restrict__ Cm, int nproj, int nsys, const double* __restrict__ D,
                            const int* __restrict__ active, double* __restrict__ pap, int nparts) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (w >= count) return;
-  C* col = Cm + (size_t)w * nproj;
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (s >= nsys) return;
+  if (active && !active[s]) return;
+  double2* col = Cm + (size_t)s * nproj;
   double acc = 0.0;
   for (int j = lane; j < nproj; j += 32) {
-    const C v = col[j];
-    const Rr d = D[j];
-    acc += (double)d * ((double)v.x * v.x + (double)v.y * v.y);
-    col[j] = mk<C>(d * v.x, d * v.y);
+    const double2 v = col[j];
+    const double d = D[j];
+    acc += d * (v.x * v.x + v.y * v.y);
+    col[j] = make_double2(d * v.x, d * v.y);
   }
   acc = warp_sum(acc);
-  const int s = s0 + w;
-  if (pap && lane == 0 && (!active || active[s])) pap[(size_t)s * nparts] += acc;
+  if (pap && lane == 0) pap[(size_t)s * nparts] += acc;
 }
 
 }  // namespace
@@ -127,81 +112,45 @@ void set_nonlocal(ikr_ctx* c, int ncentres, const double* centres, const double*
     IKR_CUDA(cudaStreamSynchronize(c->stream));   // dm is released at the end of the iteration
   }
   std::vector<double> dd(nproj);
-  std::vector<float> df(nproj);
   for (int a = 0; a < ncentres; ++a)
-    for (int ch = 0; ch < 4; ++ch) {
-      dd[4 * a + ch] = ch == 0 ? D[0] : D[1];
-      df[4 * a + ch] = (float)dd[4 * a + ch];
-    }
+    for (int ch = 0; ch < 4; ++ch) dd[4 * a + ch] = ch == 0 ? D[0] : D[1];
+  std::vector<int> koff(nk), kcnt(nk, nproj);
+  for (int k = 0; k < nk; ++k) koff[k] = k * nproj;      // projector j of k-point k is row k nproj + j
+  c->d_kboff.reserve(nk);
+  c->d_kbcnt.reserve(nk);
+  IKR_CUDA(cudaMemcpyAsync(c->d_kboff.p, koff.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, c->stream));
+  IKR_CUDA(cudaMemcpyAsync(c->d_kbcnt.p, kcnt.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, c->stream));
   c->d_kbD.reserve(nproj);
-  c->d_kbD32.reserve(nproj);
   IKR_CUDA(cudaMemcpyAsync(c->d_kbD.p, dd.data(), sizeof(double) * nproj, cudaMemcpyHostToDevice, c->stream));
-  IKR_CUDA(cudaMemcpyAsync(c->d_kbD32.p, df.data(), sizeof(float) * nproj, cudaMemcpyHostToDevice, c->stream));
   IKR_CUDA(cudaStreamSynchronize(c->stream));
   c->nproj = nproj;
   c->kb_dmax = std::max(D[0], D[1]);
 }
 
-namespace {
-
-template <typename R> struct Blas;
-template <> struct Blas<double> {
-  using T = cuDoubleComplex;
-  static const double2* B(ikr_ctx* c) { return c->d_kb.p; }
-  static const double* D(ikr_ctx* c) { return c->d_kbD.p; }
-  static cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
-                             double ar, const double2* A, int lda, const double2* Bm, int ldb, double br, double2* Cm,
-                             int ldc) {
-    const T a = make_cuDoubleComplex(ar, 0.0), b = make_cuDoubleComplex(br, 0.0);
-    return cublasZgemm(h, ta, tb, m, n, k, &a, reinterpret_cast<const T*>(A), lda, reinterpret_cast<const T*>(Bm),
-                       ldb, &b, reinterpret_cast<T*>(Cm), ldc);
-  }
-};
-template <> struct Blas<float> {
-  using T = cuComplex;
-  static const float2* B(ikr_ctx* c) { return c->d_kb32.p; }
-  static const float* D(ikr_ctx* c) { return c->d_kbD32.p; }
-  static cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
-                             double ar, const float2* A, int lda, const float2* Bm, int ldb, double br, float2* Cm,
-                             int ldc) {
-    const T a = make_cuComplex((float)ar, 0.f), b = make_cuComplex((float)br, 0.f);
-    return cublasCgemm(h, ta, tb, m, n, k, &a, reinterpret_cast<const T*>(A), lda, reinterpret_cast<const T*>(Bm),
-                       ldb, &b, reinterpret_cast<T*>(Cm), ldc);
-  }
-};
-
-}  // namespace
+OrbSet kb_set(ikr_ctx* c) {
+  OrbSet o;
+  o.phi = c->d_kb.p;
+  o.phi32 = c->d_kb32.p;
+  o.off = c->d_kboff.p;
+  o.cnt = c->d_kbcnt.p;
+  o.maxcnt = c->nproj;
+  return o;
+}
 
 template <typename R>
 void apply_nonlocal(ikr_ctx* c, const SysList& L, const C_t<R>* in, int ld, C_t<R>* out, const int* active,
                     double* pap, int nparts) {
   if (c->nproj == 0 || L.n == 0) return;
-  ProfScope ps(c, kKidProjApply, 2, L.n, (int)sizeof(R));
-  cublasHandle_t h = blas(c);
-  const int np = c->nproj;
-  const int nk_groups = (int)L.kcount.size();
-  const int* kstart = L.kstart.data();
-  const int* kcount = L.kcount.data();
-  int maxc = 0;
-  for (int g = 0; g < nk_groups; ++g) maxc = std::max(maxc, kcount[g]);
-  if (maxc == 0) return;
-  DBuf<double2>& ws = c->ws.kbc;
-  ws.reserve(((size_t)np * maxc * sizeof(C_t<R>) + sizeof(double2) - 1) / sizeof(double2));
-  C_t<R>* Cm = reinterpret_cast<C_t<R>*>(ws.p);
-  const size_t per_k = (size_t)np * c->ld;
-  for (int g = 0; g < nk_groups; ++g) {
-    const int cnt = kcount[g];
-    if (cnt == 0) continue;
-    const int k = g, nb = c->k[k].nb;
-    const C_t<R>* Bk = Blas<R>::B(c) + k * per_k;
-    const C_t<R>* ik = in + (size_t)kstart[g] * ld;
-    C_t<R>* ok = out + (size_t)kstart[g] * ld;
-    blas_check(Blas<R>::gemm(h, CUBLAS_OP_C, CUBLAS_OP_N, np, cnt, nb, 1.0, Bk, c->ld, ik, ld, 0.0, Cm, np), "B^H x");
-    k_kb_scale<C_t<R>, R><<<(cnt * 32 + 255) / 256, 256, 0, c->stream>>>(Cm, np, cnt, Blas<R>::D(c), kstart[g],
-                                                                         active, pap, nparts);
+  const OrbSet kb = kb_set(c);
+  c->ws.kbc.reserve((size_t)L.n * c->nproj);
+  double2* Cm = c->ws.kbc.p;
+  proj_coef<R>(c, L, in, ld, active, Cm, &kb);
+  {
+    ProfScope ps(c, kKidProjApply, 1);
+    k_kb_scale<<<(L.n * 32 + 255) / 256, 256, 0, c->stream>>>(Cm, c->nproj, L.n, c->d_kbD.p, active, pap, nparts);
     IKR_CUDA(cudaGetLastError());
-    blas_check(Blas<R>::gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, nb, cnt, np, 1.0, Bk, c->ld, Cm, np, 1.0, ok, ld), "B C");
   }
+  proj_apply<R>(c, L, Cm, out, R(1), R(1), out, ld, nullptr, nullptr, active, &kb);
 }
 template void apply_nonlocal<double>(ikr_ctx*, const SysList&, const double2*, int, double2*, const int*, double*,
                                      int);

@@ -87,6 +87,7 @@ struct OrbSet {
 OrbSet occ_set(ikr_ctx* c);     // Phi_k
 OrbSet schur_set(ikr_ctx* c);   // [Phi_k Psi_k]: the occupied and the extra computed bands
 OrbSet extra_set(ikr_ctx* c);   // Psi_k
+OrbSet kb_set(ikr_ctx* c);      // the Kleinman-Bylander projectors B_k (kb.cu)
 
 // ops.cu
 // Fused FP32 CG update after the H_k application (cg_fused.cu): false when the

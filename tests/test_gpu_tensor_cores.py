@@ -96,3 +96,27 @@ def test_tensor_cores_with_schur_sets_in_chi0():
     ref = response.chi0(gs, dV)
     assert np.linalg.norm(d.cpu().numpy() - ref.ravel()) < 1e-9 * np.linalg.norm(ref)
     ctx.destroy()
+
+
+def test_tensor_core_nonlocal_projectors():
+    """The Kleinman-Bylander term B diag(D) B^H of H_k runs on the projection
+    kernels with the projectors as the vector set: in FP32 on the CUDA cores and
+    on the tensor cores (tcgen05, three-term TF32 split) it matches the oracle's
+    dense H_k to the FP32 tolerance of the other H_k tests."""
+    from paper_2505_02319_gb300 import ikr
+    gs, ctx = oracle_state("tiny_kb"), context("tiny_kb")
+    rng = np.random.default_rng(29)
+    for k, kb in enumerate(gs.kblocks):
+        nb = len(kb.eps)
+        psi = (rng.normal(size=(5, nb)) + 1j * rng.normal(size=(5, nb))).astype(np.complex64)
+        ref = psi.astype(np.complex128) @ kb.H.T
+        outs = []
+        for tc in (False, True):
+            ctx.set_tensor_cores(tc)
+            try:
+                outs.append(ctx.apply_hamiltonian(k, torch.tensor(psi, device="cuda"), precision=ikr.MIXED)
+                            .cpu().numpy())
+            finally:
+                ctx.set_tensor_cores(False)
+        for out in outs:
+            assert np.linalg.norm(out - ref) < 2e-6 * np.linalg.norm(ref), k
