@@ -373,9 +373,10 @@ __device__ __forceinline__ int sw_g(int i) { return (int)((0x67453210u >> (4 * i
 __device__ __forceinline__ int sw_h(int i) { return (int)((0x654210u >> (4 * i)) & 7u); }
 
 // y-line of column x: 8 lanes, lane t holds x[t + 8 q]; then the 8-point DFTs of
-// k2 = t < E (E <= 8) across the lanes; natural order out
-template <int NX, int NY, bool INV>
-__device__ __forceinline__ void yline_sw(dfloat2* P, int x, const dfloat2* tab, int t, unsigned mask) {
+// k2 = t < E (E <= 8) across the lanes; natural order out.  Forward transform;
+// cj = true gives the inverse as conj(FFT(conj x)) (conjugated load and store).
+template <int NX, int NY>
+__device__ __forceinline__ void yline_sw(dfloat2* P, int x, const dfloat2* tab, int t, unsigned mask, bool cj) {
   using C = dfloat2;
   constexpr int T = 8, E = NY / T;
   static_assert(E <= T, "one 8-point DFT per lane");
@@ -384,14 +385,13 @@ __device__ __forceinline__ void yline_sw(dfloat2* P, int x, const dfloat2* tab, 
   C* col = P + t * NX;
   C v[E];
 #pragma unroll
-  for (int q = 0; q < E; ++q) v[q] = col[8 * q * NX + (a ^ ((0x654210 >> (4 * q)) & 7))];
-  RegFft<C, E, NY, INV>::run(v, tab);
-#pragma unroll
-  for (int k2 = 1; k2 < E; ++k2) {
-    C w = tab[t * k2];
-    if (INV) w.y = -w.y;
-    v[k2] = cmul(v[k2], w);
+  for (int q = 0; q < E; ++q) {
+    v[q] = col[8 * q * NX + (a ^ ((0x654210 >> (4 * q)) & 7))];
+    if (cj) v[q].y = -v[q].y;
   }
+  RegFft<C, E, NY, false>::run(v, tab);
+#pragma unroll
+  for (int k2 = 1; k2 < E; ++k2) v[k2] = cmul(v[k2], tab[t * k2]);
   __syncwarp(mask);
 #pragma unroll
   for (int k2 = 0; k2 < E; ++k2) col[8 * k2 * NX + (a ^ ((0x654210 >> (4 * k2)) & 7))] = v[k2];
@@ -402,22 +402,26 @@ __device__ __forceinline__ void yline_sw(dfloat2* P, int x, const dfloat2* tab, 
     const C* blk = P + 8 * t * NX;
 #pragma unroll
     for (int tp = 0; tp < T; ++tp) w[tp] = blk[tp * NX + (b ^ ((0x67453210 >> (4 * tp)) & 7))];
-    RegFft<C, T, NY, INV>::run(w, tab);
+    RegFft<C, T, NY, false>::run(w, tab);
   }
   __syncwarp(mask);
   if (t < E) {
 #pragma unroll
     for (int k1 = 0; k1 < T; ++k1) {
       const int y = t + E * k1;
-      P[y * NX + (cx ^ sw_row(y))] = w[k1];
+      C o = w[k1];
+      if (cj) o.y = -o.y;
+      P[y * NX + (cx ^ sw_row(y))] = o;
     }
   }
   __syncwarp(mask);
 }
 
-// x-line of row y: 4 lanes; inverse FFT (unless the row is already in real
-// space), product with the potential row, forward FFT (as line_fft_ivf and
-// line_fft_finish, on the swizzled row)
+// x-line of row y: 4 lanes; two passes of one forward pipeline (E-point DFT,
+// twiddles, transpose through the row, T-point DFTs): pass 0 transforms the
+// conjugated row (the inverse FFT, conjugated back in registers) unless the row
+// is already in real space, pass 1 the product with the potential row, whose
+// result is written back in natural order
 template <int NX>
 __device__ __forceinline__ void xline_ivf_sw(dfloat2* P, int y, const dfloat2* tab, int t, unsigned mask,
                                              const double* __restrict__ pot_row, dfloat sc, bool in_real) {
@@ -432,50 +436,44 @@ __device__ __forceinline__ void xline_ivf_sw(dfloat2* P, int y, const dfloat2* t
 #define IKR_SW_LIN(k) (8 * ((k) >> 1) + (u ^ ((4 * ((k) & 1)) ^ (2 * (((k) >> 1) & 1)))))
   C v[E];
 #pragma unroll
-  for (int q = 0; q < E; ++q) v[q] = row[IKR_SW_LIN(q)];
-  if (!in_real) {
-    RegFft<C, E, NX, true>::run(v, tab);
+  for (int q = 0; q < E; ++q) {
+    v[q] = row[IKR_SW_LIN(q)];
+    if (!in_real) v[q].y = -v[q].y;
+  }
+  C w[J][T];
+#pragma unroll 1
+  for (int pass = in_real ? 1 : 0; pass < 2; ++pass) {
+    if (pass == 1) {
 #pragma unroll
-    for (int k2 = 1; k2 < E; ++k2) {
-      C w = tab[t * k2];
-      w.y = -w.y;
-      v[k2] = cmul(v[k2], w);
+      for (int q = 0; q < E; ++q) {
+        const dfloat p = to_r<dfloat>(__ldg(pot_row + t + T * q)) * sc;
+        C a = v[q];
+        if (!in_real) a.y = -a.y;                   // conj of the inverse pass's output
+        v[q] = cscale(a, p);
+      }
     }
+    RegFft<C, E, NX, false>::run(v, tab);
+#pragma unroll
+    for (int k2 = 1; k2 < E; ++k2) v[k2] = cmul(v[k2], tab[t * k2]);
     __syncwarp(mask);
 #pragma unroll
     for (int k2 = 0; k2 < E; ++k2) row[IKR_SW_LIN(k2)] = v[k2];
     __syncwarp(mask);
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-      C w[T];
 #pragma unroll
-      for (int tp = 0; tp < T; ++tp) w[tp] = rowt[16 * j + (m ^ tp)];
-      RegFft<C, T, NX, true>::run(w, tab);
-#pragma unroll
-      for (int k1 = 0; k1 < T; ++k1) v[j + J * k1] = w[k1];
+      for (int tp = 0; tp < T; ++tp) w[j][tp] = rowt[16 * j + (m ^ tp)];
+      RegFft<C, T, NX, false>::run(w[j], tab);
     }
-  }
+    // the outputs X[t + T j + E k1] = X[t + T (j + J k1)] are the next pass's inputs
 #pragma unroll
-  for (int q = 0; q < E; ++q) v[q] = cscale(v[q], to_r<dfloat>(__ldg(pot_row + t + T * q)) * sc);
-  RegFft<C, E, NX, false>::run(v, tab);
+    for (int j = 0; j < J; ++j)
 #pragma unroll
-  for (int k2 = 1; k2 < E; ++k2) v[k2] = cmul(v[k2], tab[t * k2]);
-  __syncwarp(mask);
-#pragma unroll
-  for (int k2 = 0; k2 < E; ++k2) row[IKR_SW_LIN(k2)] = v[k2];
-  __syncwarp(mask);
-  C w[J][T];
-#pragma unroll
-  for (int j = 0; j < J; ++j) {
-#pragma unroll
-    for (int tp = 0; tp < T; ++tp) w[j][tp] = rowt[16 * j + (m ^ tp)];
-    RegFft<C, T, NX, false>::run(w[j], tab);
+      for (int k1 = 0; k1 < T; ++k1) v[j + J * k1] = w[j][k1];
   }
   __syncwarp(mask);
 #pragma unroll
-  for (int j = 0; j < J; ++j)
-#pragma unroll
-    for (int k1 = 0; k1 < T; ++k1) row[IKR_SW_LIN(j + J * k1)] = w[j][k1];
+  for (int q = 0; q < E; ++q) row[IKR_SW_LIN(q)] = v[q];
   __syncwarp(mask);
 #undef IKR_SW_LIN
 }
@@ -506,7 +504,6 @@ __global__ void __launch_bounds__(192, 3) k_plane_sw(const double2* __restrict__
       const int y = e / NX, x = e - y * NX;
       P[sw_at<NX>(y, x, sw_row(y))] = to_c<C>(real_in[plane * NY * NX + e]);
     }
-    __syncthreads();
   } else {
     for (int i = threadIdx.x; i < NX * NY; i += blockDim.x) P[i] = mk<C>(dfloat(0), dfloat(0));
     __syncthreads();
@@ -514,43 +511,37 @@ __global__ void __launch_bounds__(192, 3) k_plane_sw(const double2* __restrict__
       const int x = col_xy[2 * col], y = col_xy[2 * col + 1];
       P[sw_at<NX>(y, x, sw_row(y))] = to_c<C>(b1[plane * ncp + col]);
     }
-    __syncthreads();
-    const int slots = blockDim.x / 8, slot = threadIdx.x / 8, t = threadIdx.x % 8;
-    const int rounds = (nxa + slots - 1) / slots;
-    for (int r = 0; r < rounds; ++r) {
-      const int l = r * slots + slot;
-      const bool ok = l < nxa;
-      const unsigned mask = __ballot_sync(0xffffffffu, ok);
-      if (ok) yline_sw<NX, NY, true>(P, xp[l], ty, t, mask);
-    }
-    __syncthreads();
   }
-  {
-    const dfloat sc = pot_scale ? to_r<dfloat>(*pot_scale) : dfloat(1);
-    const int slots = blockDim.x / 4, slot = threadIdx.x / 4, t = threadIdx.x % 4;
-    const int rounds = (NY + slots - 1) / slots;
-    for (int r = 0; r < rounds; ++r) {
-      const int it = r * slots + slot;
-      const bool ok = it < NY;
-      const unsigned mask = __ballot_sync(0xffffffffu, ok);
-      if (ok) {
-        const int y = 8 * (it >> 3) + ((it & 7) >> 1) + 4 * (it & 1);   // quarter-warp rows y, y + 4
-        xline_ivf_sw<NX>(P, y, tx, t, mask, pot + ((size_t)iz * NY + y) * NX, sc, real_in != nullptr);
+  __syncthreads();
+  const dfloat sc = pot_scale ? to_r<dfloat>(*pot_scale) : dfloat(1);
+  // phase 0: inverse y-lines (not for real-space input), 1: x-lines, 2: forward y-lines;
+  // one y-line and one x-line code site (the transforms are unrolled once each)
+#pragma unroll 1
+  for (int ph = real_in ? 1 : 0; ph < 3; ++ph) {
+    if (ph != 1) {
+      const int slots = blockDim.x / 8, slot = threadIdx.x / 8, t = threadIdx.x % 8;
+      const int rounds = (nxa + slots - 1) / slots;
+      for (int r = 0; r < rounds; ++r) {
+        const int l = r * slots + slot;
+        const bool ok = l < nxa;
+        const unsigned mask = __ballot_sync(0xffffffffu, ok);
+        if (ok) yline_sw<NX, NY>(P, xp[l], ty, t, mask, ph == 0);
+      }
+    } else {
+      const int slots = blockDim.x / 4, slot = threadIdx.x / 4, t = threadIdx.x % 4;
+      const int rounds = (NY + slots - 1) / slots;
+      for (int r = 0; r < rounds; ++r) {
+        const int it = r * slots + slot;
+        const bool ok = it < NY;
+        const unsigned mask = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+          const int y = 8 * (it >> 3) + ((it & 7) >> 1) + 4 * (it & 1);   // quarter-warp rows y, y + 4
+          xline_ivf_sw<NX>(P, y, tx, t, mask, pot + ((size_t)iz * NY + y) * NX, sc, real_in != nullptr);
+        }
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
-  {
-    const int slots = blockDim.x / 8, slot = threadIdx.x / 8, t = threadIdx.x % 8;
-    const int rounds = (nxa + slots - 1) / slots;
-    for (int r = 0; r < rounds; ++r) {
-      const int l = r * slots + slot;
-      const bool ok = l < nxa;
-      const unsigned mask = __ballot_sync(0xffffffffu, ok);
-      if (ok) yline_sw<NX, NY, false>(P, xp[l], ty, t, mask);
-    }
-  }
-  __syncthreads();
   for (int col = threadIdx.x; col < nc; col += blockDim.x) {
     const int x = col_xy[2 * col], y = col_xy[2 * col + 1];
     b4[plane * ncp + col] = from_c(P[sw_at<NX>(y, x, sw_row(y))]);

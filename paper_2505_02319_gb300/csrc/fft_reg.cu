@@ -275,8 +275,9 @@ __global__ void __launch_bounds__(RcGeom<NX, NY>::NTH, MINB)
                const float* __restrict__ pot, const double* __restrict__ pot_scale,
                const int* __restrict__ active, int nsys, const int* __restrict__ list,
                float2* __restrict__ b4) {
+  static_assert(NX == NY, "one transform body serves both line directions");
   using G = RcGeom<NX, NY>;
-  constexpr int PL = G::PL, NTH = G::NTH, ldp = G::ldp, SH = G::SH;
+  constexpr int PL = G::PL, NTH = G::NTH, ldp = G::ldp, SH = G::SH, N = NX;
   const int ldc = G::ldc(nxa), PS = G::ps(nxa);
   const int iz = blockIdx.x;
   __shared__ int live[PL];   // system of slot j, or -1
@@ -314,64 +315,79 @@ __global__ void __launch_bounds__(RcGeom<NX, NY>::NTH, MINB)
   }
   cp_async_wait_all();
   __syncthreads();
-  // inverse y-lines of the active columns (column l: only its y-interval is non-zero)
-  for (int it = threadIdx.x; it < PL * nxa; it += NTH) {
-    const int l = it / PL, j = it - l * PL;
-    if (live[j] < 0) continue;
-    const int ylo = xr_s[3 * l + 1], span = xr_s[3 * l + 2];
-    float2* colp = planes + j * PS + l;
-    float2 v[NY];
-#pragma unroll
-    for (int y = 0; y < NY; ++y) {
-      int d = y - ylo;
-      d += d < 0 ? NY : 0;
-      v[y] = d <= span ? colp[y * ldc] : zero;
-    }
-    CtFft<float2, NY, true>::run(v);
-#pragma unroll
-    for (int y = 0; y < NY; ++y) colp[y * ldc] = v[y];
-  }
-  __syncthreads();
-  // x-lines: inverse transform of the active inputs, potential, forward transform,
-  // active outputs kept; shifted position (x + SH) mod NX sits at column (that - pxlo)
-  {
-    const float sc = pot_scale ? (float)*pot_scale : 1.f;
-    for (int it = threadIdx.x; it < PL * NY; it += NTH) {
-      const int iy = it / PL, j = it - iy * PL;
+  const float sc = pot_scale ? (float)*pot_scale : 1.f;
+  // Three phases with one forward-transform code site between them (the whole
+  // kernel issues one copy of the unrolled FFT, so every warp, whatever its
+  // phase, runs the same instructions): an inverse transform is
+  // conj(FFT(conj(x))).
+  //   phase 0: inverse y-lines of the active columns (input: the column's y-interval)
+  //   phase 1: x-lines, two passes: inverse, then conj, times the potential row,
+  //            forward; the active x positions are read and written
+  //   phase 2: forward y-lines, only the column's interval is kept
+#pragma unroll 1
+  for (int ph = 0; ph < 3; ++ph) {
+    const bool xph = ph == 1;
+    const int items = xph ? PL * NY : PL * nxa;
+    for (int it = threadIdx.x; it < items; it += NTH) {
+      const int line = it / PL, j = it - line * PL;
       if (live[j] < 0) continue;
-      const int base = j * PS + iy * ldc - pxlo;
-      const float* prow = pot_s + iy * ldp;
-      float2 v[NX];
+      float2 v[N];
+      float2* colp = planes + j * PS + line;                        // y-line of column `line`
+      const int base = j * PS + line * ldc - pxlo;                  // x-line of row `line`
+      int ylo = 0, span = N - 1;
+      if (!xph) {
+        ylo = xr_s[3 * line + 1];
+        span = xr_s[3 * line + 2];
+      }
+      if (xph) {
 #pragma unroll
-      for (int x = 0; x < NX; ++x) v[x] = ((xmask >> x) & 1ull) ? planes[base + (x + SH) % NX] : zero;
-      CtFft<float2, NX, true>::run(v);
+        for (int x = 0; x < N; ++x) {
+          const float2 a = ((xmask >> x) & 1ull) ? planes[base + (x + SH) % NX] : zero;
+          v[x] = make_float2(a.x, -a.y);
+        }
+      } else if (ph == 0) {
 #pragma unroll
-      for (int x = 0; x < NX; ++x) v[x] = cscale(v[x], prow[x] * sc);
-      CtFft<float2, NX, false>::run(v);
+        for (int y = 0; y < N; ++y) {
+          int d = y - ylo;
+          d += d < 0 ? N : 0;
+          const float2 a = d <= span ? colp[y * ldc] : zero;
+          v[y] = make_float2(a.x, -a.y);
+        }
+      } else {
 #pragma unroll
-      for (int x = 0; x < NX; ++x)
-        if ((xmask >> x) & 1ull) planes[base + (x + SH) % NX] = v[x];
+        for (int y = 0; y < N; ++y) v[y] = colp[y * ldc];
+      }
+      const int npass = xph ? 2 : 1;
+#pragma unroll 1
+      for (int pass = 0; pass < npass; ++pass) {
+        if (pass == 1) {
+          const float* prow = pot_s + line * ldp;
+#pragma unroll
+          for (int x = 0; x < N; ++x) {
+            const float p = prow[x] * sc;
+            v[x] = make_float2(v[x].x * p, -v[x].y * p);
+          }
+        }
+        CtFft<float2, N, false>::run(v);
+      }
+      if (xph) {
+#pragma unroll
+        for (int x = 0; x < N; ++x)
+          if ((xmask >> x) & 1ull) planes[base + (x + SH) % NX] = v[x];
+      } else if (ph == 0) {
+#pragma unroll
+        for (int y = 0; y < N; ++y) colp[y * ldc] = make_float2(v[y].x, -v[y].y);
+      } else {
+#pragma unroll
+        for (int y = 0; y < N; ++y) {
+          int d = y - ylo;
+          d += d < 0 ? N : 0;
+          if (d <= span) colp[y * ldc] = v[y];
+        }
+      }
     }
+    __syncthreads();
   }
-  __syncthreads();
-  // forward y-lines of the active columns; only the column's interval is kept
-  for (int it = threadIdx.x; it < PL * nxa; it += NTH) {
-    const int l = it / PL, j = it - l * PL;
-    if (live[j] < 0) continue;
-    const int ylo = xr_s[3 * l + 1], span = xr_s[3 * l + 2];
-    float2* colp = planes + j * PS + l;
-    float2 v[NY];
-#pragma unroll
-    for (int y = 0; y < NY; ++y) v[y] = colp[y * ldc];
-    CtFft<float2, NY, false>::run(v);
-#pragma unroll
-    for (int y = 0; y < NY; ++y) {
-      int d = y - ylo;
-      d += d < 0 ? NY : 0;
-      if (d <= span) colp[y * ldc] = v[y];
-    }
-  }
-  __syncthreads();
   for (int e = threadIdx.x; e < PL * nc; e += NTH) {
     const int j = e / nc, col = e - j * nc;
     if (live[j] < 0) continue;
@@ -387,6 +403,7 @@ template <int NX, int NY>
 bool try_reg(ikr_ctx* c, int nsys, const float2* b1, const float* pot, const double* pot_scale, const int* active,
              float2* b4, const float2* real_in, const int* list) {
   if (c->N[0] != NX || c->N[1] != NY) return false;
+  if constexpr (NX == NY) {
   if (!real_in && c->xr_contig && c->plane_rc) {
     using H = RcGeom<NX, NY>;
     const size_t smem = H::smem(c->nxa);
@@ -403,6 +420,7 @@ bool try_reg(ikr_ctx* c, int nsys, const float2* b1, const float* pot, const dou
       else launch(k_plane_rc<NX, NY, 5>);
       return true;
     }
+  }
   }
   using G = RegGeom<NX, NY>;
   const size_t smem = G::smem(c->nxa);
