@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--cfg4-guaranteed", action="store_true",
                    help="also solve the 64-atom cell with Kleinman-Bylander projectors (cfg4) with the "
                         "guaranteed rule grt_exact, beside bal")
+    p.add_argument("--no-cfg4", action="store_true",
+                   help="leave out the mixed-vs-FP64 comparison on the largest workload (cfg4)")
     p.add_argument("--no-cpu-baseline", action="store_true",
                    help="leave out the oracle's timed solve (for runs of the studies only)")
     p.add_argument("--profile-run", action="store_true",
@@ -370,6 +372,51 @@ def cfg4_guaranteed(tau, m):
     return out
 
 
+def cfg4_comparison(tau, m, stream):
+    """The largest single-GPU workload (cfg4: 96^3 grid, Gamma, N_b = 36,785, 256
+    Kleinman-Bylander projectors, N_occ = 128 with a 1e-4 Ha gap): mixed precision
+    against FP64, both with Schur-complement Sternheimer solves over the 8 computed
+    bands above the gap (Sec. 3.4.2) and the balanced rule, each timed once with
+    CUDA events after a loose warm-up solve; true residuals from an FP64 E
+    application at tight CG tolerances."""
+    import numpy as np
+    import torch
+    from paper_2505_02319_gb300 import groundstate
+    from workloads import make_system, perturbation
+    s = make_system("cfg4")
+    t0 = time.time()
+    ctx = groundstate.context_for(s, eig_tol=1e-9, schur=True)
+    torch.cuda.synchronize()
+    setup = time.time() - t0
+    nsys = ctx.groundstate_nsys
+    b, _ = ctx.apply_chi0(torch.tensor(perturbation(s).ravel(), device="cuda"), tol=np.full(nsys, 1e-12))
+    b = (b / torch.linalg.norm(b)).contiguous()
+    out = {"workload": "cfg4: 20.5 bohr cell, 64 Gaussian atoms with s+p KB projectors, Ecut 20 Ha, 96^3 grid, "
+                       "Gamma, 136 bands (N_occ 128), Schur-complement solves, bal, tau = 1e-8, m = 20",
+           "setup_s": setup}
+    for prec in ("mixed", "fp64"):
+        ctx.solve_response(b, tau=1e-2, m=m, strategy="bal", precision=prec)          # workspaces, shapes
+        (x, rep), t = timed(lambda: ctx.solve_response(b, tau=tau, m=m, strategy="bal", precision=prec), stream)
+        Ex, _ = ctx.apply_dielectric(x, tol=np.full(nsys, 1e-12))
+        r = rep[0]
+        out[prec] = {"time_s": t, "status": r["status"], "n_ham": r["n_ham"], "n_ham_fp64": r["n_ham_fp64"],
+                     "outer_iters": r["outer_iters"], "true_residual": float(torch.linalg.norm(b - Ex))}
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["time_s"] / out["mixed"]["time_s"]
+    # the same mixed solve with the FP32 projection products (occupied, extra and
+    # Kleinman-Bylander vectors) on the tensor cores
+    ctx.set_tensor_cores(True)
+    try:
+        ctx.solve_response(b, tau=1e-2, m=m, strategy="bal", precision="mixed")
+        (x, rep), t = timed(lambda: ctx.solve_response(b, tau=tau, m=m, strategy="bal", precision="mixed"), stream)
+    finally:
+        ctx.set_tensor_cores(False)
+    Ex, _ = ctx.apply_dielectric(x, tol=np.full(nsys, 1e-12))
+    out["mixed_tensor_cores"] = {"time_s": t, "status": rep[0]["status"], "n_ham": rep[0]["n_ham"],
+                                 "true_residual": float(torch.linalg.norm(b - Ex))}
+    ctx.destroy()
+    return out
+
+
 SUPERCELL_BASE = "cfg1"
 SUPERCELL_BUMP = (0.3, 0.6, 0.45)       # fractional position of dV0 in the base cell
 
@@ -564,6 +611,8 @@ def run_ours(args, rank, world, local_rank):
         sys.stderr.write(json.dumps({key: out[key]}) + "\n")
         sys.stderr.flush()
 
+    if not args.no_cfg4 and not args.profile_run:
+        study("cfg4", lambda: cfg4_comparison(TAU, M, stream))
     if args.strategies:
         study("strategies", lambda: strategy_sweep(ctx, b, nsys, TAU, M, ikr.MIXED))
     if args.schur:

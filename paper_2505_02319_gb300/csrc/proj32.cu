@@ -214,7 +214,9 @@ int proj_chunks32() { return kPG; }
 
 void proj_coef32(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef,
                  const OrbSet& set) {
-  if (tc_proj_ok(c, set)) {
+  // the tensor-core coefficient kernel reads two plane waves per 16-byte load: even strides
+  // only (vectors in a caller's layout, e.g. Nb_k-strided, take the CUDA cores)
+  if (tc_proj_ok(c, set) && ldy % 2 == 0) {
     proj_coef_tc(c, L, Y, ldy, active, coef, set);
     return;
   }
