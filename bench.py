@@ -68,6 +68,9 @@ def parse():
                    help="leave out the mixed-vs-FP64 comparison on the largest workload (cfg4)")
     p.add_argument("--no-cpu-baseline", action="store_true",
                    help="leave out the oracle's timed solve (for runs of the studies only)")
+    p.add_argument("--profile-cfg4-tc", action="store_true",
+                   help="set up cfg4 and run one mixed solve with the tensor-core projections inside the "
+                        "NVTX range cfg4_tc, then exit (for an ncu capture of the tensor-core kernels)")
     p.add_argument("--profile-run", action="store_true",
                    help="only setup, warm-up and the timed steps (for ncu); prints no bench line")
     return p.parse_args()
@@ -468,6 +471,28 @@ def supercell_study(ells, tau, m, precision):
 
 
 # ------------------------------------------------------------------- ours --
+def profile_cfg4_tc():
+    """One mixed cfg4 solve (Schur form, bal) with the tensor-core projections,
+    inside the NVTX range cfg4_tc."""
+    import numpy as np
+    import torch
+    from paper_2505_02319_gb300 import groundstate
+    from workloads import make_system, perturbation
+    s = make_system("cfg4")
+    ctx = groundstate.context_for(s, eig_tol=1e-9, schur=True)
+    nsys = ctx.groundstate_nsys
+    b, _ = ctx.apply_chi0(torch.tensor(perturbation(s).ravel(), device="cuda"), tol=np.full(nsys, 1e-12))
+    b = (b / torch.linalg.norm(b)).contiguous()
+    ctx.set_tensor_cores(True)
+    ctx.solve_response(b, tau=1e-2, strategy="bal", precision="mixed")
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("cfg4_tc")
+    ctx.solve_response(b, tau=TAU, m=M, strategy="bal", precision="mixed")
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    ctx.destroy()
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -476,6 +501,9 @@ def run_ours(args, rank, world, local_rank):
     __graft_entry__.build()
     from paper_2505_02319_gb300 import groundstate, ikr
     from workloads import make_system, perturbation
+    if args.profile_cfg4_tc:
+        profile_cfg4_tc()
+        return
 
     dist = None
     if world > 1:
