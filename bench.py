@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--cfg4-guaranteed", action="store_true",
                    help="also solve the 64-atom cell with Kleinman-Bylander projectors (cfg4) with the "
                         "guaranteed rule grt_exact, beside bal")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default kernel variants instead of timing them on the workload")
     p.add_argument("--no-cfg4", action="store_true",
                    help="leave out the mixed-vs-FP64 comparison on the largest workload (cfg4)")
     p.add_argument("--no-cpu-baseline", action="store_true",
@@ -520,6 +522,8 @@ def run_ours(args, rank, world, local_rank):
     ctx = groundstate.context_for(s)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
+    # the kernel variants (plane kernels, projection path) chosen by timing on this workload
+    tuned = None if args.no_autotune else ctx.autotune()
     info = ctx.groundstate_info(ctx.nbands, s.n_grid)
     nsys = int(info["nocc"].sum())
     dV = torch.tensor(perturbation(s).ravel(), device="cuda")
@@ -605,7 +609,11 @@ def run_ours(args, rank, world, local_rank):
     peaks, src = measured_peaks()
     dev = ikr.device_peaks()
     alu = alu_peaks(dev, clk.get("sm_mhz") or dev["sm_clock_mhz"])
-    roof = roofline(prof["plane"], geom, peaks, alu, dev)
+    # which plane kernels ran: the autotuner's choice, else the defaults (or the environment's)
+    rc = tuned["plane_rc"] if tuned else int(os.environ.get("IKR_PLANE_RC", "5"))
+    sw = tuned["plane_sw"] if tuned else os.environ.get("IKR_PLANE_SW", "1") != "0"
+    roof = roofline(prof["plane"], geom, peaks, alu, dev, fp32_kernel="k_plane_rc" if rc else "k_plane_r",
+                    df64_kernel="k_plane_sw" if sw else "k_plane_t")
     value = t_max / args.steps
     out = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -628,6 +636,7 @@ def run_ours(args, rank, world, local_rank):
                                 for k, v in shares.items()},
         "dominant_class": dominant,
         "setup_s": setup_s,
+        "autotune": tuned,
     }
     def study(key, fn):
         """Runs one optional study; its result (or its error) goes into the line and,
@@ -683,14 +692,27 @@ def alu_peaks(dev, sm_mhz):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per system of one
-# launch of each plane kernel, from one ncu capture of a launch with every
-# system active (k_plane_r: 22.89 MB read + 7 KB written for 252 systems;
-# k_plane_t<dfloat>: 41.83 MB + 4.48 MB for 251), 48^3 grid
-TRAFFIC_PER_UNIT_FP32 = (22.888e6 + 7.2e3) / 252
-TRAFFIC_PER_UNIT_DF64 = (41.832e6 + 4.479e6) / 251
+# launch of each plane kernel, from one ncu capture of a launch of the cfg2 solve
+# (48^3 grid) per kernel:
+#   k_plane_r<48,48>:       22.888 MB read + 7.2 KB written, 252 systems
+#   k_plane_rc<48,48,5>:    20.149 MB + 22.0 KB, 47 groups of 4 systems (185-188; 186.5 taken)
+#   k_plane_t<dfloat,48,48>: 41.832 MB + 4.479 MB, 251 systems
+#   k_plane_sw<48,48>:      40.250 MB + 2.496 MB, 251 systems
+TRAFFIC_PER_UNIT = {
+    "k_plane_r": (22.888e6 + 7.2e3) / 252,
+    "k_plane_rc": (20.149e6 + 22.0e3) / 186.5,
+    "k_plane_t": (41.832e6 + 4.479e6) / 251,
+    "k_plane_sw": (40.250e6 + 2.496e6) / 251,
+}
+KERNEL_NAMES = {
+    "k_plane_r": "k_plane_r<48,48> (FP32 H_k plane pass of the CG, full plane in shared memory)",
+    "k_plane_rc": "k_plane_rc<48,48> (FP32 H_k plane pass of the CG, active columns in shared memory)",
+    "k_plane_t": "k_plane_t<dfloat,48,48> (FP64-accurate plane pass, double-float, padded rows)",
+    "k_plane_sw": "k_plane_sw<48,48> (FP64-accurate plane pass, double-float, swizzled plane)",
+}
 
 
-def roofline(d, geom, peaks, alu, dev):
+def roofline(d, geom, peaks, alu, dev, fp32_kernel="k_plane_rc", df64_kernel="k_plane_sw"):
     """Roofline of the plane pass (the H_k application of the Sternheimer CG),
     from the library's CUDA events over the timed steps: achieved = algorithmic
     flops of the units (system-plane passes) the launches processed / their
@@ -707,9 +729,9 @@ def roofline(d, geom, peaks, alu, dev):
         tfl = d["units_fp32"] * f32 / t / 1e12
         gbs = d["units_fp32"] * b32 / t / 1e9
         entries.append((d["ms_fp32"], {
-            "kernel": "k_plane_r<48,48> (H_k plane pass of the FP32 CG)", "bound": "alu",
+            "kernel": KERNEL_NAMES[fp32_kernel], "bound": "alu",
             "achieved": tfl, "peak": alu["fp32"], "unit": "TFLOP/s", "frac": tfl / alu["fp32"],
-            "traffic": TRAFFIC_PER_UNIT_FP32 * d["units_fp32"] / calls if geom[:3] == (48, 48, 48) else None,
+            "traffic": TRAFFIC_PER_UNIT[fp32_kernel] * d["units_fp32"] / calls if geom[:3] == (48, 48, 48) else None,
             "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled to the average launch)",
             "peak_source": f"derived: {alu['sms']} SMs (device) x 128 FP32 lanes x 2 x {alu['sm_mhz']:.0f} MHz "
                            f"(median SM clock sampled during the timed steps)",
@@ -722,10 +744,10 @@ def roofline(d, geom, peaks, alu, dev):
         calls = max(d["calls_fp64"], 1)
         tfl = d["units_fp64"] * f64 / t / 1e12
         entries.append((d["ms_fp64"], {
-            "kernel": "k_plane_t<dfloat,48,48> (FP64-accurate plane pass, double-float on the FP32 pipe)",
+            "kernel": KERNEL_NAMES[df64_kernel],
             "bound": "alu", "achieved": tfl, "peak": alu["df64"], "unit": "TFLOP/s (FP64-equivalent)",
             "frac": tfl / alu["df64"],
-            "traffic": TRAFFIC_PER_UNIT_DF64 * d["units_fp64"] / calls if geom[:3] == (48, 48, 48) else None,
+            "traffic": TRAFFIC_PER_UNIT[df64_kernel] * d["units_fp64"] / calls if geom[:3] == (48, 48, 48) else None,
             "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled to the average launch)",
             "peak_source": f"derived: FP32 instruction peak ({alu['sms']} SMs x 128 x {alu['sm_mhz']:.0f} MHz) / "
                            f"{DF64_INSTR_PER_FLOP:.2f} FP32 instructions per double-float flop",

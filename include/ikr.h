@@ -235,6 +235,24 @@ ikr_status ikr_projection_coefficients(ikr_ctx* ctx, int k, int nvec, const void
  * overwritten.  Errors as ikr_projection_coefficients. */
 ikr_status ikr_project_out(ikr_ctx* ctx, int k, int nvec, void* y, int method, cudaStream_t stream);
 
+/* Autotuner (no counterpart in the paper).  Several kernels have variants that
+ * compute the same result with different launch shapes and layouts; this call
+ * times them on the context's own occupied systems (on `stream`, CUDA events,
+ * best of two after one untimed run) and keeps the fastest for every later
+ * call on the context:
+ *   - a 4-iteration FP32 CG over all systems for each FP32 plane kernel
+ *     (full-plane; compact at 4 or 5 blocks per SM) with the projection
+ *     products on the CUDA cores (fused cluster update) or the tensor cores;
+ *   - one FP64-accurate (double-float) H_k application over all systems for
+ *     the padded and the swizzled plane kernel, on 48 x 48 planes.
+ * The variants agree to FP32 (double-float) rounding.  out: HOST, 12 doubles:
+ * [0..5] ms per CG iteration for (CUDA cores: plane 0, 4, 5; tensor cores:
+ * plane 0, 4, 5), [6] chosen FP32 plane variant (0, 4, 5), [7] tensor cores
+ * chosen (0/1), [8..9] ms of the double-float application (padded, swizzled;
+ * -1 when not timed), [10] swizzled chosen (0/1), [11] unused (-1).
+ * IKR_ERR_STATE before the eigenpairs are set. */
+ikr_status ikr_autotune(ikr_ctx* ctx, double* out, cudaStream_t stream);
+
 /* Arithmetic throughput of the current device, measured by FMA-chain and
  * radix-4 butterfly kernels timed with CUDA events on `stream` (about 0.1 s).
  * The paper has no counterpart: these are the measured references of the ALU

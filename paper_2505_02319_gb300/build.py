@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libikr.so")
-SOURCES = ["fft.cu", "fft_plane.cu", "fft_reg.cu", "ops.cu", "proj32.cu", "cg_fused.cu", "eigen.cu", "kb.cu", "batch.cu", "tc_proj.cu", "setup.cu", "solver.cu", "mixed.cu", "capi.cu", "noalloc.cu", "peaks.cu"]
+SOURCES = ["fft.cu", "fft_plane.cu", "fft_reg.cu", "ops.cu", "proj32.cu", "cg_fused.cu", "eigen.cu", "kb.cu", "batch.cu", "tc_proj.cu", "setup.cu", "solver.cu", "mixed.cu", "capi.cu", "noalloc.cu", "peaks.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
 

@@ -269,6 +269,12 @@ ikr_status ikr_compute_eigenpairs(ikr_ctx* c, int nbands, double tol, int maxit,
   return s;
 }
 
+ikr_status ikr_autotune(ikr_ctx* c, double* out, cudaStream_t stream) {
+  if (!c || !out) return IKR_ERR_ARG;
+  c->stream = stream;
+  return guarded(c, [&] { ikr::autotune(c, out); });
+}
+
 ikr_status ikr_device_peaks(double* out, cudaStream_t stream) {
   if (!out) return IKR_ERR_ARG;
   try {

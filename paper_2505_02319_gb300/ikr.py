@@ -108,6 +108,7 @@ def _load():
         "ikr_profile_read": (I, [P, ct.POINTER(KernelStat), I]),
         "ikr_fft_geometry": (I, [P, ct.POINTER(I)]),
         "ikr_device_peaks": (I, [ct.POINTER(ct.c_double), P]),
+        "ikr_autotune": (I, [P, ct.POINTER(ct.c_double), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -220,6 +221,17 @@ class Context:
         """Schur-complement Sternheimer solves over the extra computed bands
         (ikr_set_schur): same chi0, better conditioned CG."""
         self._check(_LIB.ikr_set_schur(self._h, 1 if enable else 0))
+
+    def autotune(self):
+        """Time the interchangeable kernel variants on this context's systems and
+        keep the fastest (ikr_autotune); returns the timings and the choice."""
+        out = (ct.c_double * 12)()
+        self._check(_LIB.ikr_autotune(self._h, out, _stream()))
+        v = list(out)
+        return {"cg_iter_ms_cuda_cores": {"plane_full": v[0], "plane_compact4": v[1], "plane_compact5": v[2]},
+                "cg_iter_ms_tensor_cores": {"plane_full": v[3], "plane_compact4": v[4], "plane_compact5": v[5]},
+                "plane_rc": int(v[6]), "tensor_cores": bool(v[7]),
+                "df64_apply_ms": {"padded": v[8], "swizzled": v[9]}, "plane_sw": bool(v[10])}
 
     def set_tensor_cores(self, enable=True):
         """FP32 projection coefficients on the tensor cores (ikr_set_tensor_cores)."""

@@ -60,14 +60,16 @@ def test_roofline_picks_dominant_kernel_and_scales_traffic():
     assert math.isclose(alu["df64"], alu["fp32"] / 2 / bench.DF64_INSTR_PER_FLOP)
     d = dict(ms_fp32=20.0, units_fp32=40000, calls_fp32=300, ms_fp64=25.0, units_fp64=7000, calls_fp64=35)
     r = bench.roofline(d, geom, peaks, alu, dev)
-    assert r["kernel"].startswith("k_plane_t<dfloat")                    # 25 ms > 20 ms
+    assert r["kernel"].startswith("k_plane_sw<48,48>")                   # 25 ms > 20 ms
     _, f64 = bench.plane_pass_work(geom, 8)
     assert math.isclose(r["achieved"], 7000 * f64 / 25e-3 / 1e12, rel_tol=1e-12)
     assert math.isclose(r["frac"], r["achieved"] / alu["df64"], rel_tol=1e-12)
-    assert math.isclose(r["traffic"], bench.TRAFFIC_PER_UNIT_DF64 * 7000 / 35, rel_tol=1e-12)
+    assert math.isclose(r["traffic"], bench.TRAFFIC_PER_UNIT["k_plane_sw"] * 7000 / 35, rel_tol=1e-12)
     o = r["other_plane_kernel"]
     _, f32 = bench.plane_pass_work(geom, 4)
     assert math.isclose(o["frac"], 40000 * f32 / 20e-3 / 1e12 / alu["fp32"], rel_tol=1e-12)
     # another grid: no traffic figure (the captures are of the 48^3 grid)
     assert bench.roofline(d, (32, 32, 32, 200, 15), peaks, alu, dev)["traffic"] is None
-    assert bench.roofline(dict(d, ms_fp64=0.0, units_fp64=0), geom, peaks, alu, dev)["kernel"].startswith("k_plane_r")
+    assert bench.roofline(dict(d, ms_fp64=0.0, units_fp64=0), geom, peaks, alu, dev)["kernel"].startswith("k_plane_rc")
+    r0 = bench.roofline(d, geom, peaks, alu, dev, fp32_kernel="k_plane_r", df64_kernel="k_plane_t")
+    assert r0["kernel"].startswith("k_plane_t<dfloat") and r0["other_plane_kernel"]["kernel"].startswith("k_plane_r<")
