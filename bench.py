@@ -70,9 +70,9 @@ def parse():
                    help="leave out the mixed-vs-FP64 comparison on the largest workload (cfg4)")
     p.add_argument("--no-cpu-baseline", action="store_true",
                    help="leave out the oracle's timed solve (for runs of the studies only)")
-    p.add_argument("--profile-cfg4-tc", action="store_true",
-                   help="set up cfg4 and run one mixed solve with the tensor-core projections inside the "
-                        "NVTX range cfg4_tc, then exit (for an ncu capture of the tensor-core kernels)")
+    p.add_argument("--profile-tc", default=None, metavar="WORKLOAD",
+                   help="set up the workload (cfg1, cfg4, ...) and run one mixed solve with the tensor-core "
+                        "projections inside the NVTX range tc_solve, then exit (for ncu captures)")
     p.add_argument("--profile-run", action="store_true",
                    help="only setup, warm-up and the timed steps (for ncu); prints no bench line")
     return p.parse_args()
@@ -399,6 +399,9 @@ def cfg4_comparison(tau, m, stream):
     out = {"workload": "cfg4: 20.5 bohr cell, 64 Gaussian atoms with s+p KB projectors, Ecut 20 Ha, 96^3 grid, "
                        "Gamma, 136 bands (N_occ 128), Schur-complement solves, bal, tau = 1e-8, m = 20",
            "setup_s": setup}
+    def classes(prof):
+        return {k: round(v["ms_fp32"] + v["ms_fp64"], 2) for k, v in prof.items() if v["ms_fp32"] + v["ms_fp64"] > 0}
+
     for prec in ("mixed", "fp64"):
         ctx.solve_response(b, tau=1e-2, m=m, strategy="bal", precision=prec)          # workspaces, shapes
         (x, rep), t = timed(lambda: ctx.solve_response(b, tau=tau, m=m, strategy="bal", precision=prec), stream)
@@ -409,15 +412,23 @@ def cfg4_comparison(tau, m, stream):
     out["speedup_mixed_vs_fp64"] = out["fp64"]["time_s"] / out["mixed"]["time_s"]
     # the same mixed solve with the FP32 projection products (occupied, extra and
     # Kleinman-Bylander vectors) on the tensor cores
+    # kernel time per class of one mixed solve (library CUDA events), CUDA cores and tensor cores
+    from paper_2505_02319_gb300 import ikr
+    ctx.profile_start(timed=ikr.Context.KERNEL_CLASSES)
+    ctx.solve_response(b, tau=tau, m=m, strategy="bal", precision="mixed")
+    out["mixed"]["kernel_ms"] = classes(ctx.profile_read())
     ctx.set_tensor_cores(True)
     try:
         ctx.solve_response(b, tau=1e-2, m=m, strategy="bal", precision="mixed")
         (x, rep), t = timed(lambda: ctx.solve_response(b, tau=tau, m=m, strategy="bal", precision="mixed"), stream)
+        ctx.profile_start(timed=ikr.Context.KERNEL_CLASSES)
+        ctx.solve_response(b, tau=tau, m=m, strategy="bal", precision="mixed")
+        tc_classes = classes(ctx.profile_read())
     finally:
         ctx.set_tensor_cores(False)
     Ex, _ = ctx.apply_dielectric(x, tol=np.full(nsys, 1e-12))
     out["mixed_tensor_cores"] = {"time_s": t, "status": rep[0]["status"], "n_ham": rep[0]["n_ham"],
-                                 "true_residual": float(torch.linalg.norm(b - Ex))}
+                                 "true_residual": float(torch.linalg.norm(b - Ex)), "kernel_ms": tc_classes}
     ctx.destroy()
     return out
 
@@ -473,22 +484,22 @@ def supercell_study(ells, tau, m, precision):
 
 
 # ------------------------------------------------------------------- ours --
-def profile_cfg4_tc():
-    """One mixed cfg4 solve (Schur form, bal) with the tensor-core projections,
-    inside the NVTX range cfg4_tc."""
+def profile_tc(name):
+    """One mixed solve of the workload (Schur form where it has extra bands, bal)
+    with the tensor-core projections, inside the NVTX range tc_solve."""
     import numpy as np
     import torch
     from paper_2505_02319_gb300 import groundstate
     from workloads import make_system, perturbation
-    s = make_system("cfg4")
-    ctx = groundstate.context_for(s, eig_tol=1e-9, schur=True)
+    s = make_system(name)
+    ctx = groundstate.context_for(s, eig_tol=1e-9, schur=s.nbands > s.n_electrons // 2)
     nsys = ctx.groundstate_nsys
     b, _ = ctx.apply_chi0(torch.tensor(perturbation(s).ravel(), device="cuda"), tol=np.full(nsys, 1e-12))
     b = (b / torch.linalg.norm(b)).contiguous()
     ctx.set_tensor_cores(True)
     ctx.solve_response(b, tau=1e-2, strategy="bal", precision="mixed")
     torch.cuda.synchronize()
-    torch.cuda.nvtx.range_push("cfg4_tc")
+    torch.cuda.nvtx.range_push("tc_solve")
     ctx.solve_response(b, tau=TAU, m=M, strategy="bal", precision="mixed")
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
@@ -503,8 +514,8 @@ def run_ours(args, rank, world, local_rank):
     __graft_entry__.build()
     from paper_2505_02319_gb300 import groundstate, ikr
     from workloads import make_system, perturbation
-    if args.profile_cfg4_tc:
-        profile_cfg4_tc()
+    if args.profile_tc:
+        profile_tc(args.profile_tc)
         return
 
     dist = None
