@@ -418,6 +418,18 @@ def cfg4_comparison(tau, m, stream):
     out["speedup_mixed_vs_fp64"] = out["fp64"]["time_s"] / out["mixed"]["time_s"]
     # the same mixed solve with the FP32 projection products (occupied, extra and
     # Kleinman-Bylander vectors) on the tensor cores
+    # the FP32 Q-projection y <- y - Phi (Phi^H y) of 128 vectors (all active), CUDA cores
+    # against tensor cores, through ikr_project_out
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    nb0 = ctx.basis_size(0)
+    y0 = torch.complex(torch.randn(128, nb0, device="cuda", generator=gen),
+                       torch.randn(128, nb0, device="cuda", generator=gen)).to(torch.complex64)
+    proj = {}
+    for method, key in ((0, "cuda_cores_ms"), (1, "tensor_cores_ms")):
+        y = y0.clone()
+        ctx.project_out(0, y, method=method)
+        proj[key] = min(timed(lambda: ctx.project_out(0, y, method=method), stream)[1] for _ in range(3)) * 1e3
+    out["q_projection_128_vectors"] = proj
     # kernel time per class of one mixed solve (library CUDA events), CUDA cores and tensor cores
     from paper_2505_02319_gb300 import ikr
     ctx.profile_start(timed=ikr.Context.KERNEL_CLASSES)
