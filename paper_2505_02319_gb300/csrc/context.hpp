@@ -123,6 +123,8 @@ struct Workspace {
   // dphi^P coefficients and deps; per right-hand side the Krylov basis and three vectors
   DBuf<double> bu, bdrho, bnrm, bM, bCP, bdeps, bgm;
   DBuf<double2> bB, bX;
+  // tensor-core projections: the active systems of every k-point in order, and their counts
+  DBuf<int> tc_list, tc_cnt;
 };
 
 // offsets into the per-system scalar block (nsys doubles each)

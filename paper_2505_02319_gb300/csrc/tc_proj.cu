@@ -129,7 +129,8 @@ template <int NT>
 __global__ void __launch_bounds__(128, 1)
     k_tc_coef(const float2* __restrict__ phi, const int* __restrict__ set_off,
               const int* __restrict__ set_cnt, const int* __restrict__ nb_k, const int* __restrict__ kstart,
-              const int* __restrict__ kcount, const float2* __restrict__ Y, int ldy, int ld, int nmt, int nch,
+              const int* __restrict__ kcount, const int* __restrict__ slist, const int* __restrict__ scount,
+              const float2* __restrict__ Y, int ldy, int ld, int nmt, int nch,
               int maxcnt, const int* __restrict__ active, double2* __restrict__ part, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* sAhi = sm;
@@ -140,7 +141,9 @@ __global__ void __launch_bounds__(128, 1)
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
   const int k = blockIdx.y, chunk = blockIdx.x;
   const int tm = blockIdx.z % nmt, tn = blockIdx.z / nmt;
-  const int cnt = set_cnt[k], nb = nb_k[k], ns = kcount[k];
+  const int cnt = set_cnt[k], nb = nb_k[k], ns = scount ? scount[k] : kcount[k];
+  // system of tile row j: the k-point's j-th active system (compacted list) or its j-th system
+  auto sys_at = [&](int j) { return slist ? slist[kstart[k] + j] : kstart[k] + j; };
   const int i0 = tm * kTM, s0 = tn * NT;
   const int k0 = chunk * kTC, k1 = min(k0 + kTC, 2 * nb);
   if (i0 >= 2 * cnt || s0 >= ns || k0 >= k1) return;   // uniform over the block
@@ -154,7 +157,6 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t tmem = *slot;
   const float* vbase = reinterpret_cast<const float*>(phi + ((size_t)set_off[k] + i0 / 2) * ld);
   const size_t lda = 2 * (size_t)ld;                    // reals per orbital
-  const int sbase = kstart[k] + s0;
   bool ok = true;
   uint32_t phase = 0;
   uint32_t acc = 0;
@@ -176,11 +178,14 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
     for (int j = 0; j < kBE; ++j) {
       const int e = tid + 128 * j, r = e >> 3, c4 = e & 7;
-      const int s = sbase + r, re = kb + 4 * c4;       // first real of the group (two plane waves)
+      const int re = kb + 4 * c4;                      // first real of the group (two plane waves)
       rb[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (s0 + r < ns && (!active || active[s]) && re < k1) {
-        rb[j] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Y + (size_t)s * ldy) + re);
-        if (re + 2 >= k1) rb[j].z = rb[j].w = 0.f;      // second plane wave past Nb_k
+      if (s0 + r < ns && re < k1) {
+        const int s = sys_at(s0 + r);
+        if (!active || active[s]) {
+          rb[j] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Y + (size_t)s * ldy) + re);
+          if (re + 2 >= k1) rb[j].z = rb[j].w = 0.f;    // second plane wave past Nb_k
+        }
       }
     }
   };
@@ -253,9 +258,10 @@ __global__ void __launch_bounds__(128, 1)
       for (int j = 0; j < 32; ++j) {
         const float im = __shfl_xor_sync(0xffffffffu, v[j], 1);
         const int sl = s0 + c0 + j;
-        const int s = kstart[k] + sl;
-        if (!(lane & 1) && i < 2 * cnt && sl < ns && (!active || active[s]))
-          part[((size_t)s * maxcnt + m) * nch + chunk] = make_double2((double)v[j], (double)im);
+        if (!(lane & 1) && i < 2 * cnt && sl < ns) {
+          const int s = sys_at(sl);
+          if (!active || active[s]) part[((size_t)s * maxcnt + m) * nch + chunk] = make_double2((double)v[j], (double)im);
+        }
       }
     }
   }
@@ -274,6 +280,7 @@ template <int NT>
 __global__ void __launch_bounds__(128, 1)
     k_tc_apply(const float2* __restrict__ phi, const int* __restrict__ set_off, const int* __restrict__ set_cnt,
                const int* __restrict__ nb_k, const int* __restrict__ kstart, const int* __restrict__ kcount,
+               const int* __restrict__ slist, const int* __restrict__ scount,
                const double2* __restrict__ coef, int maxcnt, const float2* in, float alpha, float beta,
                float2* out, int ldy, int ld, const float2* __restrict__ dv, double* __restrict__ dpart, int nparts,
                const int* __restrict__ active, int* __restrict__ err) {
@@ -286,15 +293,18 @@ __global__ void __launch_bounds__(128, 1)
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
   double* red = reinterpret_cast<double*>(slot + 2);              // [4 warps][NT] dot partials
   const int k = blockIdx.y, tile = blockIdx.x, tn = blockIdx.z;
-  const int cnt = set_cnt[k], nb = nb_k[k], ns = kcount[k];
+  const int cnt = set_cnt[k], nb = nb_k[k], ns = scount ? scount[k] : kcount[k];
+  // system of tile row j: the k-point's j-th active system (compacted list) or its j-th system
+  auto sys_at = [&](int j) { return slist ? slist[kstart[k] + j] : kstart[k] + j; };
   const int r0 = tile * kTM, s0 = tn * NT;                        // first real row (2 g + c), first system
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (s0 >= ns) return;                                           // uniform
   if (r0 >= 2 * nb) {                                             // tile past Nb_k: define the dot partials
     if (dpart)
       for (int j = tid; j < NT; j += 128) {
-        const int s = kstart[k] + s0 + j;
-        if (s0 + j < ns && (!active || active[s])) dpart[(size_t)s * nparts + tile] = 0.0;
+        if (s0 + j >= ns) continue;
+        const int s = sys_at(s0 + j);
+        if (!active || active[s]) dpart[(size_t)s * nparts + tile] = 0.0;
       }
     return;
   }
@@ -307,7 +317,6 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t tmem = *slot;
   const int g0 = r0 / 2;                                          // first plane wave of the tile
   const float2* vk = phi + (size_t)set_off[k] * ld;
-  const int sbase = kstart[k] + s0;
   const int kend = 2 * cnt;
   bool ok = true;
   uint32_t phase = 0, acc = 0;
@@ -333,8 +342,8 @@ __global__ void __launch_bounds__(128, 1)
     for (int e = tid; e < NT * (kTK / 4); e += 128) {
       const int r = e >> 3, c4 = e & 7;
       float x[4] = {0.f, 0.f, 0.f, 0.f};
-      const int s = sbase + r;
-      if (s0 + r < ns && (!active || active[s]))
+      const int s = s0 + r < ns ? sys_at(s0 + r) : -1;
+      if (s >= 0 && (!active || active[s]))
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           const int i = kb + 4 * c4 + 2 * q;                      // real index 2 m (+1 below)
@@ -388,8 +397,8 @@ __global__ void __launch_bounds__(128, 1)
       for (int j = 0; j < 32; ++j) {
         const float im = __shfl_xor_sync(0xffffffffu, v[j], 1);
         const int sl = s0 + c0 + j;
-        const int s = kstart[k] + sl;
-        const bool on = !(lane & 1) && g < nb && sl < ns && (!active || active[s]);
+        const int s = sl < ns ? sys_at(sl) : -1;
+        const bool on = !(lane & 1) && g < nb && s >= 0 && (!active || active[s]);
         double d = 0.0;
         if (on) {
           const size_t o = (size_t)s * ldy + g;
@@ -414,8 +423,9 @@ __global__ void __launch_bounds__(128, 1)
     if (dpart) {
       __syncthreads();
       for (int j = tid; j < NT; j += 128) {
-        const int s = kstart[k] + s0 + j;
-        if (s0 + j < ns && (!active || active[s]))
+        if (s0 + j >= ns) continue;
+        const int s = sys_at(s0 + j);
+        if (!active || active[s])
           dpart[(size_t)s * nparts + tile] = ((red[j] + red[NT + j]) + red[2 * NT + j]) + red[3 * NT + j];
       }
     }
@@ -452,7 +462,45 @@ __global__ void k_tc_reduce(const double2* __restrict__ part, int nsys, int maxc
   if (lane == 0) coef[w] = make_double2(ax, ay);
 }
 
+// The active systems of every k-point, in order, at the k-point's offset kstart[k]
+// (slist), and their number (scount): the tensor-core kernels tile over these, so
+// systems whose CG has finished cost nothing.  One warp per k-point: ballot and
+// population count over chunks of 32 systems.
+__global__ void k_tc_compact(const int* __restrict__ active, const int* __restrict__ kstart,
+                             const int* __restrict__ kcount, int nk, int* __restrict__ slist,
+                             int* __restrict__ scount) {
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (k >= nk) return;
+  const int s0 = kstart[k], n = kcount[k];
+  int pos = 0;
+  for (int j0 = 0; j0 < n; j0 += 32) {
+    const int j = j0 + lane;
+    const bool a = j < n && active[s0 + j] != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, a);
+    if (a) slist[s0 + pos + __popc(m & ((1u << lane) - 1u))] = s0 + j;
+    pos += __popc(m);
+  }
+  if (lane == 0) scount[k] = pos;
+}
+
 // ----------------------------------------------------------------- host --
+
+namespace {
+// compacted active lists for a masked launch (nullptr, nullptr without a mask)
+void tc_active_lists(ikr_ctx* c, const SysList& L, const int* active, const int** slist, const int** scount) {
+  *slist = nullptr;
+  *scount = nullptr;
+  if (!active || L.n == 0) return;
+  const int nk = (int)c->k.size();
+  c->ws.tc_list.reserve(L.n);
+  c->ws.tc_cnt.reserve(nk);
+  k_tc_compact<<<(nk + 3) / 4, 128, 0, c->stream>>>(active, L.d_kstart.p, L.d_kcount.p, nk, c->ws.tc_list.p,
+                                                     c->ws.tc_cnt.p);
+  IKR_CUDA(cudaGetLastError());
+  *slist = c->ws.tc_list.p;
+  *scount = c->ws.tc_cnt.p;
+}
+}  // namespace
 
 // the error flag of the tensor-core kernels: set by any launch whose wait ran out,
 // cleared only when it is created and by tc_check, so no later launch hides it
@@ -481,10 +529,12 @@ void proj_coef_tc(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const 
   tc_flag_ready(c);
   dim3 grid(nch, (unsigned)c->k.size(), (unsigned)(nmt * std::max(nnt, 1)));
   const size_t smem = 2 * kTileBytes + 2 * (size_t)nt * kTK * 4 + 64;
+  const int *slist, *scount;
+  tc_active_lists(c, L, active, &slist, &scount);
   auto launch = [&](auto kern) {
     IKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, 128, smem, c->stream>>>(set.phi32, set.off, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p, Y,
-                                         ldy, c->ld, nmt, nch, set.maxcnt, active, part, c->tc_err.p);
+    kern<<<grid, 128, smem, c->stream>>>(set.phi32, set.off, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p, slist,
+                                         scount, Y, ldy, c->ld, nmt, nch, set.maxcnt, active, part, c->tc_err.p);
   };
   if (nt == 32) launch(k_tc_coef<32>);
   else if (nt == 64) launch(k_tc_coef<64>);
@@ -506,11 +556,13 @@ void proj_apply_tc(ikr_ctx* c, const SysList& L, const double2* coef, const floa
   tc_flag_ready(c);
   dim3 grid(nparts, (unsigned)c->k.size(), (unsigned)nnt);
   const size_t smem = 2 * kTileBytes + 2 * (size_t)nt * kTK * 4 + 16 + 32 * (size_t)nt;
+  const int *slist, *scount;
+  tc_active_lists(c, L, active, &slist, &scount);
   auto launch = [&](auto kern) {
     IKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, 128, smem, c->stream>>>(set.phi32, set.off, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p, coef,
-                                         set.maxcnt, in, alpha, beta, out, ldy, c->ld, dv, dpart, nparts, active,
-                                         c->tc_err.p);
+    kern<<<grid, 128, smem, c->stream>>>(set.phi32, set.off, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p, slist,
+                                         scount, coef, set.maxcnt, in, alpha, beta, out, ldy, c->ld, dv, dpart, nparts,
+                                         active, c->tc_err.p);
   };
   if (nt == 32) launch(k_tc_apply<32>);
   else if (nt == 64) launch(k_tc_apply<64>);
