@@ -121,6 +121,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
+// Work item e of a tile fill -> (row, 16-byte group c4 along K).  In the canonical
+// K-major layout the 16-byte bank slot of an element is row mod 8, so a quarter-warp
+// (8 threads, one 128-byte wavefront) must write 8 different rows: lanes 0-7 of a warp
+// take rows 8 b .. 8 b + 7 at one group, lanes 8-15 the next group, ...; every row then
+// gets 4 consecutive groups (64 contiguous bytes of its global vector) from one warp.
+__device__ __forceinline__ void tile_item(int e, int& row, int& c4) {
+  const int q = e & 31, w = e >> 5;
+  row = (q & 7) + 8 * (w >> 1);
+  c4 = (q >> 3) + 4 * (w & 1);
+}
+
 }  // namespace
 
 // Partial sums of D = A B^T over one split-K chunk: part[(s * maxcnt + m) * nch + chunk] = (Re, Im) C[s][m].
@@ -168,7 +179,8 @@ __global__ void __launch_bounds__(128, 1)
   auto fetch = [&](int kb) {
 #pragma unroll
     for (int j = 0; j < kAE; ++j) {
-      const int e = tid + 128 * j, mo = e >> 3, c4 = e & 7;
+      int mo, c4;
+      tile_item(tid + 128 * j, mo, c4);
       ra[j] = make_float4(0.f, 0.f, 0.f, 0.f);
       // orbitals past cnt are zero; the orbitals are zero past Nb_k, so a group across
       // 2 Nb_k needs no mask
@@ -177,7 +189,8 @@ __global__ void __launch_bounds__(128, 1)
     }
 #pragma unroll
     for (int j = 0; j < kBE; ++j) {
-      const int e = tid + 128 * j, r = e >> 3, c4 = e & 7;
+      int r, c4;
+      tile_item(tid + 128 * j, r, c4);
       const int re = kb + 4 * c4;                      // first real of the group (two plane waves)
       rb[j] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (s0 + r < ns && re < k1) {
@@ -195,7 +208,8 @@ __global__ void __launch_bounds__(128, 1)
     // waves per 16-byte group; B tile: the systems' vectors; both split into hi and lo
 #pragma unroll
     for (int j = 0; j < kAE; ++j) {
-      const int e = tid + 128 * j, mo = e >> 3, c4 = e & 7;
+      int mo, c4;
+      tile_item(tid + 128 * j, mo, c4);
       const float4 x = ra[j];
       const float4 y = make_float4(-x.y, x.x, -x.w, x.z);
       const float4 xh = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
@@ -209,7 +223,8 @@ __global__ void __launch_bounds__(128, 1)
     }
 #pragma unroll
     for (int j = 0; j < kBE; ++j) {
-      const int e = tid + 128 * j, r = e >> 3, c4 = e & 7;
+      int r, c4;
+      tile_item(tid + 128 * j, r, c4);
       const float4 x = rb[j];
       const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
       *reinterpret_cast<float4*>(sBhi + core_off(r, c4)) = h;
@@ -322,25 +337,29 @@ __global__ void __launch_bounds__(128, 1)
   uint32_t phase = 0, acc = 0;
   for (int kb = 0; kb < kend && ok; kb += kTK) {
     // A tile = AT[2g + c][2m + q] from the orbitals: (c, q) = (0, 0) Re v_m[g], (0, 1) -Im,
-    // (1, 0) Im, (1, 1) Re; 64 plane waves x 16 orbitals, plane waves fastest (coalesced);
-    // orbitals past cnt are zero (g0 + 63 < ld: the orbitals are zero past Nb_k)
-    for (int e = tid; e < (kTM / 2) * (kTK / 2); e += 128) {
-      const int gl = e & 63, ml = e >> 6;
-      const int m = kb / 2 + ml;
-      float2 p = make_float2(0.f, 0.f);
-      if (m < cnt) p = vk[(size_t)m * ld + g0 + gl];
-      const float v4[4] = {p.x, -p.y, p.y, p.x};
-      const int c4 = ml >> 1, wpos = 2 * (ml & 1);
-#pragma unroll
-      for (int cq = 0; cq < 4; ++cq) {
-        const int byte = core_off(2 * gl + (cq >> 1), c4) + 4 * (wpos + (cq & 1));
-        const float h = tf32_hi(v4[cq]);
-        *reinterpret_cast<float*>(sAhi + byte) = h;
-        *reinterpret_cast<float*>(sAlo + byte) = v4[cq] - h;
-      }
+    // (1, 0) Im, (1, 1) Re; an item is one plane wave and one 16-byte group (orbitals 2 c4,
+    // 2 c4 + 1), written as one 16-byte store per row; consecutive threads take consecutive
+    // plane waves (coalesced loads; rows 2 g and 2 g + 1 of a quarter-warp fall 2 per bank
+    // slot); orbitals past cnt are zero (g0 + 63 < ld: the orbitals are zero past Nb_k)
+    for (int e = tid; e < (kTM / 2) * (kTK / 4); e += 128) {
+      const int gl = e & 63, c4 = e >> 6;
+      const int m0 = kb / 2 + 2 * c4;
+      const float2 z = make_float2(0.f, 0.f);
+      const float2 p0 = m0 < cnt ? vk[(size_t)m0 * ld + g0 + gl] : z;
+      const float2 p1 = m0 + 1 < cnt ? vk[(size_t)(m0 + 1) * ld + g0 + gl] : z;
+      const float4 r0 = make_float4(p0.x, -p0.y, p1.x, -p1.y), r1 = make_float4(p0.y, p0.x, p1.y, p1.x);
+      const float4 h0 = make_float4(tf32_hi(r0.x), tf32_hi(r0.y), tf32_hi(r0.z), tf32_hi(r0.w));
+      const float4 h1 = make_float4(tf32_hi(r1.x), tf32_hi(r1.y), tf32_hi(r1.z), tf32_hi(r1.w));
+      *reinterpret_cast<float4*>(sAhi + core_off(2 * gl, c4)) = h0;
+      *reinterpret_cast<float4*>(sAlo + core_off(2 * gl, c4)) =
+          make_float4(r0.x - h0.x, r0.y - h0.y, r0.z - h0.z, r0.w - h0.w);
+      *reinterpret_cast<float4*>(sAhi + core_off(2 * gl + 1, c4)) = h1;
+      *reinterpret_cast<float4*>(sAlo + core_off(2 * gl + 1, c4)) =
+          make_float4(r1.x - h1.x, r1.y - h1.y, r1.z - h1.z, r1.w - h1.w);
     }
     for (int e = tid; e < NT * (kTK / 4); e += 128) {
-      const int r = e >> 3, c4 = e & 7;
+      int r, c4;
+      tile_item(e, r, c4);
       float x[4] = {0.f, 0.f, 0.f, 0.f};
       const int s = s0 + r < ns ? sys_at(s0 + r) : -1;
       if (s >= 0 && (!active || active[s]))
