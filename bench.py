@@ -389,10 +389,12 @@ def cfg4_comparison(tau, m, stream):
     against FP64, both with Schur-complement Sternheimer solves over the 8 computed
     bands above the gap (Sec. 3.4.2) and the balanced rule, each timed once with
     CUDA events after a loose warm-up solve; true residuals from an FP64 E
-    application at tight CG tolerances."""
+    application at tight CG tolerances.  The mixed solve runs its FP32
+    projection products (occupied, extra and Kleinman-Bylander vectors) on the
+    tensor cores; the same solve with them on the CUDA cores is timed beside it."""
     import numpy as np
     import torch
-    from paper_2505_02319_gb300 import groundstate
+    from paper_2505_02319_gb300 import groundstate, ikr
     from workloads import make_system, perturbation
     s = make_system("cfg4")
     t0 = time.time()
@@ -405,19 +407,32 @@ def cfg4_comparison(tau, m, stream):
     out = {"workload": "cfg4: 20.5 bohr cell, 64 Gaussian atoms with s+p KB projectors, Ecut 20 Ha, 96^3 grid, "
                        "Gamma, 136 bands (N_occ 128), Schur-complement solves, bal, tau = 1e-8, m = 20",
            "setup_s": setup}
+
     def classes(prof):
         return {k: round(v["ms_fp32"] + v["ms_fp64"], 2) for k, v in prof.items() if v["ms_fp32"] + v["ms_fp64"] > 0}
 
-    for prec in ("mixed", "fp64"):
-        ctx.solve_response(b, tau=1e-2, m=m, strategy="bal", precision=prec)          # workspaces, shapes
-        (x, rep), t = timed(lambda: ctx.solve_response(b, tau=tau, m=m, strategy="bal", precision=prec), stream)
-        Ex, _ = ctx.apply_dielectric(x, tol=np.full(nsys, 1e-12))
-        r = rep[0]
-        out[prec] = {"time_s": t, "status": r["status"], "n_ham": r["n_ham"], "n_ham_fp64": r["n_ham_fp64"],
-                     "outer_iters": r["outer_iters"], "true_residual": float(torch.linalg.norm(b - Ex))}
+    def run(key, prec, tensor_cores):
+        ctx.set_tensor_cores(tensor_cores)
+        try:
+            ctx.solve_response(b, tau=1e-2, m=m, strategy="bal", precision=prec)      # workspaces, shapes
+            (x, rep), t = timed(lambda: ctx.solve_response(b, tau=tau, m=m, strategy="bal", precision=prec), stream)
+            Ex, _ = ctx.apply_dielectric(x, tol=np.full(nsys, 1e-12))
+            r = rep[0]
+            out[key] = {"time_s": t, "status": r["status"], "n_ham": r["n_ham"], "n_ham_fp64": r["n_ham_fp64"],
+                        "outer_iters": r["outer_iters"], "true_residual": float(torch.linalg.norm(b - Ex))}
+            if prec == "mixed":   # kernel time per class of one more solve (library CUDA events)
+                ctx.profile_start(timed=ikr.Context.KERNEL_CLASSES)
+                ctx.solve_response(b, tau=tau, m=m, strategy="bal", precision=prec)
+                out[key]["kernel_ms"] = classes(ctx.profile_read())
+        finally:
+            ctx.set_tensor_cores(False)
+
+    run("mixed", "mixed", True)
+    out["mixed"]["projections"] = "tensor cores (tcgen05, three-piece bf16 split)"
+    run("fp64", "fp64", False)
+    run("mixed_cuda_cores", "mixed", False)
     out["speedup_mixed_vs_fp64"] = out["fp64"]["time_s"] / out["mixed"]["time_s"]
-    # the same mixed solve with the FP32 projection products (occupied, extra and
-    # Kleinman-Bylander vectors) on the tensor cores
+    out["speedup_tensor_vs_cuda_cores"] = out["mixed_cuda_cores"]["time_s"] / out["mixed"]["time_s"]
     # the FP32 Q-projection y <- y - Phi (Phi^H y) of 128 vectors (all active), CUDA cores
     # against tensor cores, through ikr_project_out
     gen = torch.Generator(device="cuda").manual_seed(5)
@@ -430,23 +445,6 @@ def cfg4_comparison(tau, m, stream):
         ctx.project_out(0, y, method=method)
         proj[key] = min(timed(lambda: ctx.project_out(0, y, method=method), stream)[1] for _ in range(3)) * 1e3
     out["q_projection_128_vectors"] = proj
-    # kernel time per class of one mixed solve (library CUDA events), CUDA cores and tensor cores
-    from paper_2505_02319_gb300 import ikr
-    ctx.profile_start(timed=ikr.Context.KERNEL_CLASSES)
-    ctx.solve_response(b, tau=tau, m=m, strategy="bal", precision="mixed")
-    out["mixed"]["kernel_ms"] = classes(ctx.profile_read())
-    ctx.set_tensor_cores(True)
-    try:
-        ctx.solve_response(b, tau=1e-2, m=m, strategy="bal", precision="mixed")
-        (x, rep), t = timed(lambda: ctx.solve_response(b, tau=tau, m=m, strategy="bal", precision="mixed"), stream)
-        ctx.profile_start(timed=ikr.Context.KERNEL_CLASSES)
-        ctx.solve_response(b, tau=tau, m=m, strategy="bal", precision="mixed")
-        tc_classes = classes(ctx.profile_read())
-    finally:
-        ctx.set_tensor_cores(False)
-    Ex, _ = ctx.apply_dielectric(x, tol=np.full(nsys, 1e-12))
-    out["mixed_tensor_cores"] = {"time_s": t, "status": rep[0]["status"], "n_ham": rep[0]["n_ham"],
-                                 "true_residual": float(torch.linalg.norm(b - Ex)), "kernel_ms": tc_classes}
     ctx.destroy()
     return out
 

@@ -212,18 +212,21 @@ ikr_status ikr_set_schur(ikr_ctx* ctx, int enable);
 /* The FP32 projection products (eq. discretised_sternheimer: M = Phi^H Y, and
  * the Q-projection Y - Phi (Phi^H Y) of every FP32 CG iteration), both V_k^H Y
  * and Y - V_k C, on the 5th-generation tensor cores: tcgen05 MMAs of
- * kind::tf32 with each operand split into a TF32 high part and the remainder
- * (three products, FP32 accumulation in tensor memory); V_k^H Y split-K over
- * thread blocks with a fixed-order reduction of the chunk partials.
- * enable = 0 returns to the CUDA-core kernels.  IKR_ERR_STATE before the eigenpairs are set.  A
- * tensor-core launch whose internal wait runs out makes the calling solve
+ * kind::f16 on bf16 operands, every FP32 operand split exactly into three
+ * bf16 pieces and six of their products accumulated in FP32 in tensor memory
+ * (products as accurate as FP32 multiplications); V_k^H Y split-K over thread
+ * blocks with a fixed-order reduction of the chunk partials.  mode: 0 the
+ * CUDA-core kernels, 1 the tensor cores with 64-byte swizzled operand tiles,
+ * 2 the tensor cores with the canonical (unswizzled) operand layout.
+ * IKR_ERR_ARG for another mode; IKR_ERR_STATE before the eigenpairs are set.
+ * A tensor-core launch whose internal wait runs out makes the calling solve
  * return IKR_ERR_TIMEOUT. */
-ikr_status ikr_set_tensor_cores(ikr_ctx* ctx, int enable);
+ikr_status ikr_set_tensor_cores(ikr_ctx* ctx, int mode);
 
 /* c[s][m] = <phi_m,k, y_s> for the occupied orbitals of k-point k (the
  * coefficient product of eq. discretised_sternheimer, M = Phi_k^H Y) in FP32
- * arithmetic: method 0 on the CUDA cores, 1 on the tensor cores (as
- * ikr_set_tensor_cores).  y: DEVICE, Nb_k x nvec complex64, column-major
+ * arithmetic: method 0 on the CUDA cores, 1 and 2 on the tensor cores (as
+ * ikr_set_tensor_cores modes 1 and 2).  y: DEVICE, Nb_k x nvec complex64, column-major
  * (vector s at s * Nb_k); c: HOST, nvec x N_occ,k complex128 (row s).
  * IKR_ERR_ARG for a bad k, nvec < 1 or NULL pointers; IKR_ERR_TIMEOUT as above. */
 ikr_status ikr_projection_coefficients(ikr_ctx* ctx, int k, int nvec, const void* y, int method, double* c,
@@ -231,7 +234,7 @@ ikr_status ikr_projection_coefficients(ikr_ctx* ctx, int k, int nvec, const void
 
 /* y <- Q_k y = y - Phi_k (Phi_k^H y), the projector of eq.
  * discretised_sternheimer, in FP32 arithmetic: method 0 on the CUDA cores, 1
- * on the tensor cores.  y: DEVICE, Nb_k x nvec complex64, column-major,
+ * and 2 on the tensor cores (as ikr_set_tensor_cores modes 1 and 2).  y: DEVICE, Nb_k x nvec complex64, column-major,
  * overwritten.  Errors as ikr_projection_coefficients. */
 ikr_status ikr_project_out(ikr_ctx* ctx, int k, int nvec, void* y, int method, cudaStream_t stream);
 
@@ -242,14 +245,20 @@ ikr_status ikr_project_out(ikr_ctx* ctx, int k, int nvec, void* y, int method, c
  * call on the context:
  *   - a 4-iteration FP32 CG over all systems for each FP32 plane kernel
  *     (full-plane; compact at 4 or 5 blocks per SM) with the projection
- *     products on the CUDA cores (fused cluster update) or the tensor cores;
+ *     products on the CUDA cores (fused cluster update) or the tensor cores,
+ *     projecting on the vector set of the context's solves (with
+ *     ikr_set_schur: the occupied and the extra computed bands);
+ *   - with the CUDA cores, the same CG for each cluster size of the fused
+ *     update (16, 12, 10, 8 CTAs per k-point) that fits;
  *   - one FP64-accurate (double-float) H_k application over all systems for
  *     the padded and the swizzled plane kernel, on 48 x 48 planes.
- * The variants agree to FP32 (double-float) rounding.  out: HOST, 12 doubles:
+ * The variants agree to FP32 (double-float) rounding.  out: HOST, 16 doubles:
  * [0..5] ms per CG iteration for (CUDA cores: plane 0, 4, 5; tensor cores:
  * plane 0, 4, 5), [6] chosen FP32 plane variant (0, 4, 5), [7] tensor cores
  * chosen (0/1), [8..9] ms of the double-float application (padded, swizzled;
- * -1 when not timed), [10] swizzled chosen (0/1), [11] unused (-1).
+ * -1 when not timed), [10] swizzled chosen (0/1), [11] chosen cluster size of
+ * the fused update (0: tensor cores, no fused update), [12..15] ms per CG
+ * iteration with cluster size 16, 12, 10, 8 (-1 where it does not fit).
  * IKR_ERR_STATE before the eigenpairs are set. */
 ikr_status ikr_autotune(ikr_ctx* ctx, double* out, cudaStream_t stream);
 

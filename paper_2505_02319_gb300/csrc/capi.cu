@@ -163,11 +163,13 @@ ikr_status ikr_set_schur(ikr_ctx* c, int enable) {
   });
 }
 
-ikr_status ikr_set_tensor_cores(ikr_ctx* c, int enable) {
+ikr_status ikr_set_tensor_cores(ikr_ctx* c, int mode) {
   if (!c) return IKR_ERR_ARG;
   return guarded(c, [&] {
+    IKR_REQUIRE(mode >= 0 && mode <= 2, IKR_ERR_ARG, "mode must be 0, 1 or 2");
     IKR_REQUIRE(c->have_gs, IKR_ERR_STATE, "the ground state is not set");
-    c->tc_proj = enable != 0;
+    c->tc_proj = mode != 0;
+    if (mode != 0) c->tc_swizzle = mode == 1;
   });
 }
 
@@ -175,11 +177,11 @@ ikr_status ikr_projection_coefficients(ikr_ctx* c, int k, int nvec, const void* 
                                        cudaStream_t stream) {
   if (!c) return IKR_ERR_ARG;
   c->stream = stream;
-  const bool old = c->tc_proj;
+  const bool old = c->tc_proj, old_swz = c->tc_swizzle;
   ikr_status s = guarded(c, [&] {
     IKR_REQUIRE(c->have_gs, IKR_ERR_STATE, "the ground state is not set");
     IKR_REQUIRE(k >= 0 && k < (int)c->k.size() && nvec >= 1 && y && coef, IKR_ERR_ARG, "invalid arguments");
-    IKR_REQUIRE(method == 0 || method == 1, IKR_ERR_ARG, "method must be 0 or 1");
+    IKR_REQUIRE(method >= 0 && method <= 2, IKR_ERR_ARG, "method must be 0, 1 or 2");
     const KPoint& K = c->k[k];
     std::vector<int> kof(nvec, k), band(nvec, 0);
     SysList L;
@@ -190,7 +192,8 @@ ikr_status ikr_projection_coefficients(ikr_ctx* c, int k, int nvec, const void* 
     IKR_CUDA(cudaMemsetAsync(w.Z32.p, 0, sizeof(float2) * (size_t)nvec * ld, stream));
     IKR_CUDA(cudaMemcpy2DAsync(w.Z32.p, sizeof(float2) * ld, y, sizeof(float2) * K.nb, sizeof(float2) * K.nb, nvec,
                                cudaMemcpyDeviceToDevice, stream));
-    c->tc_proj = method == 1;
+    c->tc_proj = method != 0;
+    c->tc_swizzle = method != 2;
     double2* cf = reinterpret_cast<double2*>(w.coef.p);
     proj_coef<float>(c, L, w.Z32.p, ld, nullptr, cf);
     if (c->tc_proj) tc_check(c);
@@ -204,17 +207,18 @@ ikr_status ikr_projection_coefficients(ikr_ctx* c, int k, int nvec, const void* 
       }
   });
   c->tc_proj = old;
+  c->tc_swizzle = old_swz;
   return s;
 }
 
 ikr_status ikr_project_out(ikr_ctx* c, int k, int nvec, void* y, int method, cudaStream_t stream) {
   if (!c) return IKR_ERR_ARG;
   c->stream = stream;
-  const bool old = c->tc_proj;
+  const bool old = c->tc_proj, old_swz = c->tc_swizzle;
   ikr_status s = guarded(c, [&] {
     IKR_REQUIRE(c->have_gs, IKR_ERR_STATE, "the ground state is not set");
     IKR_REQUIRE(k >= 0 && k < (int)c->k.size() && nvec >= 1 && y, IKR_ERR_ARG, "invalid arguments");
-    IKR_REQUIRE(method == 0 || method == 1, IKR_ERR_ARG, "method must be 0 or 1");
+    IKR_REQUIRE(method >= 0 && method <= 2, IKR_ERR_ARG, "method must be 0, 1 or 2");
     const KPoint& K = c->k[k];
     std::vector<int> kof(nvec, k), band(nvec, 0);
     SysList L;
@@ -225,7 +229,8 @@ ikr_status ikr_project_out(ikr_ctx* c, int k, int nvec, void* y, int method, cud
     IKR_CUDA(cudaMemsetAsync(w.Z32.p, 0, sizeof(float2) * (size_t)nvec * ld, stream));
     IKR_CUDA(cudaMemcpy2DAsync(w.Z32.p, sizeof(float2) * ld, y, sizeof(float2) * K.nb, sizeof(float2) * K.nb, nvec,
                                cudaMemcpyDeviceToDevice, stream));
-    c->tc_proj = method == 1;
+    c->tc_proj = method != 0;
+    c->tc_swizzle = method != 2;
     double2* cf = reinterpret_cast<double2*>(w.coef.p);
     proj_coef<float>(c, L, w.Z32.p, ld, nullptr, cf);
     proj_apply<float>(c, L, cf, w.Z32.p, 1.0f, -1.0f, w.Z32.p, ld, nullptr, nullptr, nullptr);
@@ -235,6 +240,7 @@ ikr_status ikr_project_out(ikr_ctx* c, int k, int nvec, void* y, int method, cud
     IKR_CUDA(cudaStreamSynchronize(stream));
   });
   c->tc_proj = old;
+  c->tc_swizzle = old_swz;
   return s;
 }
 

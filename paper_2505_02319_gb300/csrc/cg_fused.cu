@@ -352,7 +352,8 @@ struct FusedPlan {
 FusedPlan plan_fused(ikr_ctx* c, const SysList& L, int maxcnt) {
   FusedPlan p;
   for (int v : L.kcount) p.nsmax = std::max(p.nsmax, v);
-  if (c->cgf_nsmax == p.nsmax && c->cgf_maxcnt == maxcnt) {   // planned before for this shape
+  if (c->cgf_nsmax == p.nsmax && c->cgf_maxcnt == maxcnt && c->cgf_planned_force == c->cgf_force) {
+    // planned before for this shape
     p.ok = c->cgf_ok;
     p.cs = c->cgf_cs;
     p.sl = c->cgf_sl;
@@ -362,6 +363,7 @@ FusedPlan plan_fused(ikr_ctx* c, const SysList& L, int maxcnt) {
   }
   c->cgf_nsmax = p.nsmax;
   c->cgf_maxcnt = maxcnt;
+  c->cgf_planned_force = c->cgf_force;
   c->cgf_ok = false;
   if (p.nsmax == 0 || p.nsmax > 64 || maxcnt > 64) return p;
   // IKR_CG_FUSED=0 selects the unfused sequence of kernels (read when a context plans)
@@ -376,6 +378,7 @@ FusedPlan plan_fused(ikr_ctx* c, const SysList& L, int maxcnt) {
   const int nk = (int)c->k.size();
   int best_waves = 0;
   for (int cs : {16, 12, 10, 8}) {
+    if (c->cgf_force > 0 && cs != c->cgf_force) continue;   // the autotuner's choice only
     const int sl = (c->ld + cs - 1) / cs;
     if (sl > 32 * kFU) continue;
     const int lds = sl | 1;
@@ -423,7 +426,10 @@ FusedPlan plan_fused(ikr_ctx* c, const SysList& L, int maxcnt) {
 
 }  // namespace
 
-bool cg_fused_available(ikr_ctx* c, const SysList& L) { return plan_fused(c, L, c->noccmax).ok; }
+int cg_fused_cluster(ikr_ctx* c, const SysList& L, int maxcnt) {
+  const FusedPlan p = plan_fused(c, L, maxcnt);
+  return p.ok ? p.cs : 0;
+}
 
 bool launch_cg_fused(ikr_ctx* c, const SysList& L, float2* X, float2* Rv, float2* P, const float2* W, double* sys,
                      int maxit, int* active, int* counter, int* list, const double* zpart, int nzf,
@@ -466,6 +472,10 @@ bool launch_cg_fused(ikr_ctx* c, const SysList& L, float2* X, float2* Rv, float2
   cfg.blockDim = dim3(kFT, 1, 1);
   cfg.dynamicSmemBytes = p.smem;
   cfg.stream = c->stream;
+  // the attributes belong to the kernel, not to this context: another context's plan may
+  // have set a smaller shared-memory size since this plan was made
+  if (p.cs > 8) IKR_CUDA(cudaFuncSetAttribute(k_cg_fused, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  IKR_CUDA(cudaFuncSetAttribute(k_cg_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   IKR_CUDA(cudaLaunchKernelEx(&cfg, k_cg_fused, a));

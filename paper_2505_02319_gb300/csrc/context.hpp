@@ -210,6 +210,8 @@ struct ikr_ctx {
   bool zreg_ok = false;
   // launch plan of the fused FP32 CG update (cg_fused.cu), for cgf_nsmax systems per k-point
   int cgf_nsmax = -1, cgf_maxcnt = -1, cgf_cs = 0, cgf_sl = 0, cgf_lds = 0;
+  int cgf_force = 0;            // cluster size chosen by the autotuner (0: the planner's choice)
+  int cgf_planned_force = -1;   // cgf_force of the cached plan
   size_t cgf_smem = 0;
   bool cgf_ok = false;
   ikr::FftPlan plan[3];
@@ -260,6 +262,8 @@ struct ikr_ctx {
   int batch_items = -1;
   // tensor-core projection coefficients (tc_proj.cu; ikr_set_tensor_cores)
   bool tc_proj = false;
+  bool tc_swizzle = true;       // 64-byte swizzled operand tiles (false: the canonical layout)
+  int mask_bound = 0;           // > 0: at most this many systems are active in masked FP32 projections (CG)
   ikr::DBuf<int> tc_err;
   ikr::SysList batch_list;
   ikr::DBuf<int> d_batch_map;

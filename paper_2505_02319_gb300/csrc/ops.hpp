@@ -96,6 +96,8 @@ OrbSet kb_set(ikr_ctx* c);      // the Kleinman-Bylander projectors B_k (kb.cu)
 bool launch_cg_fused(ikr_ctx* c, const SysList& L, float2* X, float2* Rv, float2* P, const float2* W, double* sys,
                      int maxit, int* active, int* counter, int* list, const double* zpart, int nzf,
                      const OrbSet* set = nullptr);
+// the cluster size the fused update would launch with for sets of up to maxcnt vectors (0: none)
+int cg_fused_cluster(ikr_ctx* c, const SysList& L, int maxcnt);
 // FP32 projections (proj32.cu)
 int proj_chunks32();
 void proj_coef32(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef,

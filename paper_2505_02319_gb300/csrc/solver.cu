@@ -141,6 +141,13 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
   int* act = w.active.p;
   const int pch = proj_chunks(c, (int)sizeof(R)), cch = cg_chunks(c);
   double2* coef = reinterpret_cast<double2*>(w.coef.p);
+  // the masked projections below see at most mask_bound active systems (the count read
+  // back after every iteration); cleared when the solve ends
+  struct BoundGuard {
+    ikr_ctx* c;
+    ~BoundGuard() { c->mask_bound = 0; }
+  } bound_guard{c};
+  c->mask_bound = n;
   // initial state: x = 0, r = b, z = Q M^-1 r, p = z
   cg_xr<R>(c, L, 0, v, sys, act, nullptr);
   proj_coef<R>(c, L, v.Z, c->ld, act, coef, zset);
@@ -184,6 +191,7 @@ CgStats cg_solve(ikr_ctx* c, const SysList& L, const C_t<R>* Bv, C_t<R>* Xv, con
     IKR_CUDA(cudaMemcpyAsync(c->h_pinned, dcount, sizeof(int), cudaMemcpyDeviceToHost, strm));
     IKR_CUDA(cudaStreamSynchronize(strm));
     c->active_hint = c->h_pinned[0];
+    c->mask_bound = std::max(c->h_pinned[0], 1);
     if (c->h_pinned[0] == 0) break;
   }
   IKR_CUDA(cudaMemcpyAsync(hs.data(), sys, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, strm));

@@ -90,7 +90,7 @@ void gmres_solve_batch(ikr_ctx* c, int nrhs, const double* b, double* x, const i
                        ikr_report* reps, bool adjoint = false);
 
 // times the interchangeable kernel variants on the context's systems and keeps the
-// fastest (tune.cu); out: 12 doubles, see ikr_autotune
+// fastest (tune.cu); out: 16 doubles, see ikr_autotune
 void autotune(ikr_ctx* c, double* out);
 
 }  // namespace ikr

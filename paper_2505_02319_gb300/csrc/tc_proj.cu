@@ -1,33 +1,54 @@
-// Tensor-core projection coefficients (5th-generation tensor cores: tcgen05.mma
-// kind::tf32, accumulators in tensor memory):
-//   C[s][m] = <v_m, y_s> = sum_G conj(V_k[m][G]) y_s[G]
+// Tensor-core projection products (5th-generation tensor cores: tcgen05.mma
+// kind::f16 with bf16 operands, accumulators in tensor memory):
+//   C[s][m] = <v_m, y_s> = sum_G conj(V_k[m][G]) y_s[G]            (k_tc_coef + k_tc_reduce)
+//   out_s   = alpha in_s + beta sum_m v_m C[s][m]                    (k_tc_apply)
 // for the systems s of each k-point and the vectors v_m of an orbital set
-// (Phi_k, or [Phi_k Psi_k] for the Schur-complement solves): the M = Phi^H Y of
-// eq. discretised_sternheimer and the Q-projection of the CG, in FP32.
+// (Phi_k, [Phi_k Psi_k] for the Schur-complement solves, or the
+// Kleinman-Bylander projectors): the M = Phi^H Y of eq.
+// discretised_sternheimer, the Q-projection of the CG and B D B^H, in FP32.
 //
 // Real form.  With y and v stored as interleaved (re, im) floats, a complex
 // inner product is two real ones over 2 Nb_k reals:
 //   Re C = <v_il, y_il>,   Im C = <v'_il, y_il>,   v' = (-Im v, Re v),
-// so D = A B^T with A = [v_0; v'_0; v_1; v'_1; ...] (2 n_k rows) and B = the
-// systems' vectors (K-major both): C[s][m] = D[2m][s] + i D[2m+1][s].  A is
-// never stored: each stage forms its rows from the FP32 orbitals in registers.
+// so C = A B^T with A = [v_0; v'_0; v_1; v'_1; ...] (2 n_k rows) and B = the
+// systems' vectors; V C has the rows (Re v, -Im v) and (Im v, Re v) of every
+// plane wave against the interleaved coefficients.  The rotated rows are
+// never stored: the kernels form them from the FP32 data in registers.
 //
-// Precision.  kind::tf32 multiplies the upper 19 bits of each float.  Each
-// operand is split on the fly x = hi + lo with hi = x with its low 13
-// mantissa bits cleared (exact) and lo = x - hi (exact), and D accumulates
-// A_hi B_hi + A_hi B_lo + A_lo B_hi: products to about 2^-20 relative, FP32
-// accumulation, as the CUDA-core kernels.  Global traffic is that of the
-// FP32 operands themselves.
+// Precision.  Every FP32 operand is split exactly into three bf16 numbers,
+//   x = b0 + b1 + b2,  b0 = RN(x), b1 = RN(x - b0), b2 = x - b0 - b1
+// (x has 24 significant bits; b0 and b1 take 8 each with round-to-nearest,
+// which leaves at most 8 for b2), and D accumulates the six products
+// a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 + a2 b0, each exact in FP32.  The
+// omitted terms are below 2^-23 of |a b|: the products are as accurate as
+// FP32 multiplications.  The leading products a0 b0 and the five corrections
+// go to two accumulators (added in the epilogue), so the long FP32 sum of a
+// chunk sees one accumulation per K step instead of six, and V^H Y sums at
+// most 512 reals per chunk in FP32 before the FP64 reduction.  (A split into
+// TF32 halves leaves 2^-20 per product, which stalls the CG at the smallest
+// tolerances of the solve.)  Global traffic is that of the FP32 operands
+// themselves.
 //
-// Tiling.  One CTA (one warpgroup) owns 128 rows of A, NT systems and a
-// split-K chunk of kTC reals; stages of kTK = 32 reals are written to shared
-// memory in the canonical no-swizzle K-major layout (8 x 16-byte core
-// matrices, 128 bytes apart along K, 8-row groups 1024 bytes apart), one
-// thread issues 4 x 3 MMAs (M = 128, N = NT, K = 8 each) and commits them to
-// an mbarrier that all threads wait on (bounded) before the next stage.  The
-// 128 x NT FP32 partial tile is read back with tcgen05.ld (warp w: lanes
-// 32w..32w+31), even/odd rows paired into (re, im), and written as per-chunk
-// partials that a second kernel adds in fixed chunk order (deterministic).
+// Pipeline.  One CTA (8 warps) owns a 128-row tile of D and NT systems; K runs
+// in stages of kTK = 32 reals through a ring of two shared-memory buffers
+// holding the three pieces of both operands, K-major, in 8-row x 64-byte atoms
+// (64-byte swizzle, or the canonical layout of 8 x 16-byte core matrices:
+// ikr_set_tensor_cores mode 1 or 2).  For stage st every thread waits (bounded)
+// for the MMAs of stage st - 2, which read the same buffer, splits its
+// registers into that buffer, issues the global loads of stage st + 2 into
+// the registers it just freed, and meets the others at one barrier; thread 0
+// then issues the stage's 2 x 6 MMAs (M = 128, N = NT, K = 16) and commits
+// them to the buffer's mbarrier.  So the MMAs of one stage run while the next
+// is filled, and every load has two stages to arrive.  The systems of the
+// tile (the k-point's active systems, compacted in order) are listed once per
+// CTA in shared memory: finished systems cost nothing, and inside the CG the
+// tile width follows the number of systems still active.  The accumulator
+// tile is read back with tcgen05.ld (warp w: lanes 32 (w mod 4) + 0..31,
+// column half w / 4), even/odd rows paired into (re, im).  V^H Y runs split-K
+// with the chunks sized for about two CTAs per SM, and a second kernel adds the
+// FP32 chunk partials in FP64 in chunk order (deterministic).
+#include <cuda_bf16.h>
+
 #include <cstdint>
 
 #include "ops.hpp"
@@ -36,34 +57,63 @@ namespace ikr {
 
 namespace {
 
-constexpr int kTM = 128;     // A rows per tile (64 vectors: re and im rows)
-constexpr int kTK = 32;      // reals of K per stage (16 plane waves)
-constexpr int kTC = 1024;    // reals of K per split-K chunk (512 plane waves)
-constexpr int kTileBytes = kTM * kTK * 4;   // one A tile (16 KB)
+constexpr int kTM = 128;                  // D rows per tile (coef: 64 vectors; apply: 64 plane waves)
+constexpr int kTK = 32;                   // reals of K per stage
+constexpr int kRowB = 2 * kTK;            // bytes of one row of one bf16 piece in a stage
+constexpr int kSBO = 8 * kRowB;           // bytes between 8-row groups
+constexpr int kAPiece = kTM * kRowB;      // one piece of the A tile (8 KB)
+constexpr int kThreads = 256;
+constexpr int kMaxChunk = 512;            // reals of V^H Y summed in FP32 before the FP64 reduction
 constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz: bound of every mbarrier wait
+
+template <int NT> struct TcLayout {
+  static constexpr int kBPiece = NT * kRowB;
+  static constexpr int kStage = 3 * kAPiece + 3 * kBPiece;      // A0 A1 A2 B0 B1 B2
+  static constexpr int kBar = 2 * kStage;                       // two mbarriers
+  static constexpr int kSlot = kBar + 16;                       // tensor-memory address
+  static constexpr int kSys = kSlot + 16;                       // [NT] systems of the tile
+  static constexpr int kWcnt = kSys + 4 * NT;                   // [8] active systems per warp (scan)
+  static constexpr int kRed = (kWcnt + 4 * 8 + 15) / 16 * 16;   // apply: [NT][2] dot partials
+  static constexpr int kCoef = kRed;
+  static constexpr int kApply = kRed + 2 * NT * 8;
+  // apply: after the MMAs the ring holds D as [NT systems][128 rows] floats
+  static_assert(NT * kTM * 4 <= 2 * kStage, "the D tile fits the ring");
+  // two accumulators of NT columns: the leading products a0 b0, and the five corrections
+  static constexpr uint32_t kCols = 2 * NT < 32 ? 32 : 2 * NT;
+};
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// byte offset of the 16-byte group c4 (reals 4 c4 .. 4 c4 + 3) of row r in a
-// kTK-wide tile: canonical K-major layout without swizzle
-__device__ __forceinline__ int core_off(int r, int c4) { return (r >> 3) * 1024 + c4 * 128 + (r & 7) * 16; }
+// byte offset of the 16-byte chunk c (reals 8 c .. 8 c + 7) of row r in one piece:
+// 64-byte swizzle (row r of its atom at 64 (r mod 8), chunk c at c xor ((r / 2) mod 4)),
+// or the canonical layout (core matrices of 8 rows x 16 bytes, 128 bytes apart along K)
+template <bool SWZ>
+__device__ __forceinline__ int chunk_off(int r, int c) {
+  return SWZ ? (r >> 3) * kSBO + (r & 7) * kRowB + ((c ^ ((r >> 1) & 3)) << 4)
+             : (r >> 3) * kSBO + c * 128 + (r & 7) * 16;
+}
 
-// shared-memory matrix descriptor: start address, leading (K) byte offset 128,
-// stride (8-row group) byte offset 1024, descriptor version 1, no swizzle
+// shared-memory matrix descriptor: start address, leading byte offset (K-adjacent core
+// matrices, 128 bytes; not used by the swizzled layout), stride byte offset 512 (8-row
+// groups), descriptor version 1, layout (4: 64-byte swizzle, 0: none)
+template <bool SWZ>
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         (1ull << 46);
+  const uint64_t lbo = SWZ ? 1 : (128 >> 4);
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | (lbo << 16) | ((uint64_t)(kSBO >> 4) << 32) | (1ull << 46) |
+         ((SWZ ? 4ull : 0ull) << 61);
+}
+// start offset of K step kk (16 bf16 = 32 bytes of every row)
+template <bool SWZ> __device__ __forceinline__ uint32_t kstep_off(int kk) { return SWZ ? 32u * kk : 256u * kk; }
+
+// instruction descriptor: D F32, A and B BF16, both K-major, N = n, M = 128
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
 }
 
-// instruction descriptor: D F32, A and B TF32, both K-major, N = n, M = 128
-__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -103,423 +153,485 @@ __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
-// 32 consecutive columns of this thread's lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+// 16 consecutive columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// ------------------------------------------------------------ bf16 split --
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);        // .x (lower address) = lo
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+// the pair (a, b) split into three bf16 pairs: a = a0 + a1 + a2, b likewise, exactly
+__device__ __forceinline__ void split2(float a, float b, uint32_t& w0, uint32_t& w1, uint32_t& w2) {
+  w0 = pack_bf16(a, b);
+  const float ra = a - bf_lo(w0), rb = b - bf_hi(w0);
+  w1 = pack_bf16(ra, rb);
+  w2 = pack_bf16(ra - bf_lo(w1), rb - bf_hi(w1));
+}
+// on a bf16 pair (lo, hi), exactly: (-hi, lo), (lo, -hi), (hi, lo)
+__device__ __forceinline__ uint32_t rot_pair(uint32_t w) { return __byte_perm(w, 0, 0x1032) ^ 0x00008000u; }
+__device__ __forceinline__ uint32_t conj_pair(uint32_t w) { return w ^ 0x80000000u; }
+__device__ __forceinline__ uint32_t swap_pair(uint32_t w) { return __byte_perm(w, 0, 0x1032); }
 
-// Work item e of a tile fill -> (row, 16-byte group c4 along K).  In the canonical
-// K-major layout the 16-byte bank slot of an element is row mod 8, so a quarter-warp
-// (8 threads, one 128-byte wavefront) must write 8 different rows: lanes 0-7 of a warp
-// take rows 8 b .. 8 b + 7 at one group, lanes 8-15 the next group, ...; every row then
-// gets 4 consecutive groups (64 contiguous bytes of its global vector) from one warp.
-__device__ __forceinline__ void tile_item(int e, int& row, int& c4) {
-  const int q = e & 31, w = e >> 5;
-  row = (q & 7) + 8 * (w >> 1);
-  c4 = (q >> 3) + 4 * (w & 1);
+// Eight reals (four interleaved complex numbers) in three bf16 pieces.
+struct Pieces {
+  uint4 p[3];
+};
+__device__ __forceinline__ Pieces split8(float4 u, float4 v) {
+  Pieces q;
+  split2(u.x, u.y, q.p[0].x, q.p[1].x, q.p[2].x);
+  split2(u.z, u.w, q.p[0].y, q.p[1].y, q.p[2].y);
+  split2(v.x, v.y, q.p[0].z, q.p[1].z, q.p[2].z);
+  split2(v.z, v.w, q.p[0].w, q.p[1].w, q.p[2].w);
+  return q;
+}
+template <typename F>
+__device__ __forceinline__ Pieces map_pairs(const Pieces& q, F f) {
+  Pieces r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) r.p[i] = make_uint4(f(q.p[i].x), f(q.p[i].y), f(q.p[i].z), f(q.p[i].w));
+  return r;
+}
+// the three pieces of row r, chunk c into the piece tiles at t, t + pb, t + 2 pb
+template <bool SWZ>
+__device__ __forceinline__ void put_pieces(unsigned char* t, int pb, int r, int c, const Pieces& q) {
+  const int off = chunk_off<SWZ>(r, c);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) *reinterpret_cast<uint4*>(t + i * pb + off) = q.p[i];
+}
+// Rows 2 p and 2 p + 1 of a row pair, written by a quarter-warp of consecutive p: the
+// lanes with p mod 8 >= 4 write row 2 p + 1 first, so that each store covers 8 different
+// row slots of the atom (in both layouts the bank slot depends on the row mod 8).
+template <bool SWZ>
+__device__ __forceinline__ void put_pair(unsigned char* t, int pb, int p, int c, const Pieces& even,
+                                         const Pieces& odd) {
+  const bool swap = (p >> 2) & 1;
+  put_pieces<SWZ>(t, pb, 2 * p + (swap ? 1 : 0), c, swap ? odd : even);
+  put_pieces<SWZ>(t, pb, 2 * p + (swap ? 0 : 1), c, swap ? even : odd);
+}
+
+// Work item e of a tile fill -> (row, chunk c).  A quarter-warp (8 threads) writes 8
+// consecutive rows at one chunk; a warp covers 8 rows x the 4 chunks of a stage (the
+// 128 contiguous bytes of each row's FP32 data).
+__device__ __forceinline__ void tile_item(int e, int& row, int& c) {
+  row = (e & 7) + 8 * (e >> 5);
+  c = (e >> 3) & 3;
+}
+
+// The systems of tile rows [s0, s0 + NT) of k-point k: the k-point's active
+// systems in order (all of them without a mask), -1 past the last.  Returns the
+// number of active systems of the k-point.  One pass of the whole block per 256
+// systems (a ballot per warp, the warps' counts through shared memory), so a
+// launch waits for one load of the flags.  Contains barriers (whole block).
+template <int NT>
+__device__ int tile_systems(int* sys_s, int* wcnt, int sk, int n, const int* __restrict__ active, int s0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = threadIdx.x; j < NT; j += blockDim.x) sys_s[j] = -1;
+  int base = 0;
+  for (int j0 = 0; j0 < n; j0 += blockDim.x) {
+    const int j = j0 + threadIdx.x;
+    const bool a = j < n && (!active || active[sk + j] != 0);
+    const unsigned m = __ballot_sync(0xffffffffu, a);
+    if (lane == 0) wcnt[warp] = __popc(m);
+    __syncthreads();
+    int before = base, total = base;
+    for (int w = 0; w < nw; ++w) {
+      before += w < warp ? wcnt[w] : 0;
+      total += wcnt[w];
+    }
+    const int idx = before + __popc(m & ((1u << lane) - 1u));
+    if (a && idx >= s0 && idx < s0 + NT) sys_s[idx - s0] = sk + j;
+    __syncthreads();                                               // wcnt is rewritten by the next pass
+    base = total;
+  }
+  __syncthreads();
+  return base;
+}
+
+// The two-buffer stage loop shared by both kernels.  fetch(R, kb) loads the
+// registers of the stage at K offset kb, store(R, buffer) splits them into a
+// buffer; the loads of stage st + 2 are issued when stage st has been stored.
+// Returns whether every wait ended in time, and in last the index of the last
+// stage whose MMAs were committed (-1 if none).
+template <int NT, bool SWZ, typename Regs, typename Fetch, typename Store>
+__device__ __forceinline__ bool stage_loop(unsigned char* sm, uint64_t* bar, uint32_t tmem, int nst, int kbase,
+                                           Fetch&& fetch, Store&& store, int& last) {
+  using Lay = TcLayout<NT>;
+  const int tid = threadIdx.x;
+  Regs R0, R1;
+  if (nst > 0) fetch(R0, kbase);
+  if (nst > 1) fetch(R1, kbase + kTK);
+  last = -1;
+  auto step = [&](Regs& r, int st) -> bool {
+    const int b = st & 1;
+    unsigned char* buf = sm + b * Lay::kStage;
+    bool mine = true;
+    if (st >= 2) mine = mbar_wait(&bar[b], ((st - 2) >> 1) & 1);   // MMAs of stage st - 2 (same buffer)
+    tc_fence_after();
+    store(r, buf);
+    if (st + 2 < nst) fetch(r, kbase + (st + 2) * kTK);
+    fence_async_smem();
+    tc_fence_before();
+    if (!__syncthreads_and(mine ? 1 : 0)) return false;            // uniform: no thread leaves alone
+    if (tid == 0) {
+      tc_fence_after();
+      constexpr uint32_t id = idesc_bf16(NT);
+      const uint32_t a = saddr(buf), bb = a + 3 * kAPiece;
+#pragma unroll
+      for (int kk = 0; kk < kTK / 16; ++kk) {
+        const uint32_t off = kstep_off<SWZ>(kk);
+        const uint64_t a0 = sdesc<SWZ>(a + off), a1 = sdesc<SWZ>(a + kAPiece + off),
+                       a2 = sdesc<SWZ>(a + 2 * kAPiece + off);
+        const uint64_t b0 = sdesc<SWZ>(bb + off), b1 = sdesc<SWZ>(bb + Lay::kBPiece + off),
+                       b2 = sdesc<SWZ>(bb + 2 * Lay::kBPiece + off);
+        const uint32_t first = (st | kk) ? 1u : 0u, corr = tmem + NT;
+        mma_bf16(tmem, a0, b0, id, first);
+        mma_bf16(corr, a0, b1, id, first);
+        mma_bf16(corr, a1, b0, id, 1u);
+        mma_bf16(corr, a0, b2, id, 1u);
+        mma_bf16(corr, a1, b1, id, 1u);
+        mma_bf16(corr, a2, b0, id, 1u);
+      }
+      mma_commit(&bar[b]);
+    }
+    last = st;
+    return true;
+  };
+  bool ok = true;
+  for (int st = 0; st < nst && ok; st += 2) {
+    ok = step(R0, st);
+    if (ok && st + 1 < nst) ok = step(R1, st + 1);
+  }
+  // the commit of the last stage completes after all earlier MMAs
+  if (ok && last >= 0) ok = __syncthreads_and(mbar_wait(&bar[last & 1], (last >> 1) & 1) ? 1 : 0) != 0;
+  return ok;
+}
+
+// common prologue: tensor-memory allocation and the two mbarriers
+template <int NT>
+__device__ __forceinline__ uint32_t tc_prologue(uint64_t* bar, uint32_t* slot) {
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(slot, TcLayout<NT>::kCols);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  return *slot;
+}
+
+// common end: on a failed wait, flag it and wait (bounded) for the MMAs in
+// flight; then free the tensor memory
+template <int NT>
+__device__ __forceinline__ void tc_end(bool ok, int last, uint64_t* bar, uint32_t tmem, int* err) {
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    if (last >= 0) mbar_wait(&bar[last & 1], (last >> 1) & 1);
+    __syncthreads();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TcLayout<NT>::kCols);
+  }
+}
+
+// columns [c0, c0 + 16) of D for this thread's lane (row quarter w mod 4): the leading
+// accumulator plus the correction accumulator NT columns further
+template <int NT>
+__device__ __forceinline__ void acc_cols16(uint32_t tmem, int c0, float* v) {
+  const uint32_t a = tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16) + (uint32_t)c0;
+  float w[16];
+  tmem_ld16(a, v);
+  tmem_ld16(a + NT, w);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] += w[j];
 }
 
 }  // namespace
 
-// Partial sums of D = A B^T over one split-K chunk: part[(s * maxcnt + m) * nch + chunk] = (Re, Im) C[s][m].
-// grid: (chunks, k-points, A-tiles x system tiles); NT systems per tile.
-template <int NT>
-__global__ void __launch_bounds__(128, 1)
-    k_tc_coef(const float2* __restrict__ phi, const int* __restrict__ set_off,
-              const int* __restrict__ set_cnt, const int* __restrict__ nb_k, const int* __restrict__ kstart,
-              const int* __restrict__ kcount, const int* __restrict__ slist, const int* __restrict__ scount,
-              const float2* __restrict__ Y, int ldy, int ld, int nmt, int nch,
-              int maxcnt, const int* __restrict__ active, double2* __restrict__ part, int* __restrict__ err) {
+// Partial sums of C = V^H Y over one split-K chunk of `chunk` reals:
+// part[(chunk index * nsys + s) * maxcnt + m] = (Re, Im) C[s][m] (the FP32 accumulator).
+// grid: (A tiles, chunks, k-points x system tiles).
+template <int NT, bool SWZ>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_tc_coef(const float2* __restrict__ phi, const int* __restrict__ set_off, const int* __restrict__ set_cnt,
+              const int* __restrict__ nb_k, const int* __restrict__ kstart, const int* __restrict__ kcount,
+              const float2* __restrict__ Y, int ldy, int ld, int nnt, int chunk, int nsys, int maxcnt,
+              const int* __restrict__ active, float2* __restrict__ part, int* __restrict__ err) {
+  using Lay = TcLayout<NT>;
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* sAhi = sm;
-  unsigned char* sAlo = sm + kTileBytes;
-  unsigned char* sBhi = sm + 2 * kTileBytes;
-  unsigned char* sBlo = sBhi + NT * kTK * 4;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sBlo + NT * kTK * 4);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
-  const int k = blockIdx.y, chunk = blockIdx.x;
-  const int tm = blockIdx.z % nmt, tn = blockIdx.z / nmt;
-  const int cnt = set_cnt[k], nb = nb_k[k], ns = scount ? scount[k] : kcount[k];
-  // system of tile row j: the k-point's j-th active system (compacted list) or its j-th system
-  auto sys_at = [&](int j) { return slist ? slist[kstart[k] + j] : kstart[k] + j; };
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + Lay::kBar);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + Lay::kSlot);
+  int* sys_s = reinterpret_cast<int*>(sm + Lay::kSys);
+  int* wcnt = reinterpret_cast<int*>(sm + Lay::kWcnt);
+  const int tm = blockIdx.x, ch = blockIdx.y, k = blockIdx.z / nnt, tn = blockIdx.z - k * nnt;
+  const int cnt = set_cnt[k], nb = nb_k[k];
   const int i0 = tm * kTM, s0 = tn * NT;
-  const int k0 = chunk * kTC, k1 = min(k0 + kTC, 2 * nb);
-  if (i0 >= 2 * cnt || s0 >= ns || k0 >= k1) return;   // uniform over the block
+  const int k0 = ch * chunk, k1 = min(k0 + chunk, 2 * nb);
+  if (i0 >= 2 * cnt || k0 >= k1) return;                         // uniform over the block
+  const int nact = tile_systems<NT>(sys_s, wcnt, kstart[k], kcount[k], active, s0);
+  if (nact <= s0) return;                                          // uniform
+  const int nrow = min(NT, nact - s0);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr uint32_t kCols = NT < 32 ? 32 : NT;
-  if (warp == 0) tmem_alloc(slot, kCols);
-  if (tid == 0) mbar_init(bar, 1);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *slot;
+  const uint32_t tmem = tc_prologue<NT>(bar, slot);
+
+  // this thread's items: A (a vector, a chunk of 8 reals) and B (a system, a chunk);
+  // with NT = 32 only the first 128 threads have a B item
+  constexpr int kBN = NT * 4 / kThreads > 0 ? NT * 4 / kThreads : 1;
+  int mo, ca;
+  tile_item(tid, mo, ca);
   const float* vbase = reinterpret_cast<const float*>(phi + ((size_t)set_off[k] + i0 / 2) * ld);
-  const size_t lda = 2 * (size_t)ld;                    // reals per orbital
-  bool ok = true;
-  uint32_t phase = 0;
-  uint32_t acc = 0;
-  // each thread's share of a stage, fetched into registers one stage ahead so that the
-  // global loads of stage kb + kTK overlap the MMAs of stage kb
-  constexpr int kAE = (kTM / 2) * (kTK / 4) / 128;   // A groups per thread (64 orbitals x 8)
-  constexpr int kBE = NT * (kTK / 4) / 128;          // B groups per thread
-  float4 ra[kAE], rb[kBE];
-  auto fetch = [&](int kb) {
+  const float* pa = i0 / 2 + mo < cnt ? vbase + (size_t)mo * 2 * ld + 8 * ca : nullptr;
+  const float* pb[kBN];
+  int rb[kBN], cb[kBN];
 #pragma unroll
-    for (int j = 0; j < kAE; ++j) {
-      int mo, c4;
-      tile_item(tid + 128 * j, mo, c4);
-      ra[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-      // orbitals past cnt are zero; the orbitals are zero past Nb_k, so a group across
-      // 2 Nb_k needs no mask
-      if (i0 / 2 + mo < cnt && kb + 4 * c4 < k1)
-        ra[j] = *reinterpret_cast<const float4*>(vbase + mo * lda + kb + 4 * c4);
-    }
-#pragma unroll
-    for (int j = 0; j < kBE; ++j) {
-      int r, c4;
-      tile_item(tid + 128 * j, r, c4);
-      const int re = kb + 4 * c4;                      // first real of the group (two plane waves)
-      rb[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (s0 + r < ns && re < k1) {
-        const int s = sys_at(s0 + r);
-        if (!active || active[s]) {
-          rb[j] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Y + (size_t)s * ldy) + re);
-          if (re + 2 >= k1) rb[j].z = rb[j].w = 0.f;    // second plane wave past Nb_k
-        }
-      }
-    }
+  for (int j = 0; j < kBN; ++j) {
+    tile_item(tid + kThreads * j, rb[j], cb[j]);
+    const int s = rb[j] < NT ? sys_s[rb[j]] : -1;
+    pb[j] = s >= 0 ? reinterpret_cast<const float*>(Y + (size_t)s * ldy) + 8 * cb[j] : nullptr;
+  }
+  struct Regs {
+    float4 a[2], b[kBN][2];
   };
-  fetch(k0);
-  for (int kb = k0; kb < k1 && ok; kb += kTK) {
-    // A tile: orbital mo gives row 2 mo = (Re, Im) and row 2 mo + 1 = (-Im, Re) of two plane
-    // waves per 16-byte group; B tile: the systems' vectors; both split into hi and lo
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto fetch = [&](Regs& R, int kb) {
 #pragma unroll
-    for (int j = 0; j < kAE; ++j) {
-      int mo, c4;
-      tile_item(tid + 128 * j, mo, c4);
-      const float4 x = ra[j];
-      const float4 y = make_float4(-x.y, x.x, -x.w, x.z);
-      const float4 xh = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
-      const float4 yh = make_float4(tf32_hi(y.x), tf32_hi(y.y), tf32_hi(y.z), tf32_hi(y.w));
-      *reinterpret_cast<float4*>(sAhi + core_off(2 * mo, c4)) = xh;
-      *reinterpret_cast<float4*>(sAlo + core_off(2 * mo, c4)) =
-          make_float4(x.x - xh.x, x.y - xh.y, x.z - xh.z, x.w - xh.w);
-      *reinterpret_cast<float4*>(sAhi + core_off(2 * mo + 1, c4)) = yh;
-      *reinterpret_cast<float4*>(sAlo + core_off(2 * mo + 1, c4)) =
-          make_float4(y.x - yh.x, y.y - yh.y, y.z - yh.z, y.w - yh.w);
+    for (int h = 0; h < 2; ++h) {   // the vectors are zero past Nb_k: a group across 2 Nb_k needs no mask
+      const int q = kb + 8 * ca + 4 * h;
+      R.a[h] = pa && q < k1 ? *reinterpret_cast<const float4*>(pa + kb + 4 * h) : z4;
     }
 #pragma unroll
-    for (int j = 0; j < kBE; ++j) {
-      int r, c4;
-      tile_item(tid + 128 * j, r, c4);
-      const float4 x = rb[j];
-      const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
-      *reinterpret_cast<float4*>(sBhi + core_off(r, c4)) = h;
-      *reinterpret_cast<float4*>(sBlo + core_off(r, c4)) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-    }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      constexpr uint32_t id = idesc_tf32(NT);
+    for (int j = 0; j < kBN; ++j)
 #pragma unroll
-      for (int kk = 0; kk < kTK / 8; ++kk) {
-        const uint32_t off = kk * 256;                  // two 16-byte groups along K per MMA
-        const uint64_t ah = sdesc(saddr(sAhi) + off), al = sdesc(saddr(sAlo) + off);
-        const uint64_t bh = sdesc(saddr(sBhi) + off), bl = sdesc(saddr(sBlo) + off);
-        mma_tf32(tmem, ah, bh, id, acc);
-        mma_tf32(tmem, ah, bl, id, 1);
-        mma_tf32(tmem, al, bh, id, 1);
-        acc = 1;
+      for (int h = 0; h < 2; ++h) {
+        const int q = kb + 8 * cb[j] + 4 * h;
+        R.b[j][h] = pb[j] && q < k1 ? *reinterpret_cast<const float4*>(pb[j] + kb + 4 * h) : z4;
+        if (q + 2 >= k1) R.b[j][h].z = R.b[j][h].w = 0.f;          // second plane wave past Nb_k
       }
-      mma_commit(bar);
-    }
-    if (kb + kTK < k1) fetch(kb + kTK);
-    // the MMAs read this stage's shared memory: wait before it is rewritten; the
-    // outcome is made uniform so that no thread leaves the loop alone
-    ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
-    phase ^= 1;
+  };
+  auto store = [&](Regs& R, unsigned char* buf) {
+    // vector mo: row 2 mo = (Re, Im), row 2 mo + 1 = (-Im, Re) of the chunk's four plane waves
+    const Pieces x = split8(R.a[0], R.a[1]);
+    put_pair<SWZ>(buf, kAPiece, mo, ca, x, map_pairs(x, rot_pair));
+#pragma unroll
+    for (int j = 0; j < kBN; ++j)
+      if (rb[j] < NT) put_pieces<SWZ>(buf + 3 * kAPiece, Lay::kBPiece, rb[j], cb[j], split8(R.b[j][0], R.b[j][1]));
+  };
+  int last;
+  const int nst = (k1 - k0 + kTK - 1) / kTK;
+  const bool ok = stage_loop<NT, SWZ, Regs>(sm, bar, tmem, nst, k0, fetch, store, last);
+  if (ok) {
     tc_fence_after();
-  }
-  if (!ok) {
-    if (lane == 0) atomicExch(err, 1);
-    // a second bounded wait for the MMAs still in flight before their tensor memory is freed
-    // (the phase was flipped after the failed wait)
-    mbar_wait(bar, phase ^ 1);
-    __syncthreads();
-  } else {
-    // epilogue: lanes 32 w .. 32 w + 31 of tensor memory are rows i0 + 32 w + lane of D
-    const int r = 32 * warp + lane;
-    const int i = i0 + r, m = i >> 1;
-    float v[32];
+    // lanes 32 q .. 32 q + 31 of tensor memory are rows i0 + 32 q + lane of C^T; the two
+    // warps of a quarter take the two halves of the columns
+    const int q = warp & 3, half = warp >> 2;
+    const int i = i0 + 32 * q + lane, m = i >> 1;
+    const bool rowok = !(lane & 1) && i < 2 * cnt;
+    float v[16];
 #pragma unroll 1
-    for (int c0 = 0; c0 < NT; c0 += 32) {
-      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+    for (int c0 = half * (NT / 2); c0 < (half + 1) * (NT / 2) && c0 < nrow; c0 += 16) {   // uniform per warp
+      acc_cols16<NT>(tmem, c0, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < 16; ++j) {
         const float im = __shfl_xor_sync(0xffffffffu, v[j], 1);
-        const int sl = s0 + c0 + j;
-        if (!(lane & 1) && i < 2 * cnt && sl < ns) {
-          const int s = sys_at(sl);
-          if (!active || active[s]) part[((size_t)s * maxcnt + m) * nch + chunk] = make_double2((double)v[j], (double)im);
-        }
+        if (rowok && c0 + j < nrow)
+          part[((size_t)ch * nsys + sys_s[c0 + j]) * maxcnt + m] = make_float2(v[j], im);
       }
     }
   }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    tmem_dealloc(tmem, kCols);
-  }
+  tc_end<NT>(ok, last, bar, tmem, err);
 }
 
 // out[s][g] = alpha in[s][g] + beta sum_m v_m[g] coef[s][m] for the plane waves of one 128-real
 // tile (64 plane waves) and NT systems; with dv, dpart[s * nparts + tile] = sum Re(conj(dv) out)
 // over the tile (the chunking of the CUDA-core apply: 64 plane waves).
-template <int NT>
-__global__ void __launch_bounds__(128, 1)
+// grid: (plane-wave tiles, k-points, system tiles).
+template <int NT, bool SWZ>
+__global__ void __launch_bounds__(kThreads, 2)
     k_tc_apply(const float2* __restrict__ phi, const int* __restrict__ set_off, const int* __restrict__ set_cnt,
                const int* __restrict__ nb_k, const int* __restrict__ kstart, const int* __restrict__ kcount,
-               const int* __restrict__ slist, const int* __restrict__ scount,
                const double2* __restrict__ coef, int maxcnt, const float2* in, float alpha, float beta,
                float2* out, int ldy, int ld, const float2* __restrict__ dv, double* __restrict__ dpart, int nparts,
                const int* __restrict__ active, int* __restrict__ err) {
+  using Lay = TcLayout<NT>;
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* sAhi = sm;
-  unsigned char* sAlo = sm + kTileBytes;
-  unsigned char* sBhi = sm + 2 * kTileBytes;
-  unsigned char* sBlo = sBhi + NT * kTK * 4;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sBlo + NT * kTK * 4);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
-  double* red = reinterpret_cast<double*>(slot + 2);              // [4 warps][NT] dot partials
-  const int k = blockIdx.y, tile = blockIdx.x, tn = blockIdx.z;
-  const int cnt = set_cnt[k], nb = nb_k[k], ns = scount ? scount[k] : kcount[k];
-  // system of tile row j: the k-point's j-th active system (compacted list) or its j-th system
-  auto sys_at = [&](int j) { return slist ? slist[kstart[k] + j] : kstart[k] + j; };
-  const int r0 = tile * kTM, s0 = tn * NT;                        // first real row (2 g + c), first system
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + Lay::kBar);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + Lay::kSlot);
+  int* sys_s = reinterpret_cast<int*>(sm + Lay::kSys);
+  int* wcnt = reinterpret_cast<int*>(sm + Lay::kWcnt);
+  double* red = reinterpret_cast<double*>(sm + Lay::kRed);       // [NT][2] dot partials
+  const int tile = blockIdx.x, k = blockIdx.y, tn = blockIdx.z;
+  const int cnt = set_cnt[k], nb = nb_k[k];
+  const int r0 = tile * kTM, s0 = tn * NT, g0 = r0 / 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (s0 >= ns) return;                                           // uniform
-  if (r0 >= 2 * nb) {                                             // tile past Nb_k: define the dot partials
+  const int nact = tile_systems<NT>(sys_s, wcnt, kstart[k], kcount[k], active, s0);
+  if (nact <= s0) return;                                          // uniform
+  const int nrow = min(NT, nact - s0);
+  if (r0 >= 2 * nb) {                                              // tile past Nb_k: define the dot partials
     if (dpart)
-      for (int j = tid; j < NT; j += 128) {
-        if (s0 + j >= ns) continue;
-        const int s = sys_at(s0 + j);
-        if (!active || active[s]) dpart[(size_t)s * nparts + tile] = 0.0;
-      }
+      for (int j = tid; j < nrow; j += kThreads) dpart[(size_t)sys_s[j] * nparts + tile] = 0.0;
     return;
   }
-  constexpr uint32_t kCols = NT < 32 ? 32 : NT;
-  if (warp == 0) tmem_alloc(slot, kCols);
-  if (tid == 0) mbar_init(bar, 1);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *slot;
-  const int g0 = r0 / 2;                                          // first plane wave of the tile
-  const float2* vk = phi + (size_t)set_off[k] * ld;
-  const int kend = 2 * cnt;
-  bool ok = true;
-  uint32_t phase = 0, acc = 0;
-  for (int kb = 0; kb < kend && ok; kb += kTK) {
-    // A tile = AT[2g + c][2m + q] from the orbitals: (c, q) = (0, 0) Re v_m[g], (0, 1) -Im,
-    // (1, 0) Im, (1, 1) Re; an item is one plane wave and one 16-byte group (orbitals 2 c4,
-    // 2 c4 + 1), written as one 16-byte store per row; consecutive threads take consecutive
-    // plane waves (coalesced loads; rows 2 g and 2 g + 1 of a quarter-warp fall 2 per bank
-    // slot); orbitals past cnt are zero (g0 + 63 < ld: the orbitals are zero past Nb_k)
-    for (int e = tid; e < (kTM / 2) * (kTK / 4); e += 128) {
-      const int gl = e & 63, c4 = e >> 6;
-      const int m0 = kb / 2 + 2 * c4;
-      const float2 z = make_float2(0.f, 0.f);
-      const float2 p0 = m0 < cnt ? vk[(size_t)m0 * ld + g0 + gl] : z;
-      const float2 p1 = m0 + 1 < cnt ? vk[(size_t)(m0 + 1) * ld + g0 + gl] : z;
-      const float4 r0 = make_float4(p0.x, -p0.y, p1.x, -p1.y), r1 = make_float4(p0.y, p0.x, p1.y, p1.x);
-      const float4 h0 = make_float4(tf32_hi(r0.x), tf32_hi(r0.y), tf32_hi(r0.z), tf32_hi(r0.w));
-      const float4 h1 = make_float4(tf32_hi(r1.x), tf32_hi(r1.y), tf32_hi(r1.z), tf32_hi(r1.w));
-      *reinterpret_cast<float4*>(sAhi + core_off(2 * gl, c4)) = h0;
-      *reinterpret_cast<float4*>(sAlo + core_off(2 * gl, c4)) =
-          make_float4(r0.x - h0.x, r0.y - h0.y, r0.z - h0.z, r0.w - h0.w);
-      *reinterpret_cast<float4*>(sAhi + core_off(2 * gl + 1, c4)) = h1;
-      *reinterpret_cast<float4*>(sAlo + core_off(2 * gl + 1, c4)) =
-          make_float4(r1.x - h1.x, r1.y - h1.y, r1.z - h1.z, r1.w - h1.w);
-    }
-    for (int e = tid; e < NT * (kTK / 4); e += 128) {
-      int r, c4;
-      tile_item(e, r, c4);
-      float x[4] = {0.f, 0.f, 0.f, 0.f};
-      const int s = s0 + r < ns ? sys_at(s0 + r) : -1;
-      if (s >= 0 && (!active || active[s]))
+  const uint32_t tmem = tc_prologue<NT>(bar, slot);
+
+  // A item: plane wave gl of the tile and chunk ca (vectors 4 ca .. 4 ca + 3 of the stage);
+  // consecutive threads take consecutive plane waves (coalesced loads).  B item: a system
+  // and a chunk (its coefficients of the same four vectors).
+  constexpr int kBN = NT * 4 / kThreads > 0 ? NT * 4 / kThreads : 1;
+  const float2* vk = phi + (size_t)set_off[k] * ld + g0;          // g0 + 63 < ld: ld is a multiple of 64
+  const int gla = tid & 63, ca = tid >> 6;
+  const double2* pc[kBN];
+  int rb[kBN], cb[kBN];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int i = kb + 4 * c4 + 2 * q;                      // real index 2 m (+1 below)
-          if (i < kend) {
-            const double2 cc = coef[(size_t)s * maxcnt + (i >> 1)];
-            x[2 * q] = (float)cc.x;
-            x[2 * q + 1] = (float)cc.y;
-          }
-        }
-      const float4 h = make_float4(tf32_hi(x[0]), tf32_hi(x[1]), tf32_hi(x[2]), tf32_hi(x[3]));
-      *reinterpret_cast<float4*>(sBhi + core_off(r, c4)) = h;
-      *reinterpret_cast<float4*>(sBlo + core_off(r, c4)) =
-          make_float4(x[0] - h.x, x[1] - h.y, x[2] - h.z, x[3] - h.w);
-    }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      constexpr uint32_t id = idesc_tf32(NT);
-#pragma unroll
-      for (int kk = 0; kk < kTK / 8; ++kk) {
-        const uint32_t off = kk * 256;
-        const uint64_t ah = sdesc(saddr(sAhi) + off), al = sdesc(saddr(sAlo) + off);
-        const uint64_t bh = sdesc(saddr(sBhi) + off), bl = sdesc(saddr(sBlo) + off);
-        mma_tf32(tmem, ah, bh, id, acc);
-        mma_tf32(tmem, ah, bl, id, 1);
-        mma_tf32(tmem, al, bh, id, 1);
-        acc = 1;
-      }
-      mma_commit(bar);
-    }
-    ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
-    phase ^= 1;
-    tc_fence_after();
+  for (int j = 0; j < kBN; ++j) {
+    tile_item(tid + kThreads * j, rb[j], cb[j]);
+    const int s = rb[j] < NT ? sys_s[rb[j]] : -1;
+    pc[j] = s >= 0 ? coef + (size_t)s * maxcnt + 4 * cb[j] : nullptr;
   }
-  if (!ok) {
-    if (lane == 0) atomicExch(err, 1);
-    // a second bounded wait for the MMAs still in flight before their tensor memory is freed
-    // (the phase was flipped after the failed wait)
-    mbar_wait(bar, phase ^ 1);
-    __syncthreads();
-  } else {
-    const int row = r0 + 32 * warp + lane;                         // 2 g + c
-    const int g = row >> 1;
-    float v[32];
-#pragma unroll 1
-    for (int c0 = 0; c0 < NT; c0 += 32) {
-      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+  struct Regs {
+    float2 a[4];
+    double2 b[kBN][4];
+  };
+  const float2 z2 = make_float2(0.f, 0.f);
+  const double2 zd = make_double2(0.0, 0.0);
+  auto fetch = [&](Regs& R, int kb) {
+    const int mb = kb / 2;                                         // first vector of the stage
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float im = __shfl_xor_sync(0xffffffffu, v[j], 1);
-        const int sl = s0 + c0 + j;
-        const int s = sl < ns ? sys_at(sl) : -1;
-        const bool on = !(lane & 1) && g < nb && s >= 0 && (!active || active[s]);
-        double d = 0.0;
-        if (on) {
-          const size_t o = (size_t)s * ldy + g;
-          float2 y = make_float2(beta * v[j], beta * im);
-          if (alpha != 0.f) {
-            const float2 xi = in[o];
-            y.x += alpha * xi.x;
-            y.y += alpha * xi.y;
-          }
-          out[o] = y;
-          if (dv) {
-            const float2 w = dv[o];
-            d = (double)w.x * y.x + (double)w.y * y.y;
-          }
+    for (int u = 0; u < 4; ++u) {
+      const int m = mb + 4 * ca + u;
+      R.a[u] = m < cnt ? vk[(size_t)m * ld + gla] : z2;
+    }
+#pragma unroll
+    for (int j = 0; j < kBN; ++j)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int m = mb + 4 * cb[j] + u;
+        R.b[j][u] = pc[j] && m < cnt ? pc[j][mb + u] : zd;
+      }
+  };
+  auto store = [&](Regs& R, unsigned char* buf) {
+    // plane wave gl: row 2 gl = (Re v, -Im v), row 2 gl + 1 = (Im v, Re v) of the chunk's four vectors
+    const Pieces x = split8(make_float4(R.a[0].x, R.a[0].y, R.a[1].x, R.a[1].y),
+                            make_float4(R.a[2].x, R.a[2].y, R.a[3].x, R.a[3].y));
+    put_pair<SWZ>(buf, kAPiece, gla, ca, map_pairs(x, conj_pair), map_pairs(x, swap_pair));
+#pragma unroll
+    for (int j = 0; j < kBN; ++j) {
+      if (rb[j] >= NT) continue;
+      const double2* c = R.b[j];
+      put_pieces<SWZ>(buf + 3 * kAPiece, Lay::kBPiece, rb[j], cb[j],
+                      split8(make_float4((float)c[0].x, (float)c[0].y, (float)c[1].x, (float)c[1].y),
+                             make_float4((float)c[2].x, (float)c[2].y, (float)c[3].x, (float)c[3].y)));
+    }
+  };
+  int last;
+  const int nst = (2 * cnt + kTK - 1) / kTK;
+  const bool ok = stage_loop<NT, SWZ, Regs>(sm, bar, tmem, nst, 0, fetch, store, last);
+  if (ok) {
+    tc_fence_after();
+    // D through shared memory (the ring is free now): Ds[j][r] for system column j and
+    // tile row r = 2 g + c, so that every thread then takes whole plane waves of one system
+    float* Ds = reinterpret_cast<float*>(sm);
+    {
+      const int q = warp & 3, half = warp >> 2;
+      const int r = 32 * q + lane;
+      float v[16];
+#pragma unroll 1
+      for (int c0 = half * (NT / 2); c0 < (half + 1) * (NT / 2) && c0 < nrow; c0 += 16) {   // uniform per warp
+        if (nst > 0) {
+          acc_cols16<NT>(tmem, c0, v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = 0.f;                 // an empty set: V C = 0
         }
-        if (dpart) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) Ds[(c0 + j) * kTM + r] = v[j];
+      }
+    }
+    __syncthreads();
+    // thread t: plane wave g0 + (t mod 64) of the systems t / 64, t / 64 + 4, ...; the loads of
+    // 8 systems first (each element is read and written by this thread only)
+    const int gl = tid & 63, g = g0 + gl, j0 = tid >> 6;
+    const bool gok = g < nb;
+    const float2 z2 = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int jb = j0; jb < NT; jb += 32) {
+      float2 xin[8], w[8];
+      size_t o[8];
+      bool on[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = jb + 4 * u;
+        const int sj = j < nrow ? sys_s[j] : -1;
+        on[u] = gok && sj >= 0;
+        o[u] = on[u] ? (size_t)sj * ldy + g : 0;
+        xin[u] = on[u] && alpha != 0.f ? in[o[u]] : z2;
+        w[u] = on[u] && dv ? dv[o[u]] : z2;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = jb + 4 * u;
+        const float2 dd = j < NT ? *reinterpret_cast<const float2*>(Ds + j * kTM + 2 * gl) : z2;
+        float2 y = make_float2(beta * dd.x, beta * dd.y);
+        if (alpha != 0.f) {
+          y.x += alpha * xin[u].x;
+          y.y += alpha * xin[u].y;
+        }
+        double d = 0.0;
+        if (on[u]) {
+          out[o[u]] = y;
+          d = (double)w[u].x * y.x + (double)w[u].y * y.y;
+        }
+        if (dpart) {                                               // the 64 plane waves of system j: 2 warps
           d = warp_sum(d);
-          if (lane == 0) red[warp * NT + c0 + j] = d;
+          if (lane == 0 && j < NT) red[2 * j + ((tid >> 5) & 1)] = d;
         }
       }
     }
     if (dpart) {
       __syncthreads();
-      for (int j = tid; j < NT; j += 128) {
-        if (s0 + j >= ns) continue;
-        const int s = sys_at(s0 + j);
-        if (!active || active[s])
-          dpart[(size_t)s * nparts + tile] = ((red[j] + red[NT + j]) + red[2 * NT + j]) + red[3 * NT + j];
-      }
+      for (int j = tid; j < nrow; j += kThreads) dpart[(size_t)sys_s[j] * nparts + tile] = red[2 * j] + red[2 * j + 1];
     }
   }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    tmem_dealloc(tmem, kCols);
-  }
+  tc_end<NT>(ok, last, bar, tmem, err);
 }
 
-// coef[s][m] = sum of the chunk partials in chunk order: a warp per coefficient
-__global__ void k_tc_reduce(const double2* __restrict__ part, int nsys, int maxcnt, int nch,
+// coef[s][m] = sum of the chunk partials in chunk order: a thread per coefficient
+__global__ void k_tc_reduce(const float2* __restrict__ part, int nsys, int maxcnt, int chunk,
                             const int* __restrict__ sys_k, const int* __restrict__ set_cnt,
                             const int* __restrict__ nb_k, const int* __restrict__ active, double2* __restrict__ coef) {
-  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= (long long)nsys * maxcnt) return;
-  const int s = (int)(w / maxcnt), m = (int)(w - (long long)s * maxcnt);
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nsys * maxcnt) return;
+  const int s = (int)(t / maxcnt), m = (int)(t - (long long)s * maxcnt);
   if (active && !active[s]) return;
   const int k = sys_k[s];
   if (m >= set_cnt[k]) return;
-  const int nc = (2 * nb_k[k] + kTC - 1) / kTC;
-  const double2* p = part + ((size_t)s * maxcnt + m) * nch;
+  const int nc = (2 * nb_k[k] + chunk - 1) / chunk;
   double ax = 0.0, ay = 0.0;
-  for (int cc = lane; cc < nc; cc += 32) {
-    const double2 v = p[cc];
-    ax += v.x;
-    ay += v.y;
+  for (int c = 0; c < nc; ++c) {
+    const float2 v = part[((size_t)c * nsys + s) * maxcnt + m];
+    ax += (double)v.x;
+    ay += (double)v.y;
   }
-  ax = warp_sum(ax);
-  ay = warp_sum(ay);
-  if (lane == 0) coef[w] = make_double2(ax, ay);
-}
-
-// The active systems of every k-point, in order, at the k-point's offset kstart[k]
-// (slist), and their number (scount): the tensor-core kernels tile over these, so
-// systems whose CG has finished cost nothing.  One warp per k-point: ballot and
-// population count over chunks of 32 systems.
-__global__ void k_tc_compact(const int* __restrict__ active, const int* __restrict__ kstart,
-                             const int* __restrict__ kcount, int nk, int* __restrict__ slist,
-                             int* __restrict__ scount) {
-  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (k >= nk) return;
-  const int s0 = kstart[k], n = kcount[k];
-  int pos = 0;
-  for (int j0 = 0; j0 < n; j0 += 32) {
-    const int j = j0 + lane;
-    const bool a = j < n && active[s0 + j] != 0;
-    const unsigned m = __ballot_sync(0xffffffffu, a);
-    if (a) slist[s0 + pos + __popc(m & ((1u << lane) - 1u))] = s0 + j;
-    pos += __popc(m);
-  }
-  if (lane == 0) scount[k] = pos;
+  coef[t] = make_double2(ax, ay);
 }
 
 // ----------------------------------------------------------------- host --
-
-namespace {
-// compacted active lists for a masked launch (nullptr, nullptr without a mask)
-void tc_active_lists(ikr_ctx* c, const SysList& L, const int* active, const int** slist, const int** scount) {
-  *slist = nullptr;
-  *scount = nullptr;
-  if (!active || L.n == 0) return;
-  const int nk = (int)c->k.size();
-  c->ws.tc_list.reserve(L.n);
-  c->ws.tc_cnt.reserve(nk);
-  k_tc_compact<<<(nk + 3) / 4, 128, 0, c->stream>>>(active, L.d_kstart.p, L.d_kcount.p, nk, c->ws.tc_list.p,
-                                                     c->ws.tc_cnt.p);
-  IKR_CUDA(cudaGetLastError());
-  *slist = c->ws.tc_list.p;
-  *scount = c->ws.tc_cnt.p;
-}
-}  // namespace
 
 // the error flag of the tensor-core kernels: set by any launch whose wait ran out,
 // cleared only when it is created and by tc_check, so no later launch hides it
@@ -533,60 +645,110 @@ bool tc_proj_ok(ikr_ctx* c, const OrbSet& set) {
   return c->tc_proj && set.maxcnt >= 1 && (c->ld % 2) == 0;
 }
 
+namespace {
+
+// system tile width: the most systems of one k-point a launch can find active
+int tile_nt(int n) { return n <= 32 ? 32 : (n <= 64 ? 64 : 128); }
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  IKR_CUDA(cudaGetDevice(&dev));
+  IKR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  return std::max(sms, 1);
+}
+
+// the kernel's shared memory, with the whole carveout for shared memory (two or three
+// CTAs per SM, the L1 cache is not used by these kernels' operand traffic)
+template <typename K>
+void smem_attrs(K kern, size_t smem) {
+  IKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  IKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared));
+}
+
+// the most systems of one k-point that a launch can find active: all of them without
+// a mask, else also at most the bound the CG keeps (its count of active systems)
+int active_bound(ikr_ctx* c, const SysList& L, const int* active) {
+  int maxns = 0;
+  for (int v : L.kcount) maxns = std::max(maxns, v);
+  if (active && c->mask_bound > 0) maxns = std::min(maxns, c->mask_bound);
+  return maxns;
+}
+
+}  // namespace
+
 void proj_coef_tc(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const int* active, double2* coef,
                   const OrbSet& set) {
   IKR_REQUIRE(ldy % 2 == 0, IKR_ERR_ARG, "tensor-core projections need an even vector stride");
-  int maxns = 0, maxnb = 0;
-  for (int v : L.kcount) maxns = std::max(maxns, v);
+  int maxnb = 0;
   for (auto& K : c->k) maxnb = std::max(maxnb, K.nb);
-  const int nch = (2 * maxnb + kTC - 1) / kTC;
+  const int maxns = active_bound(c, L, active);
+  if (maxns == 0 || L.n == 0) return;
+  const int nk = (int)c->k.size();
   const int nmt = (2 * set.maxcnt + kTM - 1) / kTM;
-  const int nt = maxns <= 32 ? 32 : (maxns <= 64 ? 64 : 128);
+  const int nt = tile_nt(maxns);
   const int nnt = (maxns + nt - 1) / nt;
-  c->ws.cpart.reserve((size_t)nch * L.n * set.maxcnt * 2);
-  double2* part = reinterpret_cast<double2*>(c->ws.cpart.p);
   tc_flag_ready(c);
-  dim3 grid(nch, (unsigned)c->k.size(), (unsigned)(nmt * std::max(nnt, 1)));
-  const size_t smem = 2 * kTileBytes + 2 * (size_t)nt * kTK * 4 + 64;
-  const int *slist, *scount;
-  tc_active_lists(c, L, active, &slist, &scount);
-  auto launch = [&](auto kern) {
-    IKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, 128, smem, c->stream>>>(set.phi32, set.off, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p, slist,
-                                         scount, Y, ldy, c->ld, nmt, nch, set.maxcnt, active, part, c->tc_err.p);
+  auto launch = [&](auto kern, size_t smem) {
+    smem_attrs(kern, smem);
+    // split-K: chunks (multiples of a stage) of at most kMaxChunk reals (the length of the
+    // FP32 sums), and at least enough of them for two CTAs per SM
+    const int target = 2 * sm_count();
+    const int want = std::max((2 * maxnb + kMaxChunk - 1) / kMaxChunk, target / std::max(1, nk * nmt * nnt));
+    const int per = (2 * maxnb + want - 1) / want;
+    const int chunk = std::max(kTK, (per + kTK - 1) / kTK * kTK);
+    const int nch = (2 * maxnb + chunk - 1) / chunk;
+    c->ws.cpart.reserve((size_t)nch * L.n * set.maxcnt);            // doubles: room for float2 partials
+    float2* part = reinterpret_cast<float2*>(c->ws.cpart.p);
+    dim3 grid((unsigned)nmt, (unsigned)nch, (unsigned)(nk * nnt));
+    kern<<<grid, kThreads, smem, c->stream>>>(set.phi32, set.off, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p,
+                                              Y, ldy, c->ld, nnt, chunk, L.n, set.maxcnt, active, part, c->tc_err.p);
+    IKR_CUDA(cudaGetLastError());
+    const long long threads = (long long)L.n * set.maxcnt;
+    k_tc_reduce<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(part, L.n, set.maxcnt, chunk, L.d_k.p,
+                                                                           set.cnt, c->d_nb.p, active, coef);
+    IKR_CUDA(cudaGetLastError());
   };
-  if (nt == 32) launch(k_tc_coef<32>);
-  else if (nt == 64) launch(k_tc_coef<64>);
-  else launch(k_tc_coef<128>);
-  IKR_CUDA(cudaGetLastError());
-  const long long threads = 32LL * L.n * set.maxcnt;
-  k_tc_reduce<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(part, L.n, set.maxcnt, nch, L.d_k.p,
-                                                                         set.cnt, c->d_nb.p, active, coef);
-  IKR_CUDA(cudaGetLastError());
+  const bool swz = c->tc_swizzle;
+  if (nt == 32) {
+    if (swz) launch(k_tc_coef<32, true>, TcLayout<32>::kCoef);
+    else launch(k_tc_coef<32, false>, TcLayout<32>::kCoef);
+  } else if (nt == 64) {
+    if (swz) launch(k_tc_coef<64, true>, TcLayout<64>::kCoef);
+    else launch(k_tc_coef<64, false>, TcLayout<64>::kCoef);
+  } else {
+    if (swz) launch(k_tc_coef<128, true>, TcLayout<128>::kCoef);
+    else launch(k_tc_coef<128, false>, TcLayout<128>::kCoef);
+  }
 }
 
 void proj_apply_tc(ikr_ctx* c, const SysList& L, const double2* coef, const float2* in, float alpha, float beta,
                    float2* out, int ldy, const float2* dv, double* dpart, const int* active, const OrbSet& set) {
-  int maxns = 0;
-  for (int v : L.kcount) maxns = std::max(maxns, v);
+  const int maxns = active_bound(c, L, active);
+  if (maxns == 0 || L.n == 0) return;
   const int nparts = (c->ld + 63) / 64;                           // 64 plane waves per tile and dot partial
-  const int nt = maxns <= 32 ? 32 : (maxns <= 64 ? 64 : 128);
-  const int nnt = std::max(1, (maxns + nt - 1) / nt);
+  const int nt = tile_nt(maxns);
+  const int nnt = (maxns + nt - 1) / nt;
   tc_flag_ready(c);
-  dim3 grid(nparts, (unsigned)c->k.size(), (unsigned)nnt);
-  const size_t smem = 2 * kTileBytes + 2 * (size_t)nt * kTK * 4 + 16 + 32 * (size_t)nt;
-  const int *slist, *scount;
-  tc_active_lists(c, L, active, &slist, &scount);
-  auto launch = [&](auto kern) {
-    IKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, 128, smem, c->stream>>>(set.phi32, set.off, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p, slist,
-                                         scount, coef, set.maxcnt, in, alpha, beta, out, ldy, c->ld, dv, dpart, nparts,
-                                         active, c->tc_err.p);
+  dim3 grid((unsigned)nparts, (unsigned)c->k.size(), (unsigned)nnt);
+  auto launch = [&](auto kern, size_t smem) {
+    smem_attrs(kern, smem);
+    kern<<<grid, kThreads, smem, c->stream>>>(set.phi32, set.off, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p,
+                                              coef, set.maxcnt, in, alpha, beta, out, ldy, c->ld, dv, dpart, nparts,
+                                              active, c->tc_err.p);
+    IKR_CUDA(cudaGetLastError());
   };
-  if (nt == 32) launch(k_tc_apply<32>);
-  else if (nt == 64) launch(k_tc_apply<64>);
-  else launch(k_tc_apply<128>);
-  IKR_CUDA(cudaGetLastError());
+  const bool swz = c->tc_swizzle;
+  if (nt == 32) {
+    if (swz) launch(k_tc_apply<32, true>, TcLayout<32>::kApply);
+    else launch(k_tc_apply<32, false>, TcLayout<32>::kApply);
+  } else if (nt == 64) {
+    if (swz) launch(k_tc_apply<64, true>, TcLayout<64>::kApply);
+    else launch(k_tc_apply<64, false>, TcLayout<64>::kApply);
+  } else {
+    if (swz) launch(k_tc_apply<128, true>, TcLayout<128>::kApply);
+    else launch(k_tc_apply<128, false>, TcLayout<128>::kApply);
+  }
 }
 
 void tc_check(ikr_ctx* c) {

@@ -10,7 +10,11 @@
 //     compact k_plane_rc bounded to 4 or 5 blocks per SM) and the FP32
 //     projection products (CUDA cores with the fused cluster update, or tcgen05
 //     tensor cores with the unfused update): a few iterations of the batched
-//     CG over all occupied systems, from a fixed right-hand side;
+//     CG over all occupied systems, from a fixed right-hand side, projecting on
+//     the vector set of the context's solves (Phi_k, or [Phi_k Psi_k] in the
+//     Schur-complement form);
+//   - with the CUDA cores, the cluster size of the fused update (16, 12, 10 or 8
+//     CTAs per k-point: how many SMs work against how much each CTA holds);
 //   - the FP64-accurate (double-float) H_k application for the padded and the
 //     swizzled plane kernel, where the grid has both (48 x 48 planes).
 // Each candidate runs once untimed (allocations, attributes) and then twice
@@ -56,7 +60,7 @@ void autotune(ikr_ctx* c, double* out) {
   IKR_REQUIRE(c->have_gs, IKR_ERR_STATE, "the ground state is not set");
   const SysList& L = c->occ;
   const int n = L.n;
-  for (int i = 0; i < 12; ++i) out[i] = -1.0;
+  for (int i = 0; i < 16; ++i) out[i] = -1.0;
   if (n == 0) return;
   ensure_workspace(c, n);
   Workspace& w = c->ws;
@@ -69,7 +73,8 @@ void autotune(ikr_ctx* c, double* out) {
     kappa[s] = c->h_kappa_occ[s];
   }
   constexpr int kIters = 4;
-  const int old_rc = c->plane_rc;
+  const OrbSet set = c->schur ? schur_set(c) : occ_set(c);
+  const int old_rc = c->plane_rc, old_force = c->cgf_force;
   const bool old_tc = c->tc_proj, old_sw = c->plane_sw;
   const int rcs[3] = {0, 4, 5};
   double best = 1e300;
@@ -80,7 +85,7 @@ void autotune(ikr_ctx* c, double* out) {
       for (int r = 0; r < 3; ++r) {
         c->plane_rc = rcs[r];
         c->tc_proj = tc != 0;
-        const double ms = best_ms(st, [&] { cg_solve<float>(c, L, w.B32.p, w.X32.p, shift, kappa, tol, kIters); });
+        const double ms = best_ms(st, [&] { cg_solve<float>(c, L, w.B32.p, w.X32.p, shift, kappa, tol, kIters, &set); });
         out[3 * tc + r] = ms / kIters;
         if (ms < best) {
           best = ms;
@@ -92,6 +97,25 @@ void autotune(ikr_ctx* c, double* out) {
     c->tc_proj = best_tc;
     out[6] = best_rc;
     out[7] = best_tc ? 1.0 : 0.0;
+    // the cluster size of the fused CG update
+    out[11] = 0.0;
+    if (!best_tc) {
+      const int sizes[4] = {16, 12, 10, 8};
+      double bcs = 1e300;
+      int best_cs = 0;
+      for (int i = 0; i < 4; ++i) {
+        c->cgf_force = sizes[i];
+        if (cg_fused_cluster(c, L, set.maxcnt) != sizes[i]) continue;
+        const double ms = best_ms(st, [&] { cg_solve<float>(c, L, w.B32.p, w.X32.p, shift, kappa, tol, kIters, &set); });
+        out[12 + i] = ms / kIters;
+        if (ms < bcs) {
+          bcs = ms;
+          best_cs = sizes[i];
+        }
+      }
+      c->cgf_force = best_cs;
+      out[11] = best_cs;
+    }
     // the double-float H_k application (z-passes in FP64, plane pass in double-float)
     if (c->N[0] == 48 && c->N[1] == 48) {
       const bool old_em = c->emulate_fp64;
@@ -116,6 +140,7 @@ void autotune(ikr_ctx* c, double* out) {
     c->plane_rc = old_rc;
     c->tc_proj = old_tc;
     c->plane_sw = old_sw;
+    c->cgf_force = old_force;
     throw;
   }
 }

@@ -225,22 +225,25 @@ class Context:
     def autotune(self):
         """Time the interchangeable kernel variants on this context's systems and
         keep the fastest (ikr_autotune); returns the timings and the choice."""
-        out = (ct.c_double * 12)()
+        out = (ct.c_double * 16)()
         self._check(_LIB.ikr_autotune(self._h, out, _stream()))
         v = list(out)
         return {"cg_iter_ms_cuda_cores": {"plane_full": v[0], "plane_compact4": v[1], "plane_compact5": v[2]},
                 "cg_iter_ms_tensor_cores": {"plane_full": v[3], "plane_compact4": v[4], "plane_compact5": v[5]},
                 "plane_rc": int(v[6]), "tensor_cores": bool(v[7]),
-                "df64_apply_ms": {"padded": v[8], "swizzled": v[9]}, "plane_sw": bool(v[10])}
+                "df64_apply_ms": {"padded": v[8], "swizzled": v[9]}, "plane_sw": bool(v[10]),
+                "cg_fused_cluster": int(v[11]),
+                "cg_iter_ms_cluster": {"16": v[12], "12": v[13], "10": v[14], "8": v[15]}}
 
-    def set_tensor_cores(self, enable=True):
-        """FP32 projection coefficients on the tensor cores (ikr_set_tensor_cores)."""
-        self._check(_LIB.ikr_set_tensor_cores(self._h, 1 if enable else 0))
+    def set_tensor_cores(self, enable=True, swizzle=True):
+        """FP32 projection products on the tensor cores (ikr_set_tensor_cores):
+        swizzle=False selects the canonical operand layout."""
+        self._check(_LIB.ikr_set_tensor_cores(self._h, (1 if swizzle else 2) if enable else 0))
 
     def projection_coefficients(self, k, y, method=0):
         """<phi_m, y_s> for the occupied orbitals of k-point k, FP32 arithmetic:
         y a (nvec, Nb_k) complex64 CUDA tensor; method 0 CUDA cores, 1 tensor
-        cores.  Returns a (nvec, N_occ,k) complex128 numpy array."""
+        cores (swizzled operand tiles), 2 tensor cores (canonical layout).  Returns a (nvec, N_occ,k) complex128 numpy array."""
         yy = y.reshape(-1, y.shape[-1]).contiguous()
         nvec = yy.shape[0]
         nocc = int(self.groundstate_info(self.nbands, self.ngrid)["nocc"][k])
@@ -251,7 +254,7 @@ class Context:
 
     def project_out(self, k, y, method=0):
         """Q_k y = y - Phi_k (Phi_k^H y) for a (nvec, Nb_k) complex64 CUDA tensor
-        (in place; returned); method 0 CUDA cores, 1 tensor cores."""
+        (in place; returned); method as projection_coefficients."""
         self._check(_LIB.ikr_project_out(self._h, int(k), int(y.reshape(-1, y.shape[-1]).shape[0]), _dptr(y),
                                          int(method), _stream()))
         return y

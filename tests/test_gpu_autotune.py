@@ -1,7 +1,7 @@
 """The autotuner (ikr_autotune): it times the interchangeable kernel variants
-(FP32 plane kernel x projection path in a few CG iterations; the padded and
-the swizzled double-float plane pass) on the context's own systems and keeps
-the fastest.  Checks: every candidate was timed, the choice is the fastest
+(FP32 plane kernel x projection path in a few CG iterations; the cluster size
+of the fused CG update; the padded and the swizzled double-float plane pass)
+on the context's own systems and keeps the fastest.  Checks: every candidate was timed, the choice is the fastest
 one, and a mixed-precision solve after tuning still matches the oracle's E to
 tau (the variants agree to rounding)."""
 import numpy as np
@@ -21,6 +21,12 @@ def test_autotune_picks_the_fastest_variant(name):
           for rc, v in zip((0, 4, 5), (r[key]["plane_full"], r[key]["plane_compact4"], r[key]["plane_compact5"]))}
     assert all(v > 0 for v in cg.values())
     assert cg[(r["tensor_cores"], r["plane_rc"])] == min(cg.values())
+    cl = {int(k): v for k, v in r["cg_iter_ms_cluster"].items() if v > 0}
+    if r["tensor_cores"] or not cl:   # no fused update (tensor cores, or no cluster size fits)
+        assert r["cg_fused_cluster"] == 0
+    else:
+        assert cl and r["cg_fused_cluster"] in cl
+        assert cl[r["cg_fused_cluster"]] == min(cl.values())
     if name == "cfg2":
         d = r["df64_apply_ms"]
         assert d["padded"] > 0 and d["swizzled"] > 0
