@@ -265,6 +265,7 @@ struct ikr_ctx {
   bool tc_swizzle = true;       // 64-byte swizzled operand tiles (false: the canonical layout)
   int mask_bound = 0;           // > 0: at most this many systems are active in masked FP32 projections (CG)
   ikr::DBuf<int> tc_err;
+  ikr::DBuf<float2> tc_coef32;  // FP32 copy of the coefficients of a tensor-core V C product
   ikr::SysList batch_list;
   ikr::DBuf<int> d_batch_map;
   int rmax = 0, xmax = 0;

@@ -264,22 +264,23 @@ __device__ int tile_systems(int* sys_s, int* wcnt, int sk, int n, const int* __r
 // The two-buffer stage loop shared by both kernels.  fetch(R, kb) loads the
 // registers of the stage at K offset kb, store(R, buffer) splits them into a
 // buffer; the loads of stage st + 2 are issued when stage st has been stored.
-// Returns whether every wait ended in time, and in last the index of the last
-// stage whose MMAs were committed (-1 if none).
+// Stages are numbered globally from gbase on (a CTA that runs several tiles
+// continues the numbering, so that buffers and mbarrier phases stay in step);
+// last holds the global index of the last stage whose MMAs were committed (-1
+// if none) and is updated.  Returns whether every wait ended in time.
 template <int NT, bool SWZ, typename Regs, typename Fetch, typename Store>
 __device__ __forceinline__ bool stage_loop(unsigned char* sm, uint64_t* bar, uint32_t tmem, int nst, int kbase,
-                                           Fetch&& fetch, Store&& store, int& last) {
+                                           int gbase, Fetch&& fetch, Store&& store, int& last) {
   using Lay = TcLayout<NT>;
   const int tid = threadIdx.x;
   Regs R0, R1;
   if (nst > 0) fetch(R0, kbase);
   if (nst > 1) fetch(R1, kbase + kTK);
-  last = -1;
   auto step = [&](Regs& r, int st) -> bool {
-    const int b = st & 1;
+    const int g = gbase + st, b = g & 1;
     unsigned char* buf = sm + b * Lay::kStage;
     bool mine = true;
-    if (st >= 2) mine = mbar_wait(&bar[b], ((st - 2) >> 1) & 1);   // MMAs of stage st - 2 (same buffer)
+    if (g >= 2) mine = mbar_wait(&bar[b], ((g - 2) >> 1) & 1);     // MMAs of stage g - 2 (same buffer)
     tc_fence_after();
     store(r, buf);
     if (st + 2 < nst) fetch(r, kbase + (st + 2) * kTK);
@@ -307,7 +308,7 @@ __device__ __forceinline__ bool stage_loop(unsigned char* sm, uint64_t* bar, uin
       }
       mma_commit(&bar[b]);
     }
-    last = st;
+    last = g;
     return true;
   };
   bool ok = true;
@@ -316,9 +317,13 @@ __device__ __forceinline__ bool stage_loop(unsigned char* sm, uint64_t* bar, uin
     if (ok && st + 1 < nst) ok = step(R1, st + 1);
   }
   // the commit of the last stage completes after all earlier MMAs
-  if (ok && last >= 0) ok = __syncthreads_and(mbar_wait(&bar[last & 1], (last >> 1) & 1) ? 1 : 0) != 0;
+  if (ok && nst > 0) ok = __syncthreads_and(mbar_wait(&bar[last & 1], (last >> 1) & 1) ? 1 : 0) != 0;
   return ok;
 }
+
+// a hint to bring the 128-byte line at p into L2 (the loads of a later stage then hit L2)
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+constexpr int kPrefetch = 4;              // stages between an L2 prefetch and the loads of its stage
 
 // common prologue: tensor-memory allocation and the two mbarriers
 template <int NT>
@@ -424,6 +429,14 @@ __global__ void __launch_bounds__(kThreads, 2)
         R.b[j][h] = pb[j] && q < k1 ? *reinterpret_cast<const float4*>(pb[j] + kb + 4 * h) : z4;
         if (q + 2 >= k1) R.b[j][h].z = R.b[j][h].w = 0.f;          // second plane wave past Nb_k
       }
+    // the rows' lines kPrefetch stages on (chunk 0 of a row starts its 128-byte line)
+    const int kp = kb + kPrefetch * kTK;
+    if (kp < k1) {
+      if (pa && ca == 0) prefetch_l2(pa + kp);
+#pragma unroll
+      for (int j = 0; j < kBN; ++j)
+        if (pb[j] && cb[j] == 0) prefetch_l2(pb[j] + kp);
+    }
   };
   auto store = [&](Regs& R, unsigned char* buf) {
     // vector mo: row 2 mo = (Re, Im), row 2 mo + 1 = (-Im, Re) of the chunk's four plane waves
@@ -433,9 +446,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int j = 0; j < kBN; ++j)
       if (rb[j] < NT) put_pieces<SWZ>(buf + 3 * kAPiece, Lay::kBPiece, rb[j], cb[j], split8(R.b[j][0], R.b[j][1]));
   };
-  int last;
+  int last = -1;
   const int nst = (k1 - k0 + kTK - 1) / kTK;
-  const bool ok = stage_loop<NT, SWZ, Regs>(sm, bar, tmem, nst, k0, fetch, store, last);
+  const bool ok = stage_loop<NT, SWZ, Regs>(sm, bar, tmem, nst, k0, 0, fetch, store, last);
   if (ok) {
     tc_fence_after();
     // lanes 32 q .. 32 q + 31 of tensor memory are rows i0 + 32 q + lane of C^T; the two
@@ -458,17 +471,20 @@ __global__ void __launch_bounds__(kThreads, 2)
   tc_end<NT>(ok, last, bar, tmem, err);
 }
 
-// out[s][g] = alpha in[s][g] + beta sum_m v_m[g] coef[s][m] for the plane waves of one 128-real
-// tile (64 plane waves) and NT systems; with dv, dpart[s * nparts + tile] = sum Re(conj(dv) out)
-// over the tile (the chunking of the CUDA-core apply: 64 plane waves).
-// grid: (plane-wave tiles, k-points, system tiles).
+// out[s][g] = alpha in[s][g] + beta sum_m v_m[g] coef32[s][m] (coef32: the FP32 coefficients at
+// row stride ldc, even, zero past N_k), one work item = the plane waves
+// of one 128-real tile (64 plane waves) of one k-point and NT systems; with dv,
+// dpart[s * nparts + tile] = sum Re(conj(dv) out) over the tile (the chunking of the
+// CUDA-core apply: 64 plane waves).  Persistent: a CTA keeps its tensor memory, mbarriers
+// and system list and takes the items blockIdx.x, blockIdx.x + gridDim.x, ... (tile fastest,
+// then k-point, then system tile), continuing the stage numbering from item to item.
 template <int NT, bool SWZ>
 __global__ void __launch_bounds__(kThreads, 2)
     k_tc_apply(const float2* __restrict__ phi, const int* __restrict__ set_off, const int* __restrict__ set_cnt,
                const int* __restrict__ nb_k, const int* __restrict__ kstart, const int* __restrict__ kcount,
-               const double2* __restrict__ coef, int maxcnt, const float2* in, float alpha, float beta,
+               const float2* __restrict__ coef32, int ldc, const float2* in, float alpha, float beta,
                float2* out, int ldy, int ld, const float2* __restrict__ dv, double* __restrict__ dpart, int nparts,
-               const int* __restrict__ active, int* __restrict__ err) {
+               int nk, int nitems, const int* __restrict__ active, int* __restrict__ err) {
   using Lay = TcLayout<NT>;
   extern __shared__ __align__(1024) unsigned char sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + Lay::kBar);
@@ -476,73 +492,82 @@ __global__ void __launch_bounds__(kThreads, 2)
   int* sys_s = reinterpret_cast<int*>(sm + Lay::kSys);
   int* wcnt = reinterpret_cast<int*>(sm + Lay::kWcnt);
   double* red = reinterpret_cast<double*>(sm + Lay::kRed);       // [NT][2] dot partials
-  const int tile = blockIdx.x, k = blockIdx.y, tn = blockIdx.z;
-  const int cnt = set_cnt[k], nb = nb_k[k];
-  const int r0 = tile * kTM, s0 = tn * NT, g0 = r0 / 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nact = tile_systems<NT>(sys_s, wcnt, kstart[k], kcount[k], active, s0);
-  if (nact <= s0) return;                                          // uniform
-  const int nrow = min(NT, nact - s0);
-  if (r0 >= 2 * nb) {                                              // tile past Nb_k: define the dot partials
-    if (dpart)
-      for (int j = tid; j < nrow; j += kThreads) dpart[(size_t)sys_s[j] * nparts + tile] = 0.0;
-    return;
-  }
   const uint32_t tmem = tc_prologue<NT>(bar, slot);
-
-  // A item: plane wave gl of the tile and chunk ca (vectors 4 ca .. 4 ca + 3 of the stage);
-  // consecutive threads take consecutive plane waves (coalesced loads).  B item: a system
-  // and a chunk (its coefficients of the same four vectors).
   constexpr int kBN = NT * 4 / kThreads > 0 ? NT * 4 / kThreads : 1;
-  const float2* vk = phi + (size_t)set_off[k] * ld + g0;          // g0 + 63 < ld: ld is a multiple of 64
   const int gla = tid & 63, ca = tid >> 6;
-  const double2* pc[kBN];
-  int rb[kBN], cb[kBN];
-#pragma unroll
-  for (int j = 0; j < kBN; ++j) {
-    tile_item(tid + kThreads * j, rb[j], cb[j]);
-    const int s = rb[j] < NT ? sys_s[rb[j]] : -1;
-    pc[j] = s >= 0 ? coef + (size_t)s * maxcnt + 4 * cb[j] : nullptr;
-  }
-  struct Regs {
-    float2 a[4];
-    double2 b[kBN][4];
-  };
   const float2 z2 = make_float2(0.f, 0.f);
-  const double2 zd = make_double2(0.0, 0.0);
-  auto fetch = [&](Regs& R, int kb) {
-    const int mb = kb / 2;                                         // first vector of the stage
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int m = mb + 4 * ca + u;
-      R.a[u] = m < cnt ? vk[(size_t)m * ld + gla] : z2;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  int last = -1, gbase = 0, cur = -1, nact = 0;
+  bool ok = true;
+  for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+    const int tile = item % nparts, rest = item / nparts;
+    const int k = rest % nk, tn = rest / nk;
+    const int cnt = set_cnt[k], nb = nb_k[k];
+    const int r0 = tile * kTM, s0 = tn * NT, g0 = r0 / 2;
+    if (rest != cur) {                                             // uniform: the item's system list
+      nact = tile_systems<NT>(sys_s, wcnt, kstart[k], kcount[k], active, s0);
+      cur = rest;
     }
-#pragma unroll
-    for (int j = 0; j < kBN; ++j)
+    if (nact <= s0) continue;                                      // uniform
+    const int nrow = min(NT, nact - s0);
+    if (r0 >= 2 * nb) {                                            // tile past Nb_k: define the dot partials
+      if (dpart)
+        for (int j = tid; j < nrow; j += kThreads) dpart[(size_t)sys_s[j] * nparts + tile] = 0.0;
+      __syncthreads();                                             // sys_s may be rewritten by the next item
+      continue;
+    }
+    // A item: plane wave gl of the tile and chunk ca (vectors 4 ca .. 4 ca + 3 of the stage);
+    // consecutive threads take consecutive plane waves (coalesced loads).  B item: a system
+    // and a chunk (its coefficients of the same four vectors).
+    const float2* vk = phi + (size_t)set_off[k] * ld + g0;        // g0 + 63 < ld: ld is a multiple of 64
+    struct Regs {
+      float2 a[4];
+      float4 b[kBN][2];
+    };
+    // (the B items' rows and chunks are recomputed where used: fewer live registers)
+    auto fetch = [&](Regs& R, int kb) {
+      const int mb = kb / 2;                                       // first vector of the stage
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int m = mb + 4 * cb[j] + u;
-        R.b[j][u] = pc[j] && m < cnt ? pc[j][mb + u] : zd;
+        const int m = mb + 4 * ca + u;
+        R.a[u] = m < cnt ? vk[(size_t)m * ld + gla] : z2;
       }
-  };
-  auto store = [&](Regs& R, unsigned char* buf) {
-    // plane wave gl: row 2 gl = (Re v, -Im v), row 2 gl + 1 = (Im v, Re v) of the chunk's four vectors
-    const Pieces x = split8(make_float4(R.a[0].x, R.a[0].y, R.a[1].x, R.a[1].y),
-                            make_float4(R.a[2].x, R.a[2].y, R.a[3].x, R.a[3].y));
-    put_pair<SWZ>(buf, kAPiece, gla, ca, map_pairs(x, conj_pair), map_pairs(x, swap_pair));
 #pragma unroll
-    for (int j = 0; j < kBN; ++j) {
-      if (rb[j] >= NT) continue;
-      const double2* c = R.b[j];
-      put_pieces<SWZ>(buf + 3 * kAPiece, Lay::kBPiece, rb[j], cb[j],
-                      split8(make_float4((float)c[0].x, (float)c[0].y, (float)c[1].x, (float)c[1].y),
-                             make_float4((float)c[2].x, (float)c[2].y, (float)c[3].x, (float)c[3].y)));
-    }
-  };
-  int last;
-  const int nst = (2 * cnt + kTK - 1) / kTK;
-  const bool ok = stage_loop<NT, SWZ, Regs>(sm, bar, tmem, nst, 0, fetch, store, last);
-  if (ok) {
+      for (int j = 0; j < kBN; ++j) {
+        int r, c;
+        tile_item(tid + kThreads * j, r, c);
+        const int sj = r < NT ? sys_s[r] : -1;
+        // coefficients m, m + 1 per 16 bytes (the copy is zero from N_k to its even stride)
+        const float2* pc = coef32 + (size_t)(sj < 0 ? 0 : sj) * ldc + mb + 4 * c;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          R.b[j][h] = sj >= 0 && mb + 4 * c + 2 * h < ldc ? *reinterpret_cast<const float4*>(pc + 2 * h) : z4;
+      }
+      // the vectors' lines of a later stage (16 plane waves of 8 bytes per 128-byte line)
+      const int mp = mb + kPrefetch * (kTK / 2);
+      if ((gla & 15) == 0)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (mp + 4 * ca + u < cnt) prefetch_l2(vk + (size_t)(mp + 4 * ca + u) * ld + gla);
+    };
+    auto store = [&](Regs& R, unsigned char* buf) {
+      // plane wave gl: row 2 gl = (Re v, -Im v), row 2 gl + 1 = (Im v, Re v) of the chunk's four vectors
+      const Pieces x = split8(make_float4(R.a[0].x, R.a[0].y, R.a[1].x, R.a[1].y),
+                              make_float4(R.a[2].x, R.a[2].y, R.a[3].x, R.a[3].y));
+      put_pair<SWZ>(buf, kAPiece, gla, ca, map_pairs(x, conj_pair), map_pairs(x, swap_pair));
+#pragma unroll
+      for (int j = 0; j < kBN; ++j) {
+        int r, cc;
+        tile_item(tid + kThreads * j, r, cc);
+        if (r >= NT) continue;
+        put_pieces<SWZ>(buf + 3 * kAPiece, Lay::kBPiece, r, cc, split8(R.b[j][0], R.b[j][1]));
+      }
+    };
+    const int nst = (2 * cnt + kTK - 1) / kTK;
+    ok = stage_loop<NT, SWZ, Regs>(sm, bar, tmem, nst, 0, gbase, fetch, store, last);
+    gbase += nst;
+    if (!ok) break;                                                // uniform
     tc_fence_after();
     // D through shared memory (the ring is free now): Ds[j][r] for system column j and
     // tile row r = 2 g + c, so that every thread then takes whole plane waves of one system
@@ -563,43 +588,41 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int j = 0; j < 16; ++j) Ds[(c0 + j) * kTM + r] = v[j];
       }
     }
+    tc_fence_before();
     __syncthreads();
     // thread t: plane wave g0 + (t mod 64) of the systems t / 64, t / 64 + 4, ...; the loads of
     // 8 systems first (each element is read and written by this thread only)
-    const int gl = tid & 63, g = g0 + gl, j0 = tid >> 6;
+    const int g = g0 + gla, j0 = tid >> 6;
     const bool gok = g < nb;
-    const float2 z2 = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int jb = j0; jb < NT; jb += 32) {
       float2 xin[8], w[8];
-      size_t o[8];
-      bool on[8];
+      int sv[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int j = jb + 4 * u;
-        const int sj = j < nrow ? sys_s[j] : -1;
-        on[u] = gok && sj >= 0;
-        o[u] = on[u] ? (size_t)sj * ldy + g : 0;
-        xin[u] = on[u] && alpha != 0.f ? in[o[u]] : z2;
-        w[u] = on[u] && dv ? dv[o[u]] : z2;
+        sv[u] = gok && j < nrow ? sys_s[j] : -1;
+        const size_t o = (size_t)(sv[u] < 0 ? 0 : sv[u]) * ldy + g;
+        xin[u] = sv[u] >= 0 && alpha != 0.f ? in[o] : z2;
+        w[u] = sv[u] >= 0 && dv ? dv[o] : z2;
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int j = jb + 4 * u;
-        const float2 dd = j < NT ? *reinterpret_cast<const float2*>(Ds + j * kTM + 2 * gl) : z2;
+        const float2 dd = *reinterpret_cast<const float2*>(Ds + j * kTM + 2 * gla);
         float2 y = make_float2(beta * dd.x, beta * dd.y);
         if (alpha != 0.f) {
           y.x += alpha * xin[u].x;
           y.y += alpha * xin[u].y;
         }
         double d = 0.0;
-        if (on[u]) {
-          out[o[u]] = y;
+        if (sv[u] >= 0) {
+          out[(size_t)sv[u] * ldy + g] = y;
           d = (double)w[u].x * y.x + (double)w[u].y * y.y;
         }
         if (dpart) {                                               // the 64 plane waves of system j: 2 warps
           d = warp_sum(d);
-          if (lane == 0 && j < NT) red[2 * j + ((tid >> 5) & 1)] = d;
+          if (lane == 0) red[2 * j + ((tid >> 5) & 1)] = d;
         }
       }
     }
@@ -607,28 +630,71 @@ __global__ void __launch_bounds__(kThreads, 2)
       __syncthreads();
       for (int j = tid; j < nrow; j += kThreads) dpart[(size_t)sys_s[j] * nparts + tile] = red[2 * j] + red[2 * j + 1];
     }
+    __syncthreads();                                               // Ds, red and sys_s are reused by the next item
   }
   tc_end<NT>(ok, last, bar, tmem, err);
 }
 
-// coef[s][m] = sum of the chunk partials in chunk order: a thread per coefficient
-__global__ void k_tc_reduce(const float2* __restrict__ part, int nsys, int maxcnt, int chunk,
-                            const int* __restrict__ sys_k, const int* __restrict__ set_cnt,
-                            const int* __restrict__ nb_k, const int* __restrict__ active, double2* __restrict__ coef) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)nsys * maxcnt) return;
-  const int s = (int)(t / maxcnt), m = (int)(t - (long long)s * maxcnt);
-  if (active && !active[s]) return;
-  const int k = sys_k[s];
-  if (m >= set_cnt[k]) return;
-  const int nc = (2 * nb_k[k] + chunk - 1) / chunk;
-  double ax = 0.0, ay = 0.0;
-  for (int c = 0; c < nc; ++c) {
-    const float2 v = part[((size_t)c * nsys + s) * maxcnt + m];
-    ax += (double)v.x;
-    ay += (double)v.y;
+// coef[s][m] = sum of the chunk partials.  Block (32, 8): threadIdx.x picks one of 32
+// consecutive coefficients (coalesced loads of a chunk's partials), threadIdx.y = q sums the
+// chunks q, q + 8, q + 16, ...; the eight sums are added in a fixed tree through shared
+// memory, so the order is the same on every run.
+__global__ void __launch_bounds__(256) k_tc_reduce(const float2* __restrict__ part, int nsys, int maxcnt, int chunk,
+                                                   const int* __restrict__ sys_k, const int* __restrict__ set_cnt,
+                                                   const int* __restrict__ nb_k, const int* __restrict__ active,
+                                                   double2* __restrict__ coef) {
+  __shared__ double2 sh[8][32];
+  const long long t = (long long)blockIdx.x * 32 + threadIdx.x;
+  const int q = threadIdx.y;
+  bool on = t < (long long)nsys * maxcnt;
+  int s = 0, m = 0, nc = 0;
+  if (on) {
+    s = (int)(t / maxcnt);
+    m = (int)(t - (long long)s * maxcnt);
+    on = (!active || active[s]) && m < set_cnt[sys_k[s]];
+    nc = (2 * nb_k[sys_k[s]] + chunk - 1) / chunk;
   }
-  coef[t] = make_double2(ax, ay);
+  double ax = 0.0, ay = 0.0;
+  if (on) {
+    const size_t stride = (size_t)nsys * maxcnt;
+    const float2* p = part + (size_t)s * maxcnt + m;
+    int c = q;
+    for (; c + 8 < nc; c += 16) {                                  // two loads in flight
+      const float2 v0 = p[(size_t)c * stride], v1 = p[(size_t)(c + 8) * stride];
+      ax += (double)v0.x;
+      ay += (double)v0.y;
+      ax += (double)v1.x;
+      ay += (double)v1.y;
+    }
+    if (c < nc) {
+      const float2 v = p[(size_t)c * stride];
+      ax += (double)v.x;
+      ay += (double)v.y;
+    }
+  }
+  sh[q][threadIdx.x] = make_double2(ax, ay);
+  __syncthreads();
+  if (q == 0 && on) {
+    double2 r[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) r[u] = sh[u][threadIdx.x];
+    const double sx = ((r[0].x + r[1].x) + (r[2].x + r[3].x)) + ((r[4].x + r[5].x) + (r[6].x + r[7].x));
+    const double sy = ((r[0].y + r[1].y) + (r[2].y + r[3].y)) + ((r[4].y + r[5].y) + (r[6].y + r[7].y));
+    coef[t] = make_double2(sx, sy);
+  }
+}
+
+// coef32[s][m] = (float) coef[s][m] for m < N_k of the system's k-point, 0 up to the even stride
+// ldc (two coefficients per 16-byte load in k_tc_apply)
+__global__ void k_tc_coef32(const double2* __restrict__ coef, int nsys, int maxcnt, int ldc,
+                            const int* __restrict__ sys_k, const int* __restrict__ set_cnt,
+                            const int* __restrict__ active, float2* __restrict__ coef32) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nsys * ldc) return;
+  const int s = (int)(t / ldc), m = (int)(t - (long long)s * ldc);
+  if (active && !active[s]) return;
+  const double2 v = m < set_cnt[sys_k[s]] ? coef[(size_t)s * maxcnt + m] : make_double2(0.0, 0.0);
+  coef32[t] = make_float2((float)v.x, (float)v.y);
 }
 
 // ----------------------------------------------------------------- host --
@@ -692,21 +758,34 @@ void proj_coef_tc(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const 
   auto launch = [&](auto kern, size_t smem) {
     smem_attrs(kern, smem);
     // split-K: chunks (multiples of a stage) of at most kMaxChunk reals (the length of the
-    // FP32 sums), and at least enough of them for two CTAs per SM
-    const int target = 2 * sm_count();
-    const int want = std::max((2 * maxnb + kMaxChunk - 1) / kMaxChunk, target / std::max(1, nk * nmt * nnt));
-    const int per = (2 * maxnb + want - 1) / want;
-    const int chunk = std::max(kTK, (per + kTK - 1) / kTK * kTK);
-    const int nch = (2 * maxnb + chunk - 1) / chunk;
+    // FP32 sums).  Among the chunk counts that fill w = 1, 2, ... waves of two CTAs per SM, take
+    // the one with the least time: waves x (stages per CTA + the CTA's fixed cost, about three
+    // stages: the system scan, the first loads, the epilogue)
+    const int slots = 2 * sm_count(), tiles = std::max(1, nk * nmt * nnt), K = 2 * maxnb;
+    int chunk = 0;
+    double best = 1e300;
+    for (int w = 1; w <= 16; ++w) {
+      const int want = std::max(1, w * slots / tiles);
+      const int ch = std::max(kTK, ((K + want - 1) / want + kTK - 1) / kTK * kTK);
+      if (ch > kMaxChunk && w < 16) continue;
+      const int n = (K + ch - 1) / ch;
+      const int waves = (n * tiles + slots - 1) / slots;
+      const double cost = waves * (ch / (double)kTK + 3.0);
+      if (cost < best) {
+        best = cost;
+        chunk = ch;
+      }
+    }
+    const int nch = (K + chunk - 1) / chunk;
     c->ws.cpart.reserve((size_t)nch * L.n * set.maxcnt);            // doubles: room for float2 partials
     float2* part = reinterpret_cast<float2*>(c->ws.cpart.p);
     dim3 grid((unsigned)nmt, (unsigned)nch, (unsigned)(nk * nnt));
     kern<<<grid, kThreads, smem, c->stream>>>(set.phi32, set.off, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p,
                                               Y, ldy, c->ld, nnt, chunk, L.n, set.maxcnt, active, part, c->tc_err.p);
     IKR_CUDA(cudaGetLastError());
-    const long long threads = (long long)L.n * set.maxcnt;
-    k_tc_reduce<<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(part, L.n, set.maxcnt, chunk, L.d_k.p,
-                                                                           set.cnt, c->d_nb.p, active, coef);
+    const long long ncoef = (long long)L.n * set.maxcnt;
+    k_tc_reduce<<<(unsigned)((ncoef + 31) / 32), dim3(32, 8), 0, c->stream>>>(part, L.n, set.maxcnt, chunk, L.d_k.p,
+                                                                             set.cnt, c->d_nb.p, active, coef);
     IKR_CUDA(cudaGetLastError());
   };
   const bool swz = c->tc_swizzle;
@@ -729,13 +808,24 @@ void proj_apply_tc(ikr_ctx* c, const SysList& L, const double2* coef, const floa
   const int nparts = (c->ld + 63) / 64;                           // 64 plane waves per tile and dot partial
   const int nt = tile_nt(maxns);
   const int nnt = (maxns + nt - 1) / nt;
+  const int nk = (int)c->k.size();
+  const int nitems = nparts * nk * nnt;
   tc_flag_ready(c);
-  dim3 grid((unsigned)nparts, (unsigned)c->k.size(), (unsigned)nnt);
+  const int ldc = (set.maxcnt + 1) & ~1;
+  c->tc_coef32.reserve((size_t)L.n * ldc);
+  {
+    const long long n = (long long)L.n * ldc;
+    k_tc_coef32<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(coef, L.n, set.maxcnt, ldc, L.d_k.p, set.cnt,
+                                                                      active, c->tc_coef32.p);
+    IKR_CUDA(cudaGetLastError());
+  }
+  // persistent: two CTAs per SM (or one per item)
+  const dim3 grid((unsigned)std::min(nitems, 2 * sm_count()));
   auto launch = [&](auto kern, size_t smem) {
     smem_attrs(kern, smem);
     kern<<<grid, kThreads, smem, c->stream>>>(set.phi32, set.off, set.cnt, c->d_nb.p, L.d_kstart.p, L.d_kcount.p,
-                                              coef, set.maxcnt, in, alpha, beta, out, ldy, c->ld, dv, dpart, nparts,
-                                              active, c->tc_err.p);
+                                              c->tc_coef32.p, ldc, in, alpha, beta, out, ldy, c->ld, dv, dpart,
+                                              nparts, nk, nitems, active, c->tc_err.p);
     IKR_CUDA(cudaGetLastError());
   };
   const bool swz = c->tc_swizzle;
