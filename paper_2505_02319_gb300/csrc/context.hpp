@@ -266,6 +266,11 @@ struct ikr_ctx {
   int mask_bound = 0;           // > 0: at most this many systems are active in masked FP32 projections (CG)
   ikr::DBuf<int> tc_err;
   ikr::DBuf<float2> tc_coef32;  // FP32 copy of the coefficients of a tensor-core V C product
+  // the coefficient buffer (and mask, stride) whose FP32 copy tc_coef32 holds: written by the
+  // tensor-core V^H Y together with the FP64 result, cleared by every other writer
+  const double2* tc_coef32_of = nullptr;
+  const int* tc_coef32_mask = nullptr;
+  int tc_coef32_ldc = 0;
   ikr::SysList batch_list;
   ikr::DBuf<int> d_batch_map;
   int rmax = 0, xmax = 0;

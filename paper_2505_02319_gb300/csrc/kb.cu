@@ -149,6 +149,7 @@ void apply_nonlocal(ikr_ctx* c, const SysList& L, const C_t<R>* in, int ld, C_t<
     ProfScope ps(c, kKidProjApply, 1);
     k_kb_scale<<<(L.n * 32 + 255) / 256, 256, 0, c->stream>>>(Cm, c->nproj, L.n, c->d_kbD.p, active, pap, nparts);
     IKR_CUDA(cudaGetLastError());
+    c->tc_coef32_of = nullptr;   // scaled in place: the FP32 copy of the coefficients is stale
   }
   proj_apply<R>(c, L, Cm, out, R(1), R(1), out, ld, nullptr, nullptr, active, &kb);
 }

@@ -620,6 +620,7 @@ void proj_coef(ikr_ctx* c, const SysList& L, const C_t<R>* Y, int ldy, const int
                const OrbSet* set) {
   ProfScope ps(c, kKidProjCoef, 2, L.n, (int)sizeof(R));
   const OrbSet os = set ? *set : occ_set(c);
+  c->tc_coef32_of = nullptr;   // a tensor-core product below makes the FP32 copy current again
   if (sizeof(R) == 8) {
     const int nch = (c->ld + kPC - 1) / kPC;
     const int nm = os.maxcnt;
@@ -748,6 +749,7 @@ __global__ void k_deflate_coef(double2* __restrict__ a, int xmax, int nsys, cons
 }
 
 void deflate_coef(ikr_ctx* c, const SysList& L, double2* a, const double* shift) {
+  c->tc_coef32_of = nullptr;   // the coefficients change: their FP32 copy is stale
   ProfScope ps(c, kKidScalar, 1);
   const int tot = L.n * c->xmax;
   if (tot == 0) return;

@@ -50,6 +50,9 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "ops.hpp"
 
@@ -635,23 +638,25 @@ __global__ void __launch_bounds__(kThreads, 2)
   tc_end<NT>(ok, last, bar, tmem, err);
 }
 
-// coef[s][m] = sum of the chunk partials.  Block (32, 8): threadIdx.x picks one of 32
+// coef[s][m] = sum of the chunk partials, and its FP32 copy coef32[s][m] (row stride ldc,
+// even; zero from N_k on) for the V C product.  Block (32, 8): threadIdx.x picks one of 32
 // consecutive coefficients (coalesced loads of a chunk's partials), threadIdx.y = q sums the
 // chunks q, q + 8, q + 16, ...; the eight sums are added in a fixed tree through shared
 // memory, so the order is the same on every run.
 __global__ void __launch_bounds__(256) k_tc_reduce(const float2* __restrict__ part, int nsys, int maxcnt, int chunk,
                                                    const int* __restrict__ sys_k, const int* __restrict__ set_cnt,
                                                    const int* __restrict__ nb_k, const int* __restrict__ active,
-                                                   double2* __restrict__ coef) {
+                                                   double2* __restrict__ coef, float2* __restrict__ coef32, int ldc) {
   __shared__ double2 sh[8][32];
   const long long t = (long long)blockIdx.x * 32 + threadIdx.x;
   const int q = threadIdx.y;
-  bool on = t < (long long)nsys * maxcnt;
+  bool sys_on = t < (long long)nsys * maxcnt, on = false;
   int s = 0, m = 0, nc = 0;
-  if (on) {
+  if (sys_on) {
     s = (int)(t / maxcnt);
     m = (int)(t - (long long)s * maxcnt);
-    on = (!active || active[s]) && m < set_cnt[sys_k[s]];
+    sys_on = !active || active[s];
+    on = sys_on && m < set_cnt[sys_k[s]];
     nc = (2 * nb_k[sys_k[s]] + chunk - 1) / chunk;
   }
   double ax = 0.0, ay = 0.0;
@@ -674,13 +679,18 @@ __global__ void __launch_bounds__(256) k_tc_reduce(const float2* __restrict__ pa
   }
   sh[q][threadIdx.x] = make_double2(ax, ay);
   __syncthreads();
-  if (q == 0 && on) {
-    double2 r[8];
+  if (q == 0 && sys_on) {
+    double sx = 0.0, sy = 0.0;
+    if (on) {
+      double2 r[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) r[u] = sh[u][threadIdx.x];
-    const double sx = ((r[0].x + r[1].x) + (r[2].x + r[3].x)) + ((r[4].x + r[5].x) + (r[6].x + r[7].x));
-    const double sy = ((r[0].y + r[1].y) + (r[2].y + r[3].y)) + ((r[4].y + r[5].y) + (r[6].y + r[7].y));
-    coef[t] = make_double2(sx, sy);
+      for (int u = 0; u < 8; ++u) r[u] = sh[u][threadIdx.x];
+      sx = ((r[0].x + r[1].x) + (r[2].x + r[3].x)) + ((r[4].x + r[5].x) + (r[6].x + r[7].x));
+      sy = ((r[0].y + r[1].y) + (r[2].y + r[3].y)) + ((r[4].y + r[5].y) + (r[6].y + r[7].y));
+      coef[t] = make_double2(sx, sy);
+    }
+    coef32[(size_t)s * ldc + m] = make_float2((float)sx, (float)sy);
+    if (m == maxcnt - 1 && ldc > maxcnt) coef32[(size_t)s * ldc + maxcnt] = make_float2(0.f, 0.f);
   }
 }
 
@@ -717,19 +727,37 @@ namespace {
 int tile_nt(int n) { return n <= 32 ? 32 : (n <= 64 ? 64 : 128); }
 
 int sm_count() {
-  int dev = 0, sms = 0;
+  int dev = 0;
   IKR_CUDA(cudaGetDevice(&dev));
+  static int cached[64] = {};                                      // per device, read once
+  if (dev < 64 && cached[dev] > 0) return cached[dev];
+  int sms = 0;
   IKR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  return std::max(sms, 1);
+  sms = std::max(sms, 1);
+  if (dev < 64) cached[dev] = sms;
+  return sms;
 }
 
-// the kernel's shared memory, with the whole carveout for shared memory (two or three
-// CTAs per SM, the L1 cache is not used by these kernels' operand traffic)
+// The kernel's shared memory, with the whole carveout for shared memory (two or three CTAs
+// per SM; the L1 cache is not used by these kernels' operand traffic).  Every instance has a
+// fixed size, so the attributes are set once per kernel and device.
 template <typename K>
 void smem_attrs(K kern, size_t smem) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> done;
+  int dev = 0;
+  IKR_CUDA(cudaGetDevice(&dev));
+  const void* f = reinterpret_cast<const void*>(kern);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    for (const auto& e : done)
+      if (e.first == f && e.second == dev) return;
+  }
   IKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   IKR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared));
+  std::lock_guard<std::mutex> g(mu);
+  done.push_back({f, dev});
 }
 
 // the most systems of one k-point that a launch can find active: all of them without
@@ -784,9 +812,15 @@ void proj_coef_tc(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const 
                                               Y, ldy, c->ld, nnt, chunk, L.n, set.maxcnt, active, part, c->tc_err.p);
     IKR_CUDA(cudaGetLastError());
     const long long ncoef = (long long)L.n * set.maxcnt;
+    const int ldc = (set.maxcnt + 1) & ~1;
+    c->tc_coef32.reserve((size_t)L.n * ldc);
     k_tc_reduce<<<(unsigned)((ncoef + 31) / 32), dim3(32, 8), 0, c->stream>>>(part, L.n, set.maxcnt, chunk, L.d_k.p,
-                                                                             set.cnt, c->d_nb.p, active, coef);
+                                                                             set.cnt, c->d_nb.p, active, coef,
+                                                                             c->tc_coef32.p, ldc);
     IKR_CUDA(cudaGetLastError());
+    c->tc_coef32_of = coef;                                        // the FP32 copy is current
+    c->tc_coef32_mask = active;
+    c->tc_coef32_ldc = ldc;
   };
   const bool swz = c->tc_swizzle;
   if (nt == 32) {
@@ -812,12 +846,14 @@ void proj_apply_tc(ikr_ctx* c, const SysList& L, const double2* coef, const floa
   const int nitems = nparts * nk * nnt;
   tc_flag_ready(c);
   const int ldc = (set.maxcnt + 1) & ~1;
-  c->tc_coef32.reserve((size_t)L.n * ldc);
-  {
+  // the FP32 copy of the coefficients: from the tensor-core V^H Y that produced them, else made here
+  if (!(coef == c->tc_coef32_of && active == c->tc_coef32_mask && ldc == c->tc_coef32_ldc)) {
+    c->tc_coef32.reserve((size_t)L.n * ldc);
     const long long n = (long long)L.n * ldc;
     k_tc_coef32<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(coef, L.n, set.maxcnt, ldc, L.d_k.p, set.cnt,
                                                                       active, c->tc_coef32.p);
     IKR_CUDA(cudaGetLastError());
+    c->tc_coef32_of = nullptr;
   }
   // persistent: two CTAs per SM (or one per item)
   const dim3 grid((unsigned)std::min(nitems, 2 * sm_count()));
