@@ -636,9 +636,11 @@ __global__ void __launch_bounds__(256) k_density_t(const typename io<R>::cx* __r
   for (int i = threadIdx.x; i < NX; i += blockDim.x) tx[i] = to_c<C>(twx[i]);
   for (int i = threadIdx.x; i < NY; i += blockDim.x) ty[i] = to_c<C>(twy[i]);
   for (int i = threadIdx.x; i < nxa; i += blockDim.x) xp[i] = xpos[i];
-  // double-float: products and sums on the FP32 pipe, the orbitals read from
-  // their (hi, lo) copy; FP64 otherwise
-  using A = typename std::conditional<std::is_same<R, dfloat>::value, dfloat, double>::type;
+  // double-float and FP32: the sums in double-float on the FP32 pipe (FP64 runs at a small
+  // fraction of the FP32 rate); FP64 otherwise.  Double-float reads the orbitals from their
+  // (hi, lo) copy and forms the products in double-float; FP32 forms each system's
+  // contribution in FP32 (its inputs carry FP32 rounding already) and adds it exactly.
+  using A = typename std::conditional<std::is_same<R, double>::value, double, dfloat>::type;
   A acc[NE];
 #pragma unroll
   for (int i = 0; i < NE; ++i) acc[i] = A(0.0);
@@ -698,6 +700,20 @@ __global__ void __launch_bounds__(256) k_density_t(const typename io<R>::cx* __r
             const float4 q = ps[e];
             const dfloat px(q.x, q.y), py(q.z, q.w);
             acc[i] += a * (px * d.x + py * d.y) + b * (px * px + py * py);
+          }
+        }
+      } else if constexpr (std::is_same<R, float>::value) {
+        const float a = (float)coef_a[s], b = (float)coef_b[s];
+        const float2* ps = psir + ((size_t)s * Nz + iz) * NX * NY;
+#pragma unroll
+        for (int i = 0; i < NE; ++i) {
+          const int e = threadIdx.x + 256 * i;
+          if (e < NX * NY) {
+            const int iy = e / NX, ix = e - iy * NX;
+            const float2 d = planes[p * G::plane + iy * ldp + ix];
+            const float2 q = ps[e];
+            const float t = fmaf(a, fmaf(q.x, d.x, q.y * d.y), b * fmaf(q.x, q.x, q.y * q.y));
+            acc[i] += dfloat(t, 0.f);
           }
         }
       } else {
