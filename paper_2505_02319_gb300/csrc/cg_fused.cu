@@ -164,7 +164,9 @@ __global__ void __launch_bounds__(kFT, 1) k_cg_fused(CgFusedArgs a) {
         kn[u] = a.kin_all[(size_t)k * a.ld + g0 + gi];
       }
     }
-    double rr = 0.0;
+    // FP32 per lane (at most 2 kFU terms), FP64 across the lanes and ranks: FP64 arithmetic runs
+    // at a small fraction of the FP32 rate, and the FP32 vectors carry FP32 rounding already
+    float rrf = 0.f;
 #pragma unroll
     for (int u = 0; u < kFU; ++u) {
       const int gi = lane + 32 * u;
@@ -177,10 +179,10 @@ __global__ void __launch_bounds__(kFT, 1) k_cg_fused(CgFusedArgs a) {
         a.Rv[ob + gi] = r[u];
         const float mi = 1.f / (kappa + kn[u]);
         zs[(size_t)j * lds + gi] = make_float2(r[u].x * mi, r[u].y * mi);
-        rr += (double)r[u].x * r[u].x + (double)r[u].y * r[u].y;
+        rrf = fmaf(r[u].x, r[u].x, fmaf(r[u].y, r[u].y, rrf));
       }
     }
-    rr = warp_sum(rr);
+    const double rr = warp_sum((double)rrf);
     if (lane == 0) rrp[j] = rr;
   }
   cluster.sync();
@@ -286,16 +288,16 @@ __global__ void __launch_bounds__(kFT, 1) k_cg_fused(CgFusedArgs a) {
         }
       }
     }
-    double rz = 0.0;
+    float rzf = 0.f;                                              // FP32 per lane, as ||r||^2
 #pragma unroll
     for (int u = 0; u < kFU; ++u) {
       const int gi = lane + 32 * u;
       if (gi < ng) {
         zs[(size_t)j * lds + gi] = z[u];
-        rz += (double)r[u].x * z[u].x + (double)r[u].y * z[u].y;
+        rzf = fmaf(r[u].x, z[u].x, fmaf(r[u].y, z[u].y, rzf));
       }
     }
-    rz = warp_sum(rz);
+    const double rz = warp_sum((double)rzf);
     if (lane == 0) rzp[j] = rz;
   }
   cluster.sync();

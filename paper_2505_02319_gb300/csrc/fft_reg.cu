@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(kZC)
   }
   cp_async_wait_all();
   __syncthreads();
-  double dot = 0.0;
+  float dotf = 0.f;   // FP32 over the column's run, FP64 across the columns (FP64 is slow here)
   if (col < nc) {
     const int* inf = colinfo + ((size_t)k * nc + col) * 3;
     const int rel = inf[0] - base, cnt = inf[1], zs = inf[2];
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(kZC)
           const float2 p = sp[rel + t];
           val.x += d * p.x;
           val.y += d * p.y;
-          dot += (double)p.x * val.x + (double)p.y * val.y;
+          dotf = fmaf(p.x, val.x, fmaf(p.y, val.y, dotf));
         }
         so[rel + t] = val;
       }
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(kZC)
   float2* dst = out + (size_t)s * ld + base;
   for (int e = threadIdx.x; e < span; e += kZC) dst[e] = so[e];
   if (dpart) {
-    dot = warp_sum(dot);
+    const double dot = warp_sum((double)dotf);
     if (threadIdx.x == 0) dpart[(size_t)s * gridDim.x + blockIdx.x] = dot;
   }
 }
