@@ -270,7 +270,7 @@ struct ikr_ctx {
   // tensor-core V^H Y together with the FP64 result, cleared by every other writer
   const double2* tc_coef32_of = nullptr;
   const int* tc_coef32_mask = nullptr;
-  int tc_coef32_ldc = 0;
+  int tc_coef32_ldc = 0, tc_coef32_n = 0;
   ikr::SysList batch_list;
   ikr::DBuf<int> d_batch_map;
   int rmax = 0, xmax = 0;

@@ -821,6 +821,7 @@ void proj_coef_tc(ikr_ctx* c, const SysList& L, const float2* Y, int ldy, const 
     c->tc_coef32_of = coef;                                        // the FP32 copy is current
     c->tc_coef32_mask = active;
     c->tc_coef32_ldc = ldc;
+    c->tc_coef32_n = L.n;
   };
   const bool swz = c->tc_swizzle;
   if (nt == 32) {
@@ -847,7 +848,8 @@ void proj_apply_tc(ikr_ctx* c, const SysList& L, const double2* coef, const floa
   tc_flag_ready(c);
   const int ldc = (set.maxcnt + 1) & ~1;
   // the FP32 copy of the coefficients: from the tensor-core V^H Y that produced them, else made here
-  if (!(coef == c->tc_coef32_of && active == c->tc_coef32_mask && ldc == c->tc_coef32_ldc)) {
+  if (!(coef == c->tc_coef32_of && active == c->tc_coef32_mask && ldc == c->tc_coef32_ldc &&
+        L.n == c->tc_coef32_n)) {
     c->tc_coef32.reserve((size_t)L.n * ldc);
     const long long n = (long long)L.n * ldc;
     k_tc_coef32<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(coef, L.n, set.maxcnt, ldc, L.d_k.p, set.cnt,
