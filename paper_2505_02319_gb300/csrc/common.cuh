@@ -302,6 +302,12 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Sum over the block; result valid in thread 0.  `sh` needs blockDim/32 doubles.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   v = warp_sum(v);

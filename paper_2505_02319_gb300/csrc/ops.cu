@@ -227,11 +227,25 @@ __global__ void __launch_bounds__(kEC) k_cg_xr(int mode, C_t<R>* __restrict__ X,
     Rv[o] = r;
     const R mi = R(1) / (kappa + kin_all[(size_t)k * ld + g]);
     Z[o] = mk<C>(r.x * mi, r.y * mi);
-    rr = (double)r.x * r.x + (double)r.y * r.y;
+    if constexpr (sizeof(R) == 8) rr = (double)r.x * r.x + (double)r.y * r.y;
+    else rr = (double)fmaf(r.x, r.x, r.y * r.y);
   }
   if (mode == 1 && dpart) {
-    rr = block_sum(rr, sh);
-    if (threadIdx.x == 0) dpart[(size_t)s * nparts + chunk] = rr;
+    if constexpr (sizeof(R) == 4) {
+      // FP32 within the warp, FP64 across the warps (FP64 arithmetic is slow here)
+      const float wsum = warp_sum((float)rr);
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)wsum;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kEC / 32; ++w) t += sh[w];
+        dpart[(size_t)s * nparts + chunk] = t;
+      }
+    } else {
+      rr = block_sum(rr, sh);
+      if (threadIdx.x == 0) dpart[(size_t)s * nparts + chunk] = rr;
+    }
   }
 }
 

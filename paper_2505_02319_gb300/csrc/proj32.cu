@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kAT)
         acc[i][j].y += p[i].x * c[j].y + p[i].y * c[j].x;
       }
   }
-  double dd[2] = {0.0, 0.0};
+  float dd[2] = {0.f, 0.f};   // FP32 over the thread's plane waves and the 16 lanes, stored in FP64
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     const int sl = 2 * ts + j;
@@ -194,18 +194,18 @@ __global__ void __launch_bounds__(kAT)
           v.y += alpha * xin[i][j].y;
         }
         out[o] = v;
-        if (dv) dd[j] += (double)wdv[i][j].x * v.x + (double)wdv[i][j].y * v.y;
+        if (dv) dd[j] = fmaf(wdv[i][j].x, v.x, fmaf(wdv[i][j].y, v.y, dd[j]));
       }
     }
   }
   if (dpart) {
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      double t = dd[j];
+      float t = dd[j];
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       const int sl = 2 * ts + j;
-      if (tg == 0 && sl < nsl && (!active || active[s0 + sl])) dpart[(size_t)(s0 + sl) * nparts + chunk] = t;
+      if (tg == 0 && sl < nsl && (!active || active[s0 + sl])) dpart[(size_t)(s0 + sl) * nparts + chunk] = (double)t;
     }
   }
 }
