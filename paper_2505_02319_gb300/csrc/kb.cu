@@ -13,8 +13,8 @@
 // k-point as a vector set, exactly like the occupied orbitals of the
 // Q-projection: C = B_k^H in and out += B_k C run on the library's own
 // projection kernels (FP64 and double-float on the CUDA cores; FP32 on the
-// CUDA cores or, with ikr_set_tensor_cores, as tcgen05 MMAs with the three-term
-// TF32 split), all k-points in one launch each; between them a scaling kernel
+// CUDA cores or, with ikr_set_tensor_cores, as tcgen05 MMAs on the exact
+// three-piece bf16 split), all k-points in one launch each; between them a scaling kernel
 // applies diag(D) and folds <in, V_nl in> = sum_j D_j |(B^H in)_j|^2 into the
 // first <p, Ap> partial of a CG iteration.
 #include <cmath>
